@@ -1,0 +1,29 @@
+"""Plain FP64 CPU oracle of the Galilean-PSATD particle-in-cell step.
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and
+the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import
+it. The product path (the CUDA library and its Python binding) never calls
+it and shares no code with it.
+
+What it computes, stage by stage, in the order the paper gives (the paragraph
+after the Galilean-PSATD update equations): particles deposit the current at
+(n+1/2)dt and the charge density at (n+1)dt on the grid nodes, the sources go
+to Fourier space, the spectral E and B advance with the Galilean-PSATD update,
+the fields go back to real space, are interpolated to the particles, and the
+particles advance with the Galilean equations of motion.
+
+Modules:
+
+* ``coefficients`` - the per-mode coefficients C, S, nu, theta, chi1..chi3 of
+  the update, evaluated from their literal closed forms in 40-digit mpmath;
+* ``shapes``       - B-spline particle shapes evaluated from their definition;
+* ``pic``          - grid, deposit, gather, Boris push, Galilean drift,
+  spectral current correction, the update, energy and residual diagnostics
+  and the full step.
+
+Parity status: the coefficients, the vacuum update, the deposit/gather, the
+FFT and the push are pinned against closed forms, quadrature, library
+routines and invariants in ``tests/test_oracle_*.py``. The full plasma step
+has no printed values in the paper to pin against: "parity unpinned" for the
+plasma step beyond those invariants and the qualitative NCI claim.
+"""
