@@ -1,0 +1,342 @@
+"""Benchmark of the Galilean-PSATD PIC step on GB300 (one JSON line on stdout).
+
+Workload: uniform neutral electron-proton plasma drifting along +z at gamma=130
+on a periodic 256x256x512 grid, dx=dy=dz=1, dt=dz/c, 2x2x2 particles per cell
+per species on a regular lattice plus seeded 1e-3 cell jitter (536,870,912
+particles), cubic shapes, v_gal = v_drift, FP32 fields/particles with
+FP64-built coefficient tables. A step is one full pass of the path: gather,
+Boris push, Galilean drift, deposit of J and rho, forward FFT, k-space update,
+inverse FFT.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same plasma (the paper publishes no code or throughput for this
+step). Under torchrun (N > 1) every rank runs an independent replica of the
+workload (the step does not shard; replicas only) and value is the sum over
+ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-pushes/s per full Galilean-PSATD PIC step; p50/p99 batched-run latency"
+UNIT = "particle-pushes/s"
+GRID = (256, 256, 512)
+GAMMA = 130.0
+
+
+def workload(grid=GRID, order=3, precision=32):
+    import galpic_inputs as gi
+    return gi.drifting_plasma(*grid, GAMMA, galilean=True, shape_order=order, precision=precision,
+                              ppc=(2, 2, 2), jitter=1e-3, seed=2,
+                              name=f"drifting_plasma_{grid[0]}x{grid[1]}x{grid[2]}")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def particle_bytes(wl, precision):
+    """Algorithmic HBM bytes of one particle pass: each particle's cell, offsets and
+    momenta read and written once; E, B read once per node; J, rho written once per node."""
+    T = 8 if precision == 64 else 4
+    P = wl.nparticles
+    N = wl.ncells
+    return P * 2 * (4 + 6 * T) + N * (6 * T + 4 * T)
+
+
+def kspace_bytes(wl, precision):
+    """Algorithmic HBM bytes of one k-space update: reads E, B, J, rho^{n+1}, rho^n and six
+    factors; writes E, B twice (master and inverse-FFT copy) and rho^n (complex)."""
+    C = 16 if precision == 64 else 8
+    M = wl.nx * wl.ny * (wl.nz // 2 + 1)
+    return M * C * (6 + 4 + 1 + 6 + 6 + 6 + 1)
+
+
+def cpu_baseline(steps=2, grid=(16, 16, 32)):
+    """The FP64 oracle, as it stands, on a bounded sample of the same plasma."""
+    import numpy as np  # noqa: F401
+    from oracle import pic, problems
+    wl = workload(grid, order=3, precision=64)
+    cfg, st = problems.initial_state(wl)
+    pic.step(cfg, st)          # warm caches (coefficient tables are built in initial_state)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        pic.step(cfg, st)
+    dt = time.perf_counter() - t0
+    P = wl.nparticles
+    return {"value": P * steps / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{steps} FP64 oracle steps of the same gamma=130 cubic drifting plasma at "
+                      f"{grid[0]}x{grid[1]}x{grid[2]} ({P} particles); numpy deposit/gather single-threaded, "
+                      f"scipy.fft on all cores"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    grid = (16, 16, 32)
+    from oracle import pic, problems
+    wl = workload(grid, order=3, precision=64)
+    cfg, st = problems.initial_state(wl)
+    for _ in range(args.warmup):
+        pic.step(cfg, st)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        pic.step(cfg, st)
+    dt = time.perf_counter() - t0
+    P = wl.nparticles
+    v = P * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl.name + " (bounded sample of the GPU arm's plasma)",
+                                            "grid": list(grid), "particles": P, "shape_order": 3},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{args.steps} FP64 oracle steps at {grid[0]}x{grid[1]}x{grid[2]} "
+                                       f"({P} particles) of the same plasma"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    from paper_1608_00215_gb300 import build
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_1608_00215_gb300 import galpic as gp
+
+    grid = tuple(int(x) for x in args.grid.split(","))
+    wl = workload(grid, order=args.order)
+    P, N = wl.nparticles, wl.ncells
+    sim = gp.sim_from_workload(wl, precision=32)
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        sim.gather_push()
+        sim.field_update()
+    torch.cuda.synchronize()
+    sim.profile(True)
+    c0 = sim.counters()
+    stream = torch.cuda.current_stream()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            sim.gather_push()
+            sim.field_update()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = ev0.elapsed_time(ev1)
+    stages = sim.profile_read()
+    sim.profile(False)
+    c1 = sim.counters()
+    launches = c1["launches"] - c0["launches"]
+    W = sim.energy()
+    status = sim.status()
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+
+    # end to end through the C ABI from pinned host buffers: H2D of the initial
+    # particles inside pic_init, K steps each followed by a D2H read of the field energy
+    e2e = e2e_run(gp, wl, args.steps) if not args.no_e2e else {"seconds": float("nan"), "h2d": 0, "d2h": 0}
+
+    t = torch.tensor([ms, e2e["seconds"]], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max, e2e_max = float(t[0]), float(t[1])
+    if rank != 0:
+        return
+    hbm, peak_kind = peaks()
+    part = stages["particles"]
+    ks = stages["kspace"]
+    part_ms = part["ms"] / max(1, part["count"])
+    ks_ms = ks["ms"] / max(1, ks["count"])
+    achieved = particle_bytes(wl, 32) / (part_ms * 1e-3) / 1e9
+    ks_achieved = kspace_bytes(wl, 32) / (ks_ms * 1e-3) / 1e9
+    value = P * args.steps * world / (ms_max * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name + " (gamma=130 e-p plasma, 2x2x2 ppc/species, cubic shapes, "
+                                         "v_gal=v_drift, FP32 with FP64-built tables)",
+                   "grid": list(grid), "particles": P, "cells": N, "shape_order": args.order, "precision": 32,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (15 GB of particles, 0.8 GB of fields); no flush"},
+        "cell_updates_per_s": N * args.steps * world / (ms_max * 1e-3),
+        "stages_ms_per_step": {k: v["ms"] / max(1, v["count"]) for k, v in stages.items() if v["count"]},
+        "roofline": {"bound": "hbm", "kernel": f"particle_pass_kernel<float,{args.order},STEP>", "achieved": achieved,
+                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                     "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": particle_bytes(wl, 32)},
+        "roofline_kspace": {"bound": "hbm", "achieved": ks_achieved, "peak": hbm, "unit": "GB/s",
+                            "frac": ks_achieved / hbm},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "field_energy_after": W, "device_status": status,
+        "e2e": {"value": P * args.steps * world / e2e_max, "unit": UNIT,
+                "h2d_bytes_per_step": e2e["h2d"] / args.steps, "d2h_bytes_per_step": e2e["d2h"] / args.steps,
+                "seconds": e2e_max, "includes": "pic_init from pinned host particles (H2D), FP64 table "
+                                                "build, sort, initial fields, K steps each with a D2H "
+                                                "read of the field energy"},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+def e2e_run(gp, wl, steps):
+    import torch
+    sim = gp.sim_from_workload(wl, precision=32)
+    host = []
+    for k in range(len(wl.species)):
+        p = sim.get_particles(k, device="cpu")
+        host.append(p)
+    torch.cuda.synchronize()
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    pinned = []
+    h2d = 0
+    for p in host:
+        d = {"cell": p["cell"].pin_memory(), "off": [t.pin_memory() for t in p["off"]],
+             "u": [t.pin_memory() for t in p["u"]]}
+        pinned.append(d)
+        h2d += sum(t.numel() * t.element_size() for t in [d["cell"]] + d["off"] + d["u"])
+    del host
+    cfg = gp.make_config(wl.nx, wl.ny, wl.nz, dx=wl.dx, dy=wl.dy, dz=wl.dz, dt=wl.dt, vgal=wl.vgal,
+                         c=wl.c, eps0=wl.eps0, rho_bg=wl.rho_bg, beta_init=wl.beta_init,
+                         shape_order=wl.shape_order, precision=32,
+                         current_correction=wl.current_correction, init_fields=wl.init_fields)
+    species = [gp.copied_species(s.q, s.m, wl.weight(s), d["cell"], d["off"], d["u"])
+               for s, d in zip(wl.species, pinned)]
+    out = torch.empty(1, dtype=torch.float64).pin_memory()
+    dev = torch.empty(1, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim = gp.Sim(cfg, species)
+    for _ in range(steps):
+        sim.step(1)
+        sim.energy_async(dev)
+        out.copy_(dev, non_blocking=True)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    return {"seconds": sec, "h2d": h2d, "d2h": 8 * steps}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--grid", default=",".join(str(x) for x in GRID),
+                    help="nx,ny,nz of the drifting plasma (default: the 256x256x512 workload)")
+    ap.add_argument("--order", type=int, default=3, help="shape order (default 3)")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

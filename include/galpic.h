@@ -1,0 +1,230 @@
+/*
+ * galpic.h - C ABI of the Galilean-PSATD particle-in-cell step (GB300, sm_103a).
+ *
+ * Method: Kirchen et al., "Stable discrete representation of relativistically
+ * drifting plasmas" (arXiv:1608.00215). The particle-in-cell equations are
+ * written in Galilean coordinates x' = x - v_gal t (the coordinate transform
+ * and the transformed equations of motion and Maxwell equations at the start
+ * of the method section); the spectral fields advance with the Galilean-PSATD
+ * update (the update equations and the coefficient block C, S, nu, theta,
+ * chi1, chi2, chi3 that follows them); one step deposits J at (n+1/2)dt and
+ * rho at (n+1)dt, transforms them to Fourier space, updates E and B,
+ * transforms back, interpolates to the particles and advances them (the
+ * paragraph that follows the update equations).
+ *
+ * Conventions used by every call:
+ *   - Grid: nx*ny*nz collocated nodes, periodic; real arrays are row-major
+ *     [nx][ny][nz] (z contiguous). Spectral arrays are the R2C half spectrum
+ *     [nx][ny][nz/2+1] of interleaved complex numbers (re, im).
+ *   - Forward transform exp(-i k.x), inverse with 1/N; Nyquist planes of
+ *     even axes are held at zero.
+ *   - A particle sits at ((i + f_x) dx, (j + f_y) dy, (l + f_z) dz) with the
+ *     linear cell index cell = (i*ny + j)*nz + l (int32) and offsets
+ *     f in [0, 1); u = gamma v is the momentum per mass.
+ *   - precision 32: offsets, momenta, grids and spectra are float; the
+ *     coefficient tables are built in double and rounded to float.
+ *     precision 64: everything is double.
+ *   - Streams are cudaStream_t values passed as void* (NULL = legacy default
+ *     stream). Every call is asynchronous on its stream unless it says
+ *     otherwise.
+ *   - Memory: the caller allocates ONE device workspace of pic_footprint()
+ *     bytes and owns it; the library carves every grid, spectrum, table and
+ *     particle array out of it and never calls cudaMalloc for them. The
+ *     library owns only its cuFFT plans, one private stream, a CUDA graph
+ *     and the small host handle (freed by pic_destroy).
+ *   - Errors: every int-returning call returns PIC_OK (0) or a negative
+ *     PIC_E* code and leaves a message for pic_last_error() (thread-local).
+ *     Conditions that the device detects (non-finite field energy) are
+ *     recorded in a device status word and reported by pic_status(). No
+ *     call aborts the process.
+ */
+#ifndef GALPIC_H
+#define GALPIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_OK 0
+#define PIC_EINVAL (-1)     /* invalid argument or configuration            */
+#define PIC_ENOMEM (-2)     /* workspace smaller than pic_footprint()        */
+#define PIC_ECUDA (-3)      /* a CUDA runtime call failed                    */
+#define PIC_ETIMEOUT (-4)   /* a bounded device wait gave up                 */
+#define PIC_ENONFINITE (-5) /* a diagnostic saw a NaN or infinity            */
+#define PIC_EBOUNDS (-6)    /* an index left its buffer (checked build)      */
+#define PIC_ECUFFT (-7)     /* a cuFFT call failed                           */
+
+#define PIC_MAX_SPECIES 8
+
+/* Status bits of the device status word (pic_status). */
+#define PIC_STATUS_NONFINITE 1  /* a diagnostic saw a NaN or infinity                  */
+#define PIC_STATUS_BADINPUT 2   /* loaded particles had a cell outside [0, N) or an
+                                   offset outside [0, 1); they were clamped to cell 0 /
+                                   offset 0 so that every kernel stays in bounds         */
+
+typedef struct pic_sim pic_sim;
+
+/* Problem statement of one run (the paper's grid, time step and v_gal). */
+typedef struct {
+    double dx, dy, dz;          /* cell size                                          */
+    double dt;                  /* time step                                          */
+    double vgal[3];             /* Galilean frame velocity, |v_gal| < c               */
+    double c;                   /* speed of light                                     */
+    double eps0;                /* vacuum permittivity (mu0 = 1/(eps0 c^2))           */
+    double rho_bg;              /* uniform background charge density that is static
+                                   on the moving grid: adds rho_bg to rho and
+                                   rho_bg*v_gal to J                                   */
+    double beta_init[3];        /* drift velocity / c of the initial field            */
+    int32_t nx, ny, nz;         /* grid nodes per axis, each >= 2                     */
+    int32_t shape_order;        /* particle shape: B-spline of order 1, 2 or 3        */
+    int32_t precision;          /* 32 or 64                                           */
+    int32_t current_correction; /* 1: enforce the discrete Galilean continuity
+                                   equation per mode on J before the update           */
+    int32_t init_fields;        /* 0: E = B = 0; 1: field of rho^0 moving rigidly at
+                                   beta_init*c (boosted Coulomb, satisfies Gauss)     */
+    int32_t reserved;
+} pic_config;
+
+/* One particle species. Particles are either generated on the device on a
+ * regular lattice with seeded jitter (ppc[0] > 0) or copied from caller
+ * arrays (host or device memory) at pic_init. */
+typedef struct {
+    double q;                   /* charge of one physical particle                    */
+    double m;                   /* mass of one physical particle                      */
+    double w;                   /* macro weight (physical particles per macro)        */
+    double jitter;              /* generated: uniform jitter half-width in cells      */
+    double u0[3];               /* generated: initial momentum per mass               */
+    int64_t n;                  /* number of macro particles                          */
+    uint64_t seed;              /* generated: random seed                             */
+    int32_t ppc[3];             /* generated: lattice particles per cell per axis;
+                                   n must equal nx*ny*nz*ppc[0]*ppc[1]*ppc[2]          */
+    int32_t species_id;         /* generated: enters the random key (seed ^ id<<56)   */
+    const int32_t* cell;        /* copied: linear cell index, n entries               */
+    const void* off[3];         /* copied: offsets in [0,1), float or double          */
+    const void* u[3];           /* copied: momentum per mass, float or double         */
+} pic_species;
+
+/* Buffers that pic_get / pic_set address. */
+enum pic_buffer {
+    PIC_BUF_E = 0,        /* real E^n, 3*N values (x, y, z planes)                      */
+    PIC_BUF_B = 1,        /* real B^n, 3*N                                             */
+    PIC_BUF_J = 2,        /* real J of the last particle pass, 3*N                       */
+    PIC_BUF_RHO = 3,      /* real rho of the last particle pass, N                       */
+    PIC_BUF_E_HAT = 4,    /* spectral E^n, 3*M complex                                 */
+    PIC_BUF_B_HAT = 5,    /* spectral B^n, 3*M complex                                 */
+    PIC_BUF_RHO_HAT = 6,  /* spectral rho^n, M complex                                  */
+    PIC_BUF_SRC_HAT = 7,  /* spectra of the last sources (Jx, Jy, Jz, rho), 4*M complex  */
+    PIC_BUF_TABLES = 8    /* per-mode factors T1, T2, T3, T4, A5, A6, 6*M complex        */
+};
+
+/* Library version string. */
+const char* pic_version(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* pic_last_error(void);
+
+/* Bytes of device workspace that pic_init needs for this configuration.
+ * Needs a CUDA device (it sizes the cuFFT work area). Returns PIC_EINVAL for
+ * an invalid configuration. */
+int pic_footprint(const pic_config* cfg, const pic_species* species, int nspecies,
+                  size_t* bytes_out);
+
+/* Create a run: validate, carve the caller-owned device workspace (at least
+ * pic_footprint() bytes, 256-byte aligned), build the FP64 coefficient
+ * tables, load or generate the particles and sort them into cell bins,
+ * deposit rho^0, and set the initial fields. Enqueued on `stream`, then
+ * synchronises that stream: returns PIC_EINVAL (and no run) if copied
+ * particles were out of range (PIC_STATUS_BADINPUT). The species array is
+ * read during the call only. */
+int pic_init(const pic_config* cfg, const pic_species* species, int nspecies,
+             void* workspace, size_t ws_bytes, void* stream, pic_sim** out);
+
+/* Release the host handle, cuFFT plans, private stream and graph. The
+ * workspace stays the caller's. Synchronises the run's work first. */
+int pic_destroy(pic_sim* sim);
+
+/* Deposit rho and J = sum q w v S / dV at the current positions x^n with the
+ * current momenta into the real source grids (J, RHO buffers); the shape
+ * factor of the paper's "deposited to the grid nodes". */
+int pic_deposit(pic_sim* sim, void* stream);
+
+/* The particle half of a step: gather E^n, B^n at x^n (interpolation to the
+ * particles), relativistic Boris push u^{n-1/2} -> u^{n+1/2}, half Galilean
+ * drift x' += (v - v_gal) dt/2, deposit J^{n+1/2}, second half drift, deposit
+ * rho^{n+1}. Re-sorts the particles into cell bins first when the previous
+ * pass left too many outside their bin. */
+int pic_gather_push(pic_sim* sim, void* stream);
+
+/* The field half of a step: forward R2C FFT of Jx, Jy, Jz, rho^{n+1};
+ * optional current correction; Galilean-PSATD update of spectral E, B;
+ * Nyquist zeroing; rho^n <- rho^{n+1}; inverse C2R FFT to the real E, B. */
+int pic_field_update(pic_sim* sim, void* stream);
+
+/* nsteps full steps (pic_gather_push then pic_field_update), replayed from a
+ * CUDA graph captured on the first call. */
+int pic_step(pic_sim* sim, int nsteps, void* stream);
+
+/* Advance several runs by nsteps each, all enqueued on one stream. */
+int pic_step_many(pic_sim** sims, int nsims, int nsteps, void* stream);
+
+/* Field energy W = (eps0/2) sum (|E|^2 + c^2 |B|^2) dV of the real E^n, B^n,
+ * written as one double to the DEVICE address out_dev. Sets
+ * PIC_STATUS_NONFINITE in the status word if any field value is not finite. */
+int pic_diag_energy(pic_sim* sim, double* out_dev, void* stream);
+
+/* Copy a buffer out to dst (host or device, `bytes` must equal its size). */
+int pic_get(pic_sim* sim, int which, void* dst, size_t bytes, void* stream);
+
+/* Overwrite the spectral E^n, B^n or rho^n (PIC_BUF_E_HAT, _B_HAT, _RHO_HAT)
+ * from src (host or device). Setting E_HAT or B_HAT recomputes the real E, B. */
+int pic_set(pic_sim* sim, int which, const void* src, size_t bytes, void* stream);
+
+/* Copy one species' particles out (in the library's current order, which is
+ * sorted by cell bin) to caller arrays (host or device). Any pointer may be
+ * NULL to skip that array. */
+int pic_get_particles(pic_sim* sim, int species, int32_t* cell, void* off[3], void* u[3],
+                      void* stream);
+
+/* Replace one species' particles (n must match) and re-sort them into bins.
+ * Out-of-range input is clamped and flagged with PIC_STATUS_BADINPUT. */
+int pic_set_particles(pic_sim* sim, int species, const int32_t* cell, const void* const off[3],
+                      const void* const u[3], void* stream);
+
+/* Re-sort every species into its cell bins now (the order pic_get_particles
+ * returns is then stable until a later pass finds too many particles outside
+ * their bins). */
+int pic_sort(pic_sim* sim, void* stream);
+
+/* Synchronising: read the device status word (PIC_STATUS_* bits) and clear
+ * it. Returns PIC_ENONFINITE if the non-finite bit was set, else PIC_OK. */
+int pic_status(pic_sim* sim, int32_t* status_out);
+
+/* Synchronising: read the run's counters: [0] steps taken, [1] particle
+ * re-sorts performed, [2] particles outside their bin after the last pass,
+ * [3] particles handled by the out-of-tile path in the last pass, [4] the
+ * library's own kernel launches enqueued so far (graph replays included;
+ * cuFFT's kernels and memsets not counted), [5] reserved (0). */
+int pic_counters(pic_sim* sim, int64_t out[6]);
+
+/* Stage timing (tracing). While enabled, the uncaptured calls pic_gather_push,
+ * pic_field_update and pic_diag_energy record a CUDA event pair around each
+ * stage on their stream: 0 particle re-sort check, 1 particle pass (gather,
+ * push, deposit), 2 forward FFT, 3 k-space update, 4 inverse FFT, 5 energy.
+ * pic_step replays a graph and records nothing. Enabling clears old records. */
+int pic_profile(pic_sim* sim, int enable);
+
+/* Synchronising: per stage, the summed milliseconds and the number of
+ * recorded intervals since the last read (or enable); clears the records. */
+int pic_profile_read(pic_sim* sim, double ms[8], int64_t count[8]);
+
+/* Grid sizes of a run: N = nx*ny*nz and M = nx*ny*(nz/2+1). */
+int pic_sizes(pic_sim* sim, int64_t* n_cells, int64_t* n_modes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GALPIC_H */

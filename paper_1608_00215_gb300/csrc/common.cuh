@@ -1,0 +1,189 @@
+// Internal definitions shared by the galpic CUDA sources (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "galpic.h"
+
+namespace galpic {
+
+// ---------------------------------------------------------------------------
+// Error plumbing
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+
+#define GP_CUDA(call)                                                                 \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess)                                                        \
+            return ::galpic::fail(PIC_ECUDA, std::string(#call) + ": " +              \
+                                                 cudaGetErrorString(e_));             \
+    } while (0)
+
+#define GP_CUFFT(call)                                                                \
+    do {                                                                              \
+        cufftResult r_ = (call);                                                      \
+        if (r_ != CUFFT_SUCCESS)                                                      \
+            return ::galpic::fail(PIC_ECUFFT, std::string(#call) + ": cufft error " + \
+                                                  std::to_string((int)r_));           \
+    } while (0)
+
+#define GP_CHECK(expr)                                                                \
+    do {                                                                              \
+        int rc_ = (expr);                                                             \
+        if (rc_ != PIC_OK) return rc_;                                                \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Complex helpers for float2 / double2
+// ---------------------------------------------------------------------------
+template <typename T> struct cplx;
+template <> struct cplx<float> { typedef float2 type; };
+template <> struct cplx<double> { typedef double2 type; };
+
+template <typename C> __host__ __device__ __forceinline__ C mk(double re, double im) {
+    C r; r.x = (decltype(r.x))re; r.y = (decltype(r.y))im; return r;
+}
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+    C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+template <typename C, typename T> __host__ __device__ __forceinline__ C cscale(C a, T s) { a.x *= s; a.y *= s; return a; }
+template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
+template <typename C> __host__ __device__ __forceinline__ C ctimesi(C a) { C r; r.x = -a.y; r.y = a.x; return r; }
+__host__ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    double d = b.x * b.x + b.y * b.y;
+    double2 r; r.x = (a.x * b.x + a.y * b.y) / d; r.y = (a.y * b.x - a.x * b.y) / d; return r;
+}
+
+// ---------------------------------------------------------------------------
+// Counters in device memory (uint64 each)
+// ---------------------------------------------------------------------------
+enum {
+    CNT_FORCE_SORT = 0,   // nonzero: re-sort before the next particle pass
+    CNT_SORTS = 1,        // re-sorts performed
+    CNT_HOME_MISS = 2,    // particles outside their bin after the last pass
+    CNT_FAR = 3,          // particles that took the out-of-tile path in the last pass
+    CNT_THRESHOLD = 4,    // re-sort when HOME_MISS exceeds this
+    CNT_COUNT = 8
+};
+
+// Decision shared by every re-sort kernel: identical for all of them because
+// none of them writes the words it reads (the final kernel clears FORCE last).
+__device__ __forceinline__ bool sort_needed(const unsigned long long* cnt) {
+    return cnt[CNT_FORCE_SORT] != 0ull || cnt[CNT_FAR] != 0ull ||
+           cnt[CNT_HOME_MISS] > cnt[CNT_THRESHOLD];
+}
+
+// ---------------------------------------------------------------------------
+// splitmix64 (Vigna): output function applied to a counter
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// ---------------------------------------------------------------------------
+// Internal run handle
+// ---------------------------------------------------------------------------
+struct SpeciesDev {
+    double q, m, w;
+    int64_t n;
+    int32_t* cell;
+    void* off[3];
+    void* u[3];
+    int32_t* bin_start;   // nbins + 1
+};
+
+struct Layout {
+    size_t total;
+    size_t off_species[PIC_MAX_SPECIES][8];   // cell, off x/y/z, u x/y/z, bin_start
+    size_t off_tmp[8];                        // cell, off x/y/z, u x/y/z, rank
+    size_t off_bin_cnt;
+    size_t off_F, off_S, off_EBh, off_EBs, off_Sh, off_Rn, off_Tab;
+    size_t off_fftwork;
+    size_t off_epart;
+    size_t off_cnt, off_status;
+    size_t fft_bytes;
+};
+
+struct Dims {
+    int nx, ny, nz, nzh;
+    int64_t N, M;
+    int BX, BY, BZ, nbx, nby, nbz, nbins;
+    int margin;
+};
+
+struct pic_sim_impl;
+
+}  // namespace galpic
+
+struct pic_sim {
+    pic_config cfg;
+    int nspecies;
+    galpic::SpeciesDev sp[PIC_MAX_SPECIES];
+    galpic::Dims d;
+    galpic::Layout L;
+    char* ws;
+    size_t ws_bytes;
+    void* F;     // real E (3N) then B (3N)
+    void* S;     // real Jx, Jy, Jz, rho (4N)
+    void* EBh;   // spectral master E, B (6M complex)
+    void* EBs;   // C2R input: master / N (6M complex)
+    void* Sh;    // spectra of Jx, Jy, Jz, rho^{n+1} (4M complex)
+    void* Rn;    // spectral rho^n (M complex)
+    void* Tab;   // per-mode factors T1..T4, A5, A6 (6M complex)
+    void* fftwork;
+    double* epart;
+    int energy_blocks;
+    int32_t* tmp_cell;
+    void* tmp_off[3];
+    void* tmp_u[3];
+    int32_t* tmp_rank;
+    int32_t* bin_cnt;
+    unsigned long long* cnt;
+    int32_t* status;
+    cufftHandle plan_r2c, plan_c2r;
+    cudaStream_t priv;
+    cudaGraphExec_t graph;
+    bool graph_ok;
+    int64_t steps;
+    int64_t launches;        // own kernel launches enqueued (incl. graph replays)
+    int64_t graph_kernels;   // own kernels in one captured step
+    bool capturing;
+    bool profiling;
+    struct Rec { int stage; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+namespace galpic {
+
+// Launchers implemented in the .cu files (all enqueue on `st`).
+int launch_build_tables(pic_sim* s, cudaStream_t st);
+int launch_kspace_update(pic_sim* s, cudaStream_t st);
+int launch_init_fields(pic_sim* s, cudaStream_t st);
+int launch_master_to_scratch(pic_sim* s, cudaStream_t st);
+int launch_energy(pic_sim* s, double* out_dev, cudaStream_t st);
+int launch_generate(pic_sim* s, int species, const pic_species* spec, cudaStream_t st);
+int launch_sort(pic_sim* s, cudaStream_t st);
+int launch_sanitize(pic_sim* s, int species, cudaStream_t st);
+int launch_particle_pass(pic_sim* s, int mode, cudaStream_t st);
+
+enum { PASS_STEP = 0, PASS_DEPOSIT = 1 };
+enum { STAGE_SORT = 0, STAGE_PARTICLES = 1, STAGE_R2C = 2, STAGE_KSPACE = 3, STAGE_C2R = 4,
+       STAGE_ENERGY = 5, STAGE_COUNT = 8 };
+
+// Shared-memory bytes of one particle-pass CTA.
+size_t tile_bytes(const pic_config& c, const Dims& d, int mode);
+
+}  // namespace galpic

@@ -1,0 +1,291 @@
+"""ctypes binding of ``libgalpic.so`` (C ABI: ``include/galpic.h``).
+
+Argument marshalling only: every stage of the step runs in the library's CUDA
+kernels (and cuFFT). PyTorch supplies device memory (the run's workspace) and
+streams. The library must have been built (``paper_1608_00215_gb300.build``);
+loading fails loudly otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int, c_int32, c_int64, c_size_t, c_uint64, c_void_p
+from typing import Dict, List, Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgalpic.so")
+
+PIC_OK = 0
+ERRORS = {-1: "PIC_EINVAL", -2: "PIC_ENOMEM", -3: "PIC_ECUDA", -4: "PIC_ETIMEOUT",
+          -5: "PIC_ENONFINITE", -6: "PIC_EBOUNDS", -7: "PIC_ECUFFT"}
+PIC_MAX_SPECIES = 8
+PIC_STATUS_NONFINITE = 1
+
+BUF_E, BUF_B, BUF_J, BUF_RHO, BUF_E_HAT, BUF_B_HAT, BUF_RHO_HAT, BUF_SRC_HAT, BUF_TABLES = range(9)
+
+
+class PicConfig(ctypes.Structure):
+    _fields_ = [("dx", c_double), ("dy", c_double), ("dz", c_double), ("dt", c_double),
+                ("vgal", c_double * 3), ("c", c_double), ("eps0", c_double), ("rho_bg", c_double),
+                ("beta_init", c_double * 3),
+                ("nx", c_int32), ("ny", c_int32), ("nz", c_int32), ("shape_order", c_int32),
+                ("precision", c_int32), ("current_correction", c_int32), ("init_fields", c_int32),
+                ("reserved", c_int32)]
+
+
+class PicSpecies(ctypes.Structure):
+    _fields_ = [("q", c_double), ("m", c_double), ("w", c_double), ("jitter", c_double),
+                ("u0", c_double * 3), ("n", c_int64), ("seed", c_uint64), ("ppc", c_int32 * 3),
+                ("species_id", c_int32), ("cell", c_void_p), ("off", c_void_p * 3),
+                ("u", c_void_p * 3)]
+
+
+class GalpicError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run paper_1608_00215_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = c_void_p
+    sig = {
+        "pic_version": (c_char_p, []),
+        "pic_last_error": (c_char_p, []),
+        "pic_footprint": (c_int, [POINTER(PicConfig), POINTER(PicSpecies), c_int, POINTER(c_size_t)]),
+        "pic_init": (c_int, [POINTER(PicConfig), POINTER(PicSpecies), c_int, P, c_size_t, P, POINTER(P)]),
+        "pic_destroy": (c_int, [P]),
+        "pic_deposit": (c_int, [P, P]),
+        "pic_gather_push": (c_int, [P, P]),
+        "pic_field_update": (c_int, [P, P]),
+        "pic_step": (c_int, [P, c_int, P]),
+        "pic_step_many": (c_int, [POINTER(P), c_int, c_int, P]),
+        "pic_diag_energy": (c_int, [P, P, P]),
+        "pic_get": (c_int, [P, c_int, P, c_size_t, P]),
+        "pic_set": (c_int, [P, c_int, P, c_size_t, P]),
+        "pic_get_particles": (c_int, [P, c_int, P, POINTER(P), POINTER(P), P]),
+        "pic_set_particles": (c_int, [P, c_int, P, POINTER(P), POINTER(P), P]),
+        "pic_sort": (c_int, [P, P]),
+        "pic_status": (c_int, [P, POINTER(c_int32)]),
+        "pic_counters": (c_int, [P, POINTER(c_int64)]),
+        "pic_profile": (c_int, [P, c_int]),
+        "pic_profile_read": (c_int, [P, POINTER(c_double), POINTER(c_int64)]),
+        "pic_sizes": (c_int, [P, POINTER(c_int64), POINTER(c_int64)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+# the exported names, as declared in include/galpic.h
+EXPORTS = ("pic_version", "pic_last_error", "pic_footprint", "pic_init", "pic_destroy", "pic_deposit",
+           "pic_gather_push", "pic_field_update", "pic_step", "pic_step_many", "pic_diag_energy",
+           "pic_get", "pic_set", "pic_get_particles", "pic_set_particles", "pic_status",
+           "pic_counters", "pic_sizes", "pic_profile", "pic_profile_read", "pic_sort")
+
+STAGES = ("sort", "particles", "fft_r2c", "kspace", "fft_c2r", "energy")
+
+
+def check(rc: int) -> int:
+    if rc != PIC_OK:
+        raise GalpicError(rc, lib.pic_last_error().decode())
+    return rc
+
+
+def _stream_ptr(stream: Optional[torch.cuda.Stream]) -> c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return c_void_p(s.cuda_stream)
+
+
+def make_config(nx: int, ny: int, nz: int, *, dx=1.0, dy=1.0, dz=1.0, dt=1.0, vgal=(0.0, 0.0, 0.0),
+                c=1.0, eps0=1.0, rho_bg=0.0, beta_init=(0.0, 0.0, 0.0), shape_order=1,
+                precision=32, current_correction=1, init_fields=1) -> PicConfig:
+    cfg = PicConfig()
+    cfg.dx, cfg.dy, cfg.dz, cfg.dt = dx, dy, dz, dt
+    cfg.vgal[:] = list(vgal)
+    cfg.c, cfg.eps0, cfg.rho_bg = c, eps0, rho_bg
+    cfg.beta_init[:] = list(beta_init)
+    cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
+    cfg.shape_order, cfg.precision = shape_order, precision
+    cfg.current_correction, cfg.init_fields = current_correction, init_fields
+    return cfg
+
+
+def generated_species(q: float, m: float, w: float, ncells: int, ppc: Sequence[int], u0, jitter: float,
+                      seed: int, species_id: int) -> PicSpecies:
+    """A species generated on the device on a regular lattice with seeded jitter."""
+    s = PicSpecies()
+    s.q, s.m, s.w, s.jitter = q, m, w, jitter
+    s.u0[:] = list(u0)
+    s.n = ncells * ppc[0] * ppc[1] * ppc[2]
+    s.seed = seed
+    s.ppc[:] = list(ppc)
+    s.species_id = species_id
+    return s
+
+
+def copied_species(q: float, m: float, w: float, cell, off: Sequence, u: Sequence) -> PicSpecies:
+    """A species copied from caller arrays (torch tensors, host or device)."""
+    s = PicSpecies()
+    s.q, s.m, s.w = q, m, w
+    s.n = int(cell.numel())
+    s.cell = cell.data_ptr()
+    for d in range(3):
+        s.off[d] = off[d].data_ptr()
+        s.u[d] = u[d].data_ptr()
+    return s
+
+
+class Sim:
+    """One run: owns its device workspace (a torch uint8 tensor) and the library handle."""
+
+    def __init__(self, cfg: PicConfig, species: List[PicSpecies], stream=None, device="cuda",
+                 keepalive=()):
+        self.cfg = cfg
+        self.nspecies = len(species)
+        arr = (PicSpecies * max(1, len(species)))(*species)
+        self._species = arr
+        nbytes = c_size_t(0)
+        check(lib.pic_footprint(ctypes.byref(cfg), arr, len(species), ctypes.byref(nbytes)))
+        self.footprint = int(nbytes.value)
+        self.workspace = torch.empty(self.footprint, dtype=torch.uint8, device=device)
+        self.handle = c_void_p()
+        self.stream = stream
+        check(lib.pic_init(ctypes.byref(cfg), arr, len(species), c_void_p(self.workspace.data_ptr()),
+                           self.footprint, _stream_ptr(stream), ctypes.byref(self.handle)))
+        self.n = [int(s.n) for s in species]
+        self.real = torch.float64 if cfg.precision == 64 else torch.float32
+        self.cplx = torch.complex128 if cfg.precision == 64 else torch.complex64
+        nc, nm = c_int64(), c_int64()
+        check(lib.pic_sizes(self.handle, ctypes.byref(nc), ctypes.byref(nm)))
+        self.N, self.M = int(nc.value), int(nm.value)
+        self._energy = torch.zeros(1, dtype=torch.float64, device=device)
+        self._keepalive = keepalive
+        self.device = device
+
+    # --- stages ---------------------------------------------------------------
+    def deposit(self):
+        check(lib.pic_deposit(self.handle, _stream_ptr(self.stream)))
+
+    def gather_push(self):
+        check(lib.pic_gather_push(self.handle, _stream_ptr(self.stream)))
+
+    def field_update(self):
+        check(lib.pic_field_update(self.handle, _stream_ptr(self.stream)))
+
+    def step(self, nsteps: int = 1):
+        check(lib.pic_step(self.handle, nsteps, _stream_ptr(self.stream)))
+
+    def energy_async(self, out: torch.Tensor):
+        check(lib.pic_diag_energy(self.handle, c_void_p(out.data_ptr()), _stream_ptr(self.stream)))
+
+    def energy(self) -> float:
+        self.energy_async(self._energy)
+        return float(self._energy.item())
+
+    # --- state ----------------------------------------------------------------
+    def _shape(self, which: int):
+        nx, ny, nz = self.cfg.nx, self.cfg.ny, self.cfg.nz
+        nzh = nz // 2 + 1
+        return {BUF_E: ((3, nx, ny, nz), self.real), BUF_B: ((3, nx, ny, nz), self.real),
+                BUF_J: ((3, nx, ny, nz), self.real), BUF_RHO: ((nx, ny, nz), self.real),
+                BUF_E_HAT: ((3, nx, ny, nzh), self.cplx), BUF_B_HAT: ((3, nx, ny, nzh), self.cplx),
+                BUF_RHO_HAT: ((nx, ny, nzh), self.cplx), BUF_SRC_HAT: ((4, nx, ny, nzh), self.cplx),
+                BUF_TABLES: ((6, nx, ny, nzh), self.cplx)}[which]
+
+    def get(self, which: int, device=None) -> torch.Tensor:
+        shape, dt = self._shape(which)
+        out = torch.empty(shape, dtype=dt, device=device or self.device)
+        check(lib.pic_get(self.handle, which, c_void_p(out.data_ptr()),
+                          out.numel() * out.element_size(), _stream_ptr(self.stream)))
+        return out
+
+    def set(self, which: int, src: torch.Tensor):
+        src = src.contiguous()
+        check(lib.pic_set(self.handle, which, c_void_p(src.data_ptr()), src.numel() * src.element_size(),
+                          _stream_ptr(self.stream)))
+        self._pending = src
+
+    def get_particles(self, k: int, device=None) -> Dict[str, torch.Tensor]:
+        dev = device or self.device
+        n = self.n[k]
+        cell = torch.empty(n, dtype=torch.int32, device=dev)
+        off = [torch.empty(n, dtype=self.real, device=dev) for _ in range(3)]
+        u = [torch.empty(n, dtype=self.real, device=dev) for _ in range(3)]
+        po = (c_void_p * 3)(*[t.data_ptr() for t in off])
+        pu = (c_void_p * 3)(*[t.data_ptr() for t in u])
+        check(lib.pic_get_particles(self.handle, k, c_void_p(cell.data_ptr()), po, pu,
+                                    _stream_ptr(self.stream)))
+        return {"cell": cell, "off": off, "u": u}
+
+    def set_particles(self, k: int, cell: torch.Tensor, off: Sequence[torch.Tensor], u: Sequence[torch.Tensor]):
+        keep = [cell.contiguous()] + [t.contiguous() for t in off] + [t.contiguous() for t in u]
+        po = (c_void_p * 3)(*[t.data_ptr() for t in keep[1:4]])
+        pu = (c_void_p * 3)(*[t.data_ptr() for t in keep[4:7]])
+        check(lib.pic_set_particles(self.handle, k, c_void_p(keep[0].data_ptr()), po, pu,
+                                    _stream_ptr(self.stream)))
+        self._pending = keep
+
+    def sort(self):
+        check(lib.pic_sort(self.handle, _stream_ptr(self.stream)))
+
+    def status(self) -> int:
+        v = c_int32()
+        rc = lib.pic_status(self.handle, ctypes.byref(v))
+        if rc not in (PIC_OK, -5):
+            check(rc)
+        return int(v.value)
+
+    def counters(self) -> Dict[str, int]:
+        a = (c_int64 * 6)()
+        check(lib.pic_counters(self.handle, a))
+        return {"steps": a[0], "sorts": a[1], "home_miss": a[2], "far": a[3], "launches": a[4]}
+
+    def profile(self, enable: bool = True):
+        check(lib.pic_profile(self.handle, int(enable)))
+
+    def profile_read(self) -> Dict[str, Dict[str, float]]:
+        ms = (c_double * 8)()
+        cnt = (c_int64 * 8)()
+        check(lib.pic_profile_read(self.handle, ms, cnt))
+        return {name: {"ms": ms[i], "count": int(cnt[i])} for i, name in enumerate(STAGES)}
+
+    def close(self):
+        if self.handle:
+            check(lib.pic_destroy(self.handle))
+            self.handle = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def step_many(sims: Sequence[Sim], nsteps: int, stream=None):
+    arr = (c_void_p * len(sims))(*[s.handle for s in sims])
+    check(lib.pic_step_many(arr, len(sims), nsteps, _stream_ptr(stream)))
+
+
+def sim_from_workload(wl, precision: Optional[int] = None, stream=None, device="cuda") -> Sim:
+    """A run of a synthetic workload (duck-typed: grid, units, v_gal, species with
+    q, m, ppc, u0, jitter, density), particles generated on the device."""
+    prec = wl.precision if precision is None else precision
+    cfg = make_config(wl.nx, wl.ny, wl.nz, dx=wl.dx, dy=wl.dy, dz=wl.dz, dt=wl.dt, vgal=wl.vgal,
+                      c=wl.c, eps0=wl.eps0, rho_bg=wl.rho_bg, beta_init=wl.beta_init,
+                      shape_order=wl.shape_order, precision=prec,
+                      current_correction=wl.current_correction, init_fields=wl.init_fields)
+    ncells = wl.nx * wl.ny * wl.nz
+    sp = []
+    for k, s in enumerate(wl.species):
+        w = s.density * wl.dx * wl.dy * wl.dz / (s.ppc[0] * s.ppc[1] * s.ppc[2])
+        sp.append(generated_species(s.q, s.m, w, ncells, s.ppc, s.u0, s.jitter, wl.seed, k))
+    return Sim(cfg, sp, stream=stream, device=device)

@@ -1,0 +1,331 @@
+"""Parity of the CUDA library (through its C ABI) with the FP64 CPU oracle.
+
+Tolerances: FP64 mode 1e-11 relative L2 per step; FP32 mode 1e-5 per step and
+1e-4 over 20 steps on fixtures with O(1) fields; tables 1e-12 relative;
+integer/bit work (particle generation) bit-exact.
+"""
+import numpy as np
+import pytest
+
+import galpic_inputs as gi
+from oracle import coefficients as coef
+from oracle import pic, problems
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from helpers import field_rel_l2, oracle_state_from_sim, particle_errors, rel_l2  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def gp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1608_00215_gb300 import build
+    build.build()
+    from paper_1608_00215_gb300 import galpic
+    return galpic
+
+
+def _sorted_particles(cell, off, u):
+    keys = np.lexsort((off[2], off[1], off[0], cell))
+    return cell[keys], [a[keys] for a in off], [a[keys] for a in u]
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_generated_particles_bit_exact(gp, precision):
+    """On-device lattice + splitmix64 jitter equals the host generator bit for bit
+    (as multisets: the library stores particles sorted by bin)."""
+    wl = gi.drifting_plasma(12, 10, 18, 30.0, precision=precision, jitter=0.2, seed=77)
+    sim = gp.sim_from_workload(wl)
+    dt = np.float64 if precision == 64 else np.float32
+    for k in range(len(wl.species)):
+        p = sim.get_particles(k, device="cpu")
+        torch.cuda.synchronize()
+        h = gi.lattice_particles(wl, k)
+        hc = h.linear_cell(wl.ny, wl.nz)
+        hoff = [f.astype(dt) for f in (h.fx, h.fy, h.fz)]
+        hu = [x.astype(dt) for x in (h.ux, h.uy, h.uz)]
+        a = _sorted_particles(p["cell"].numpy(), [t.numpy() for t in p["off"]], [t.numpy() for t in p["u"]])
+        b = _sorted_particles(hc, hoff, hu)
+        np.testing.assert_array_equal(a[0], b[0])
+        for x, y in zip(a[1] + a[2], b[1] + b[2]):
+            np.testing.assert_array_equal(x, y)
+    sim.close()
+
+
+TABLE_CASES = [
+    dict(n=(8, 8, 16), vgal=(0.0, 0.0, gi.drift_v(130.0)), cc=0),
+    dict(n=(8, 8, 16), vgal=(0.0, 0.0, gi.drift_v(130.0)), cc=1),
+    dict(n=(4, 4, 1536), vgal=(0.0, 0.0, gi.drift_v(130.0)), cc=0),   # worst-conditioned modes
+    dict(n=(6, 5, 8), vgal=(0.3, -0.4, 0.5), cc=0, units=dict(c=1.7, dt=0.45, eps0=2.3, dx=0.8, dy=1.3, dz=0.6)),
+]
+
+
+@pytest.mark.parametrize("case", TABLE_CASES)
+def test_tables_match_literal_formulas(gp, case):
+    """FP64 tables built on the GPU from the stable integral forms equal the paper's
+    literal chi formulas evaluated in 40-digit arithmetic."""
+    u = case.get("units", {})
+    c = u.get("c", 1.0)
+    vgal = tuple(c * np.asarray(case["vgal"]))
+    cfg = gp.make_config(*case["n"], vgal=vgal, precision=64, current_correction=case["cc"], init_fields=0,
+                         **u)
+    sim = gp.Sim(cfg, [])
+    tab = sim.get(gp.BUF_TABLES, device="cpu").numpy()
+    torch.cuda.synchronize()
+    ocfg = pic.Config(*case["n"], vgal=vgal, **u)
+    t = pic.tables(ocfg)
+    kx, ky, kz = pic.kvectors(ocfg)
+    k2 = np.broadcast_to(kx * kx + ky * ky + kz * kz, t["T1"].shape)
+    safe = np.where(k2 > 0, k2, 1.0)
+    e0 = ocfg.eps0
+    if case["cc"]:
+        A5 = np.where(k2 > 0, -1j / (e0 * safe), 0.0)
+        A6 = np.where(k2 > 0, 1j * t["theta"] ** 2 * t["C"] / (e0 * safe), 0.0)
+    else:
+        A5, A6 = -1j * t["T5"], 1j * t["T6"]
+    want = [t["T1"], t["T2"], t["T3"], t["T4"], A5, A6]
+    ok = ~pic.nyquist_mask(ocfg)
+    # each factor against its size without the oscillating factor, so that zero
+    # crossings of cos, sin or chi3 do not inflate a relative error:
+    # |T1| <= 1, |T2| <= dt min(1, 1/phi), |T3| <= dt^2/eps0 min(1/2, 2/phi^2),
+    # |T4| <= dt/eps0 min(1, 1/phi), |A5|, |A6| <= min(1, phi^2)/(eps0 k^2)
+    dtt = ocfg.dt
+    phi = ocfg.c * np.sqrt(k2) * dtt
+    bound = [np.ones_like(phi), dtt * np.minimum(1, 1 / np.maximum(phi, 1e-300)),
+             dtt ** 2 / e0 * np.minimum(0.5, 2 / np.maximum(phi, 1e-300) ** 2),
+             dtt / e0 * np.minimum(1, 1 / np.maximum(phi, 1e-300)),
+             np.minimum(1, phi ** 2) / (e0 * safe), np.minimum(1, phi ** 2) / (e0 * safe)]
+    for q in range(6):
+        err = np.abs(tab[q] - want[q])[ok]
+        scale = np.maximum(np.abs(want[q][ok]), bound[q][ok])
+        scale = np.maximum(scale, 1e-300)
+        assert np.max(err / scale) < 1e-12, (q, np.max(err / scale))
+    sim.close()
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+@pytest.mark.parametrize("precision", [64, 32])
+def test_deposit_matches_oracle(gp, order, precision):
+    """rho and J = sum q w v S / dV at random positions (random momenta), several bins
+    and a ragged edge, against the oracle's deposit."""
+    wl = gi.drifting_plasma(12, 10, 18, 5.0, precision=precision, shape_order=order, jitter=0.0)
+    sim = gp.sim_from_workload(wl)
+    rng = np.random.default_rng(order + precision)
+    dt = torch.float64 if precision == 64 else torch.float32
+    for k, spec in enumerate(wl.species):
+        n = sim.n[k]
+        cell = torch.from_numpy(rng.integers(0, wl.ncells, n).astype(np.int32))
+        off = [torch.from_numpy(rng.uniform(0, 1, n)).to(dt) for _ in range(3)]
+        u = [torch.from_numpy(rng.normal(size=n) * 3).to(dt) for _ in range(3)]
+        sim.set_particles(k, cell, off, u)
+    sim.deposit()
+    rho = sim.get(gp.BUF_RHO, device="cpu").double().numpy()
+    J = sim.get(gp.BUF_J, device="cpu").double().numpy()
+    torch.cuda.synchronize()
+    cfg, st = oracle_state_from_sim(sim, wl)
+    want_rho = pic.deposit_rho(cfg, st.species)
+    vel = []
+    for sp in st.species:
+        g = np.sqrt(1 + (sp.ux ** 2 + sp.uy ** 2 + sp.uz ** 2) / cfg.c ** 2)
+        vel.append((sp.ux / g, sp.uy / g, sp.uz / g))
+    want_J = pic.deposit_J(cfg, st.species, vel)
+    tol = 1e-13 if precision == 64 else 2e-6
+    assert rel_l2(rho, want_rho) < tol
+    assert rel_l2(J, want_J) < tol
+    sim.close()
+
+
+STEP_CASES = [
+    dict(n=(16, 16, 32), gamma=130.0, galilean=True, order=3),
+    dict(n=(16, 16, 32), gamma=130.0, galilean=False, order=1),
+    dict(n=(12, 10, 18), gamma=10.0, galilean=True, order=2, jitter=0.2),
+    dict(n=(12, 10, 18), gamma=10.0, galilean=False, order=3, jitter=0.2),
+]
+
+
+@pytest.mark.parametrize("case", STEP_CASES)
+def test_fp64_step_parity(gp, case):
+    """One FP64 step from the same state (after 3 GPU steps): fields within 1e-11
+    relative L2 of the oracle, particles within 1e-12."""
+    wl = gi.drifting_plasma(*case["n"], case["gamma"], galilean=case["galilean"],
+                            shape_order=case["order"], precision=64, jitter=case.get("jitter", 0.05))
+    sim = gp.sim_from_workload(wl)
+    sim.step(3)
+    sim.sort()      # fix the particle order so that the next step keeps it
+    cfg, st = oracle_state_from_sim(sim, wl)
+    sim.step(1)
+    pic.step(cfg, st)
+    torch.cuda.synchronize()
+    assert field_rel_l2(sim, st) < 1e-11
+    pos, uerr = particle_errors(sim, st, wl)
+    assert pos < 1e-12 and uerr < 1e-12
+    sim.close()
+
+
+def test_fp64_initial_state_matches_oracle(gp):
+    """pic_init (deposit rho^0, boosted-Coulomb field) against the oracle's initial state."""
+    wl = gi.drifting_plasma(12, 10, 18, 30.0, galilean=True, shape_order=3, precision=64, jitter=0.1)
+    sim = gp.sim_from_workload(wl)
+    cfg, st_gpu = oracle_state_from_sim(sim, wl)
+    st0 = pic.init_state(cfg, st_gpu.species, wl.init_fields, wl.beta_init)
+    assert rel_l2(st_gpu.rho_hat, st0.rho_hat) < 1e-12
+    assert field_rel_l2(sim, st0) < 1e-11
+    sim.close()
+
+
+def test_energy_matches_oracle(gp):
+    wl = gi.drifting_plasma(12, 10, 18, 10.0, galilean=False, shape_order=2, precision=64, jitter=0.3)
+    sim = gp.sim_from_workload(wl)
+    sim.step(2)
+    W = sim.energy()
+    cfg, st = oracle_state_from_sim(sim, wl)
+    assert abs(W - pic.energy(cfg, st.E, st.B)) < 1e-12 * abs(W)
+    assert sim.status() == 0
+    sim.close()
+
+
+def test_graph_replay_equals_uncaptured_calls(gp):
+    """pic_step (graph replay) and pic_gather_push + pic_field_update give the same
+    state (to the rounding of the atomic deposit order)."""
+    wl = gi.drifting_plasma(12, 10, 18, 10.0, galilean=False, shape_order=3, precision=64, jitter=0.3)
+    a = gp.sim_from_workload(wl)
+    b = gp.sim_from_workload(wl)
+    a.step(3)
+    for _ in range(3):
+        b.gather_push()
+        b.field_update()
+    Ea, Ba = (a.get(gp.BUF_E, device="cpu").numpy(), a.get(gp.BUF_B, device="cpu").numpy())
+    Eb, Bb = (b.get(gp.BUF_E, device="cpu").numpy(), b.get(gp.BUF_B, device="cpu").numpy())
+    torch.cuda.synchronize()
+    assert rel_l2(Ea, Eb) < 1e-13 and rel_l2(Ba, Bb) < 1e-13
+    ca, cb = a.counters(), b.counters()
+    assert ca["sorts"] == cb["sorts"] and ca["launches"] == cb["launches"]
+    a.close()
+    b.close()
+
+
+def test_nonfinite_field_is_flagged(gp):
+    """A NaN placed in the spectral E (host-side) reaches the real field and the
+    energy diagnostic sets PIC_STATUS_NONFINITE; the run stays usable."""
+    wl = gi.drifting_plasma(8, 8, 8, 10.0, precision=64)
+    sim = gp.sim_from_workload(wl)
+    E = sim.get(gp.BUF_E_HAT, device="cpu")
+    torch.cuda.synchronize()
+    E[0, 1, 1, 1] = complex(float("nan"), 0.0)
+    sim.set(gp.BUF_E_HAT, E)
+    W = sim.energy()
+    assert np.isnan(W)
+    assert sim.status() & gp.PIC_STATUS_NONFINITE
+    assert sim.status() == 0          # reading clears the word
+
+
+def test_bad_particle_input_is_rejected(gp):
+    cfg = gp.make_config(8, 8, 8, precision=64)
+    n = 16
+    cell = torch.full((n,), 8 * 8 * 8 + 5, dtype=torch.int32)      # outside [0, N)
+    off = [torch.full((n,), 0.5, dtype=torch.float64) for _ in range(3)]
+    u = [torch.zeros(n, dtype=torch.float64) for _ in range(3)]
+    sp = gp.copied_species(-1.0, 1.0, 1.0, cell, off, u)
+    with pytest.raises(gp.GalpicError) as e:
+        gp.Sim(cfg, [sp])
+    assert e.value.code == -1
+
+
+def test_config1_nci_fp64(gp):
+    """BASELINE config 1 (32x32x64, gamma = 130, linear shapes, FP64, 200 steps):
+    field energy stays at noise level with v_gal = v_drift and grows by more
+    than 1e3 with v_gal = 0; the first steps match the oracle at full size."""
+    ratios = {}
+    for gal in (True, False):
+        wl = gi.drifting_plasma(32, 32, 64, 130.0, galilean=gal, shape_order=1, precision=64, seed=1)
+        sim = gp.sim_from_workload(wl)
+        if gal:
+            cfg, st = oracle_state_from_sim(sim, wl)
+            for _ in range(3):
+                pic.step(cfg, st)
+            sim.step(3)
+            assert field_rel_l2(sim, st) < 1e-11
+        W = [sim.energy()]
+        for _ in range(20):
+            sim.step(10)
+            W.append(sim.energy())
+        ratios[gal] = np.array(W) / W[0]
+        sim.close()
+    assert ratios[True].max() <= 10.0
+    assert ratios[False][-1] >= 1e3
+
+
+def _plane_wave_spectra(wl, amp=1.0, m=(1, 2, 3)):
+    """Spectra of E0 cos(k.x), B = k_hat x E / c on the grid (host, numpy)."""
+    d = np.array([wl.dx, wl.dy, wl.dz])
+    shape = (wl.nx, wl.ny, wl.nz)
+    k = 2 * np.pi * np.array(m) / (np.array(shape) * d)
+    E0 = np.cross(k, [1.0, 0.0, 0.0])
+    E0 *= amp / np.linalg.norm(E0)
+    B0 = np.cross(k / np.linalg.norm(k), E0) / wl.c
+    x = np.stack(np.meshgrid(*[np.arange(n) * d[i] for i, n in enumerate(shape)], indexing="ij"))
+    ph = np.cos(np.tensordot(k, x, axes=1))
+    E = E0[:, None, None, None] * ph
+    B = B0[:, None, None, None] * ph
+    return np.fft.rfftn(E, axes=(1, 2, 3)), np.fft.rfftn(B, axes=(1, 2, 3))
+
+
+def _fixture(gp, name, galilean, precision, order):
+    """FP32 parity fixtures with O(1) fields.
+    F1: gamma = 130 neutral drifting plasma plus a unit-amplitude vacuum plane wave.
+    F2: electron-only gamma = 30 plasma with a 10 % sinusoidal density modulation along z
+        (particles displaced by (0.1/k) sin(k z)) over a neutralising background static on the grid."""
+    if name == "F1":
+        wl = gi.drifting_plasma(16, 16, 32, 130.0, galilean=galilean, shape_order=order, precision=precision,
+                                jitter=0.05)
+        sim = gp.sim_from_workload(wl)
+        Eh, Bh = _plane_wave_spectra(wl)
+        dt = sim.cplx
+        E = sim.get(gp.BUF_E_HAT, device="cpu").to(torch.complex128) + torch.from_numpy(Eh)
+        B = sim.get(gp.BUF_B_HAT, device="cpu").to(torch.complex128) + torch.from_numpy(Bh)
+        torch.cuda.synchronize()
+        sim.set(gp.BUF_E_HAT, E.to(dt))
+        sim.set(gp.BUF_B_HAT, B.to(dt))
+        return wl, sim
+    wl = gi.drifting_plasma(16, 16, 32, 30.0, galilean=galilean, shape_order=order, precision=precision,
+                            jitter=0.0, electron_only=True)
+    p = gi.lattice_particles(wl, 0)
+    kz = 2 * np.pi / (wl.nz * wl.dz)
+    z = (p.iz + p.fz) * wl.dz
+    z = np.mod(z + 0.1 / kz * np.sin(kz * z), wl.nz * wl.dz) / wl.dz
+    iz = np.floor(z).astype(np.int64)
+    fz = z - iz
+    cell = torch.from_numpy(((p.ix * wl.ny + p.iy) * wl.nz + iz).astype(np.int32))
+    rdt = torch.float64 if precision == 64 else torch.float32
+    off = [torch.from_numpy(a).to(rdt) for a in (p.fx, p.fy, fz)]
+    u = [torch.from_numpy(a).to(rdt) for a in (p.ux, p.uy, p.uz)]
+    cfg = gp.make_config(wl.nx, wl.ny, wl.nz, vgal=wl.vgal, rho_bg=wl.rho_bg, beta_init=wl.beta_init,
+                         shape_order=order, precision=precision, init_fields=1)
+    spec = wl.species[0]
+    sp = gp.copied_species(spec.q, spec.m, wl.weight(spec), cell, off, u)
+    return wl, gp.Sim(cfg, [sp])
+
+
+@pytest.mark.parametrize("fixture", ["F1", "F2"])
+@pytest.mark.parametrize("galilean", [True, False])
+def test_fp32_parity(gp, fixture, galilean):
+    """FP32 mode against the FP64 oracle from the same state: <= 1e-5 relative L2
+    per step, <= 1e-4 after 20 steps (E and c B, all six components)."""
+    wl, sim = _fixture(gp, fixture, galilean, 32, 3 if fixture == "F1" else 1)
+    sim.step(2)
+    sim.sort()
+    cfg, st = oracle_state_from_sim(sim, wl)
+    sim.step(1)
+    pic.step(cfg, st)
+    torch.cuda.synchronize()
+    e1 = field_rel_l2(sim, st)
+    assert e1 < 1e-5, e1
+    for _ in range(19):
+        pic.step(cfg, st)
+    sim.step(19)
+    torch.cuda.synchronize()
+    e20 = field_rel_l2(sim, st)
+    assert e20 < 1e-4, e20
+    sim.close()
