@@ -120,7 +120,9 @@ void make_layout(const pic_config& c, const Dims& d, const int64_t* n, int ns, s
     L.off_tmp[0] = take(nmax * 4);
     for (int q = 1; q <= 6; ++q) L.off_tmp[q] = take(nmax * T);
     L.off_tmp[7] = take(nmax * 4);
-    L.off_bin_cnt = take(d.nbins * 4);
+    L.off_key_cnt = take(sort_keys(d) * 4);
+    L.off_key_start = take(sort_keys(d) * 4);
+    L.off_tile_sum = take(sort_tiles(d) * 4);
     L.off_F = take(6 * d.N * T);
     L.off_S = take(4 * d.N * T);
     L.off_EBh = take(6 * d.M * 2 * T);
@@ -178,7 +180,7 @@ void count_launches(pic_sim* s, int64_t n) {
 int sort_kernel_count(const pic_sim* s) {
     int n = 1;
     for (int k = 0; k < s->nspecies; ++k)
-        if (s->sp[k].n > 0) n += 5;
+        if (s->sp[k].n > 0) n += 7;
     return n;
 }
 
@@ -356,7 +358,9 @@ int pic_init(const pic_config* cfg, const pic_species* species, int nspecies, vo
         s->tmp_u[dd] = w + L.off_tmp[4 + dd];
     }
     s->tmp_rank = (int32_t*)(w + L.off_tmp[7]);
-    s->bin_cnt = (int32_t*)(w + L.off_bin_cnt);
+    s->key_cnt = (int32_t*)(w + L.off_key_cnt);
+    s->key_start = (int32_t*)(w + L.off_key_start);
+    s->tile_sum = (int32_t*)(w + L.off_tile_sum);
     s->F = w + L.off_F;
     s->S = w + L.off_S;
     s->EBh = w + L.off_EBh;

@@ -108,7 +108,7 @@ struct Layout {
     size_t total;
     size_t off_species[PIC_MAX_SPECIES][8];   // cell, off x/y/z, u x/y/z, bin_start
     size_t off_tmp[8];                        // cell, off x/y/z, u x/y/z, rank
-    size_t off_bin_cnt;
+    size_t off_key_cnt, off_key_start, off_tile_sum;
     size_t off_F, off_S, off_EBh, off_EBs, off_Sh, off_Rn, off_Tab;
     size_t off_fftwork;
     size_t off_epart;
@@ -149,7 +149,9 @@ struct pic_sim {
     void* tmp_off[3];
     void* tmp_u[3];
     int32_t* tmp_rank;
-    int32_t* bin_cnt;
+    int32_t* key_cnt;     // sort: particles per cell key
+    int32_t* key_start;   // sort: first particle of each cell key
+    int32_t* tile_sum;    // sort: scan partial sums
     unsigned long long* cnt;
     int32_t* status;
     cufftHandle plan_r2c, plan_c2r;
@@ -185,5 +187,8 @@ enum { STAGE_SORT = 0, STAGE_PARTICLES = 1, STAGE_R2C = 2, STAGE_KSPACE = 3, STA
 
 // Shared-memory bytes of one particle-pass CTA.
 size_t tile_bytes(const pic_config& c, const Dims& d, int mode);
+// Number of cell keys of the sort (bins x cells per bin) and of scan tiles.
+int64_t sort_keys(const Dims& d);
+int64_t sort_tiles(const Dims& d);
 
 }  // namespace galpic

@@ -1,12 +1,21 @@
 // Particle-side kernels of the Galilean-PSATD step:
 //   * generate       - regular lattice plus seeded jitter (splitmix64 counters);
-//   * sort           - counting sort of each species into bins of BX*BY*BZ cells,
-//                      executed only when the device counters ask for it;
-//   * particle pass  - one CTA per bin: the bin's field tile (plus halo) is staged
-//                      in shared memory, each particle gathers E and B, takes the
+//   * sanitize       - clamp out-of-range loaded particles and flag them;
+//   * sort           - counting sort of each species by cell, cells numbered bin by
+//                      bin (bins of BX*BY*BZ cells), executed only when the device
+//                      counters ask for it. Particles of one cell are contiguous, and
+//                      the cells of a bin form one contiguous range;
+//   * particle pass  - one CTA per bin. The bin's E, B tile (plus stencil halo and a
+//                      margin) is staged in shared memory as component pairs; each
+//                      particle gathers E and B with packed FP32x2 FMAs, takes the
 //                      relativistic Boris push and the Galilean drift in two halves,
-//                      and deposits J^{n+1/2} and rho^{n+1} into a shared-memory
-//                      tile, which is added to the global grids once per CTA.
+//                      and deposits J^{n+1/2} and rho^{n+1}. The deposit is reduced
+//                      inside the warp first: lanes write their particle's separable
+//                      weights to a per-warp staging area, then, for every group of
+//                      lanes whose particles share a stencil, the lanes take the
+//                      roles of (node, component) slots, sum over the group's
+//                      particles in registers and add each slot to the shared tile
+//                      once. The tile is added to the global grids once per CTA.
 //                      Particles whose stencil leaves the tile (they moved far from
 //                      their bin since the last sort) use global memory directly.
 #include <math.h>
@@ -16,6 +25,9 @@
 namespace galpic {
 
 namespace {
+
+constexpr int PASS_THREADS = 256;
+constexpr int PASS_WARPS = PASS_THREADS / 32;
 
 __device__ __forceinline__ int wrapi(int i, int n) {
     i %= n;
@@ -64,6 +76,95 @@ template <> struct Shape<3> {
     }
 };
 
+// Packed pair FMA: d = a * b + c per component. FP32 uses the paired FP32 FMA of
+// sm_100-class GPUs (one instruction for two IEEE round-to-nearest FMAs).
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
+    unsigned long long ra = *reinterpret_cast<unsigned long long*>(&a);
+    unsigned long long rb = *reinterpret_cast<unsigned long long*>(&b);
+    unsigned long long rc = *reinterpret_cast<unsigned long long*>(&c);
+    unsigned long long rd;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
+    return *reinterpret_cast<float2*>(&rd);
+}
+__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+
+template <typename T> struct Pair;
+template <> struct Pair<float> {
+    typedef float2 type;
+    __device__ static float2 make(float a, float b) { return make_float2(a, b); }
+};
+template <> struct Pair<double> {
+    typedef double2 type;
+    __device__ static double2 make(double a, double b) { return make_double2(a, b); }
+};
+
+// E, B tile in shared memory as three component pairs per node:
+// P0 = (Ex, Ey), P1 = (Ez, Bx), P2 = (By, Bz).
+// float: one float4 (P0, P1) and one float2 (P2) per node; double: three double2.
+template <typename T> struct FieldTile;
+template <> struct FieldTile<float> {
+    float4* q;
+    float2* r;
+    __device__ void init(unsigned char* base, int R) {
+        q = reinterpret_cast<float4*>(base);
+        r = reinterpret_cast<float2*>(base + 16 * (size_t)R);
+    }
+    __device__ void store(int idx, const float* v) {
+        q[idx] = make_float4(v[0], v[1], v[2], v[3]);
+        r[idx] = make_float2(v[4], v[5]);
+    }
+    __device__ void load(int idx, float2& p0, float2& p1, float2& p2) const {
+        float4 a = q[idx];
+        p0 = make_float2(a.x, a.y);
+        p1 = make_float2(a.z, a.w);
+        p2 = r[idx];
+    }
+    static constexpr size_t bytes_per_node = 24;
+};
+template <> struct FieldTile<double> {
+    double2 *a, *b, *c;
+    __device__ void init(unsigned char* base, int R) {
+        a = reinterpret_cast<double2*>(base);
+        b = a + R;
+        c = b + R;
+    }
+    __device__ void store(int idx, const double* v) {
+        a[idx] = make_double2(v[0], v[1]);
+        b[idx] = make_double2(v[2], v[3]);
+        c[idx] = make_double2(v[4], v[5]);
+    }
+    __device__ void load(int idx, double2& p0, double2& p1, double2& p2) const {
+        p0 = a[idx];
+        p1 = b[idx];
+        p2 = c[idx];
+    }
+    static constexpr size_t bytes_per_node = 48;
+};
+
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) / 16 * 16; }
+
+// Staging record of one particle for the grouped deposit (T words):
+// [0..3] values (J: q w v / dV in 0..2; rho: q w / dV in 0), [4..7] x weights
+// ordered (w0, w2, w1, w3) for NW = 4 (so (w_h, w_{h+2}) is one pair) or
+// (w0, w1) for NW = 2, [8 ..] y-z weight products wy[b] wz[c] at 8 + b*NW + c.
+template <int NW> struct Rec {
+    static constexpr int WORDS = 8 + NW * NW;
+};
+
+// Shared-memory layout of one particle-pass CTA (bytes), shared with the host.
+struct PassSmem {
+    size_t tile, dep, stage, total;
+    __host__ __device__ PassSmem(int R, int NW, size_t T, bool step) {
+        size_t tb = step ? (T == 4 ? FieldTile<float>::bytes_per_node : FieldTile<double>::bytes_per_node) : 0;
+        tile = 0;
+        dep = align16(tb * (size_t)R);
+        stage = align16(dep + 4 * (size_t)R * T);
+        total = align16(stage + (size_t)PASS_WARPS * 32 * (8 + NW * NW) * T);
+    }
+};
+
 template <typename T>
 struct SpeciesK {
     int32_t* cell;
@@ -109,25 +210,132 @@ __device__ __forceinline__ void drift_axis(int& i, T& f, T d, int n) {
 // (tile node t holds global node o + t with o = bin origin + J0 - margin, so the
 // stencil start i + J0 sits at t = i - bin origin + margin, taken modulo the
 // periodic axis length n); -1 if the tile does not hold the whole stencil.
-template <int ORDER>
+template <int NW>
 __device__ __forceinline__ int tile_start(int rel, int n, int extent) {
     int r = wrapi(rel, n);
-    return (r + Shape<ORDER>::NW <= extent) ? r : -1;
+    return (r + NW <= extent) ? r : -1;
+}
+
+// Direct deposit of Q values at one particle's stencil into the global grids
+// (particles outside the tile).
+template <typename T, int NW, int J0>
+__device__ void deposit_global(const PassK<T>& p, int ix, int iy, int iz, const T* wx, const T* wy,
+                               const T* wz, int q0, int Q, const T* val) {
+#pragma unroll
+    for (int a = 0; a < NW; ++a)
+#pragma unroll
+        for (int b = 0; b < NW; ++b) {
+            T wxy = wx[a] * wy[b];
+            int64_t base = ((int64_t)wrapi(ix + J0 + a, p.nx) * p.ny + wrapi(iy + J0 + b, p.ny)) * p.nz;
+#pragma unroll
+            for (int c = 0; c < NW; ++c) {
+                T w = wxy * wz[c];
+                int64_t g = base + wrapi(iz + J0 + c, p.nz);
+                for (int q = 0; q < Q; ++q) atomicAdd(&p.S[(q0 + q) * p.N + g], w * val[q]);
+            }
+        }
+}
+
+// Grouped deposit of one warp. `member`: this lane staged a record and its stencil
+// starts at tile node `key` (tile linear index). Q = 3 (J at q0 = 0) or 1 (rho at q0 = 3).
+// Every lane of the warp must call this (warp-collective).
+template <typename T, int NW, int Q>
+__device__ void group_deposit(const PassK<T>& p, T* sD, const T* stage, bool member, int key, int lane) {
+    typedef typename Pair<T>::type P2;
+    constexpr int REC = Rec<NW>::WORDS;
+    constexpr int q0 = (Q == 3) ? 0 : 3;
+    const int R = p.R;
+    unsigned pending = __ballot_sync(0xffffffffu, member);
+    while (pending) {
+        const int leader = __ffs(pending) - 1;
+        const int gkey = __shfl_sync(0xffffffffu, key, leader);
+        const unsigned grp = __ballot_sync(0xffffffffu, member && key == gkey);
+        pending &= ~grp;
+        if (NW == 4) {
+            // lane -> y-z pair bc = lane & 15 and x nodes h, h + 2 (h = lane >> 4)
+            const int bc = lane & 15, h = lane >> 4;
+            P2 acc[Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) acc[q] = Pair<T>::make((T)0, (T)0);
+            unsigned g = grp;
+            while (g) {
+                const int m = __ffs(g) - 1;
+                g &= g - 1;
+                const T* r = stage + m * REC;
+                const P2 wx2 = *reinterpret_cast<const P2*>(r + 4 + 2 * h);
+                const T wyz = r[8 + bc];
+                const P2 w = Pair<T>::make(wx2.x * wyz, wx2.y * wyz);
+#pragma unroll
+                for (int q = 0; q < Q; ++q) acc[q] = pfma(w, Pair<T>::make(r[q], r[q]), acc[q]);
+            }
+            const int b = bc >> 2, c = bc & 3;
+            const int n0 = gkey + (h * p.RY + b) * p.RZ + c;
+            const int n1 = n0 + 2 * p.RY * p.RZ;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                atomicAdd(&sD[(q0 + q) * R + n0], acc[q].x);
+                atomicAdd(&sD[(q0 + q) * R + n1], acc[q].y);
+            }
+        } else {
+            // NW == 2: lane -> (component q = lane / 8, node j = lane % 8)
+            if (lane < 8 * Q) {
+                const int q = lane >> 3, j = lane & 7;
+                const int a = j >> 2, b = (j >> 1) & 1, c = j & 1;
+                T acc = (T)0;
+                unsigned g = grp;
+                while (g) {
+                    const int m = __ffs(g) - 1;
+                    g &= g - 1;
+                    const T* r = stage + m * REC;
+                    acc = fma(r[4 + a] * r[8 + b * 2 + c], r[q], acc);
+                }
+                atomicAdd(&sD[(q0 + q) * R + gkey + (a * p.RY + b) * p.RZ + c], acc);
+            }
+        }
+    }
+}
+
+// Stage one particle's separable weights and values (Q values) for group_deposit.
+template <typename T, int NW>
+__device__ __forceinline__ void stage_record(T* r, const T* wx, const T* wy, const T* wz, const T* val,
+                                             int Q) {
+    for (int q = 0; q < 4; ++q) r[q] = q < Q ? val[q] : (T)0;
+    if (NW == 4) {
+        r[4] = wx[0];
+        r[5] = wx[2];
+        r[6] = wx[1];
+        r[7] = wx[3];
+    } else {
+        r[4] = wx[0];
+        r[5] = wx[1];
+        r[6] = (T)0;
+        r[7] = (T)0;
+    }
+#pragma unroll
+    for (int b = 0; b < NW; ++b)
+#pragma unroll
+        for (int c = 0; c < NW; ++c) r[8 + b * NW + c] = wy[b] * wz[c];
 }
 
 template <typename T, int ORDER, int MODE>
-__global__ void __launch_bounds__(256) particle_pass_kernel(PassK<T> p) {
+__global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p) {
     typedef Shape<ORDER> SH;
+    typedef typename Pair<T>::type P2;
     constexpr int NW = SH::NW;
+    constexpr int REC = Rec<NW>::WORDS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sF = reinterpret_cast<T*>(smem_raw);              // 6 * R (STEP only)
-    T* sD = sF + (MODE == PASS_STEP ? 6 * p.R : 0);       // 4 * R
+    const PassSmem L(p.R, NW, sizeof(T), MODE == PASS_STEP);
+    FieldTile<T> tile;
+    tile.init(smem_raw + L.tile, p.R);
+    T* sD = reinterpret_cast<T*>(smem_raw + L.dep);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T* stage = reinterpret_cast<T*>(smem_raw + L.stage) + warp * 32 * REC;
+    T* myrec = stage + lane * REC;
 
     const int b = blockIdx.x;
     const int bz = b % p.nbz, by = (b / p.nbz) % p.nby, bx = b / (p.nbz * p.nby);
     const int x0 = bx * p.BX, y0 = by * p.BY, z0 = bz * p.BZ;
-    // tile origin (global node of tile index 0) and the stencil origin of a
-    // particle in the bin's first cell
+    // global node of tile index 0 along each axis
     const int ox = x0 + SH::J0 - p.margin, oy = y0 + SH::J0 - p.margin, oz = z0 + SH::J0 - p.margin;
     const int R = p.R;
     const int64_t N = p.N;
@@ -137,8 +345,10 @@ __global__ void __launch_bounds__(256) particle_pass_kernel(PassK<T> p) {
         if (MODE == PASS_STEP) {
             int64_t g = ((int64_t)wrapi(ox + rx, p.nx) * p.ny + wrapi(oy + ry, p.ny)) * p.nz +
                         wrapi(oz + rz, p.nz);
+            T v[6];
 #pragma unroll
-            for (int q = 0; q < 6; ++q) sF[q * R + idx] = p.F[q * N + g];
+            for (int q = 0; q < 6; ++q) v[q] = p.F[q * N + g];
+            tile.store(idx, v);
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) sD[q * R + idx] = (T)0;
@@ -149,146 +359,146 @@ __global__ void __launch_bounds__(256) particle_pass_kernel(PassK<T> p) {
     for (int s = 0; s < p.nspecies; ++s) {
         const SpeciesK<T> sp = p.sp[s];
         const int beg = sp.bin_start[b], end = sp.bin_start[b + 1];
-        for (int i = beg + threadIdx.x; i < end; i += blockDim.x) {
-            int c = sp.cell[i];
-            int ix = c / (p.ny * p.nz);
-            int rem = c - ix * (p.ny * p.nz);
-            int iy = rem / p.nz;
-            int iz = rem - iy * p.nz;
-            T fx = sp.off[0][i], fy = sp.off[1][i], fz = sp.off[2][i];
-            T ux = sp.u[0][i], uy = sp.u[1][i], uz = sp.u[2][i];
+        for (int base = beg; base < end; base += PASS_THREADS) {
+            const int i = base + threadIdx.x;
+            const bool valid = i < end;
+            int ix = 0, iy = 0, iz = 0;
+            T fx = 0, fy = 0, fz = 0, ux = 0, uy = 0, uz = 0;
             T wx[4], wy[4], wz[4];
-            T vx, vy, vz;
-            if (MODE == PASS_STEP) {
-                // ---- gather E^n, B^n at x^n
-                SH::w(fx, wx);
-                SH::w(fy, wy);
-                SH::w(fz, wz);
-                T E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
-                int rx = tile_start<ORDER>(ix - x0 + p.margin, p.nx, p.RX);
-                int ry = tile_start<ORDER>(iy - y0 + p.margin, p.ny, p.RY);
-                int rz = tile_start<ORDER>(iz - z0 + p.margin, p.nz, p.RZ);
-                if (rx >= 0 && ry >= 0 && rz >= 0) {
-#pragma unroll
-                    for (int a = 0; a < NW; ++a)
-#pragma unroll
-                        for (int bb = 0; bb < NW; ++bb) {
-                            T wxy = wx[a] * wy[bb];
-                            int base = ((rx + a) * p.RY + (ry + bb)) * p.RZ + rz;
-#pragma unroll
-                            for (int cc = 0; cc < NW; ++cc) {
-                                T w = wxy * wz[cc];
-                                int q0 = base + cc;
-                                E[0] += w * sF[0 * R + q0];
-                                E[1] += w * sF[1 * R + q0];
-                                E[2] += w * sF[2 * R + q0];
-                                B[0] += w * sF[3 * R + q0];
-                                B[1] += w * sF[4 * R + q0];
-                                B[2] += w * sF[5 * R + q0];
-                            }
-                        }
-                } else {
-                    far++;
-#pragma unroll
-                    for (int a = 0; a < NW; ++a)
-#pragma unroll
-                        for (int bb = 0; bb < NW; ++bb) {
-                            T wxy = wx[a] * wy[bb];
-                            int64_t base = ((int64_t)wrapi(ix + SH::J0 + a, p.nx) * p.ny +
-                                            wrapi(iy + SH::J0 + bb, p.ny)) * p.nz;
-#pragma unroll
-                            for (int cc = 0; cc < NW; ++cc) {
-                                T w = wxy * wz[cc];
-                                int64_t g = base + wrapi(iz + SH::J0 + cc, p.nz);
-                                E[0] += w * p.F[0 * N + g];
-                                E[1] += w * p.F[1 * N + g];
-                                E[2] += w * p.F[2 * N + g];
-                                B[0] += w * p.F[3 * N + g];
-                                B[1] += w * p.F[4 * N + g];
-                                B[2] += w * p.F[5 * N + g];
-                            }
-                        }
-                }
-                // ---- relativistic Boris push u^{n-1/2} -> u^{n+1/2}
-                const T a = sp.qdt2m;
-                T umx = ux + a * E[0], umy = uy + a * E[1], umz = uz + a * E[2];
-                T gm = sqrt((T)1 + (umx * umx + umy * umy + umz * umz) * p.inv_c2);
-                T tx = a * B[0] / gm, ty = a * B[1] / gm, tz = a * B[2] / gm;
-                T s2 = (T)2 / ((T)1 + tx * tx + ty * ty + tz * tz);
-                T sx = s2 * tx, sy = s2 * ty, sz = s2 * tz;
-                T upx = umx + (umy * tz - umz * ty);
-                T upy = umy + (umz * tx - umx * tz);
-                T upz = umz + (umx * ty - umy * tx);
-                ux = umx + (upy * sz - upz * sy) + a * E[0];
-                uy = umy + (upz * sx - upx * sz) + a * E[1];
-                uz = umz + (upx * sy - upy * sx) + a * E[2];
-            }
-            T gam = sqrt((T)1 + (ux * ux + uy * uy + uz * uz) * p.inv_c2);
-            vx = ux / gam;
-            vy = uy / gam;
-            vz = uz / gam;
-            // deposit passes: J (3 values) at x^{n+1/2} then rho at x^{n+1} (STEP),
-            // or J and rho at the current x (DEPOSIT)
-#pragma unroll
-            for (int phase = 0; phase < 2; ++phase) {
+            T vx = 0, vy = 0, vz = 0;
+            if (valid) {
+                const int c = sp.cell[i];
+                ix = c / (p.ny * p.nz);
+                const int rem = c - ix * (p.ny * p.nz);
+                iy = rem / p.nz;
+                iz = rem - iy * p.nz;
+                fx = sp.off[0][i];
+                fy = sp.off[1][i];
+                fz = sp.off[2][i];
+                ux = sp.u[0][i];
+                uy = sp.u[1][i];
+                uz = sp.u[2][i];
                 if (MODE == PASS_STEP) {
-                    drift_axis(ix, fx, (vx - p.vgal[0]) * p.hd[0], p.nx);
-                    drift_axis(iy, fy, (vy - p.vgal[1]) * p.hd[1], p.ny);
-                    drift_axis(iz, fz, (vz - p.vgal[2]) * p.hd[2], p.nz);
-                }
-                if (MODE == PASS_STEP || phase == 0) {
+                    // ---- gather E^n, B^n at x^n
                     SH::w(fx, wx);
                     SH::w(fy, wy);
                     SH::w(fz, wz);
-                }
-                // quantities deposited in this phase: Jx, Jy, Jz, then rho
-                const int q_lo = phase == 0 ? 0 : 3;
-                const int q_hi = phase == 0 ? 3 : 4;
-                T val[3];
-                if (phase == 0) {
-                    val[0] = sp.qw_dv * vx;
-                    val[1] = sp.qw_dv * vy;
-                    val[2] = sp.qw_dv * vz;
-                } else {
-                    val[0] = sp.qw_dv;
-                }
-                int rx = tile_start<ORDER>(ix - x0 + p.margin, p.nx, p.RX);
-                int ry = tile_start<ORDER>(iy - y0 + p.margin, p.ny, p.RY);
-                int rz = tile_start<ORDER>(iz - z0 + p.margin, p.nz, p.RZ);
-                if (rx >= 0 && ry >= 0 && rz >= 0) {
+                    T E[3], B[3];
+                    const int rx = tile_start<NW>(ix - x0 + p.margin, p.nx, p.RX);
+                    const int ry = tile_start<NW>(iy - y0 + p.margin, p.ny, p.RY);
+                    const int rz = tile_start<NW>(iz - z0 + p.margin, p.nz, p.RZ);
+                    if (rx >= 0 && ry >= 0 && rz >= 0) {
+                        P2 a0 = Pair<T>::make(0, 0), a1 = a0, a2 = a0;
 #pragma unroll
-                    for (int a = 0; a < NW; ++a)
+                        for (int a = 0; a < NW; ++a)
 #pragma unroll
-                        for (int bb = 0; bb < NW; ++bb) {
-                            T wxy = wx[a] * wy[bb];
-                            int base = ((rx + a) * p.RY + (ry + bb)) * p.RZ + rz;
+                            for (int bb = 0; bb < NW; ++bb) {
+                                const T wxy = wx[a] * wy[bb];
+                                const int base_t = ((rx + a) * p.RY + (ry + bb)) * p.RZ + rz;
 #pragma unroll
-                            for (int cc = 0; cc < NW; ++cc) {
-                                T w = wxy * wz[cc];
-                                for (int q = q_lo; q < q_hi; ++q)
-                                    atomicAdd(&sD[q * R + base + cc], w * val[q - q_lo]);
+                                for (int cc = 0; cc < NW; ++cc) {
+                                    const T w = wxy * wz[cc];
+                                    const P2 w2 = Pair<T>::make(w, w);
+                                    P2 f0, f1, f2;
+                                    tile.load(base_t + cc, f0, f1, f2);
+                                    a0 = pfma(w2, f0, a0);
+                                    a1 = pfma(w2, f1, a1);
+                                    a2 = pfma(w2, f2, a2);
+                                }
                             }
-                        }
-                } else {
-                    if (phase == 1) far++;
+                        E[0] = a0.x; E[1] = a0.y; E[2] = a1.x;
+                        B[0] = a1.y; B[1] = a2.x; B[2] = a2.y;
+                    } else {
+                        far++;
+                        for (int q = 0; q < 3; ++q) E[q] = B[q] = (T)0;
 #pragma unroll
-                    for (int a = 0; a < NW; ++a)
+                        for (int a = 0; a < NW; ++a)
 #pragma unroll
-                        for (int bb = 0; bb < NW; ++bb) {
-                            T wxy = wx[a] * wy[bb];
-                            int64_t base = ((int64_t)wrapi(ix + SH::J0 + a, p.nx) * p.ny +
-                                            wrapi(iy + SH::J0 + bb, p.ny)) * p.nz;
+                            for (int bb = 0; bb < NW; ++bb) {
+                                const T wxy = wx[a] * wy[bb];
+                                const int64_t gb = ((int64_t)wrapi(ix + SH::J0 + a, p.nx) * p.ny +
+                                                    wrapi(iy + SH::J0 + bb, p.ny)) * p.nz;
 #pragma unroll
-                            for (int cc = 0; cc < NW; ++cc) {
-                                T w = wxy * wz[cc];
-                                int64_t g = base + wrapi(iz + SH::J0 + cc, p.nz);
-                                for (int q = q_lo; q < q_hi; ++q)
-                                    atomicAdd(&p.S[q * N + g], w * val[q - q_lo]);
+                                for (int cc = 0; cc < NW; ++cc) {
+                                    const T w = wxy * wz[cc];
+                                    const int64_t g = gb + wrapi(iz + SH::J0 + cc, p.nz);
+                                    E[0] += w * p.F[0 * N + g];
+                                    E[1] += w * p.F[1 * N + g];
+                                    E[2] += w * p.F[2 * N + g];
+                                    B[0] += w * p.F[3 * N + g];
+                                    B[1] += w * p.F[4 * N + g];
+                                    B[2] += w * p.F[5 * N + g];
+                                }
                             }
-                        }
+                    }
+                    // ---- relativistic Boris push u^{n-1/2} -> u^{n+1/2}
+                    const T a = sp.qdt2m;
+                    const T umx = ux + a * E[0], umy = uy + a * E[1], umz = uz + a * E[2];
+                    const T gm = sqrt((T)1 + (umx * umx + umy * umy + umz * umz) * p.inv_c2);
+                    const T tx = a * B[0] / gm, ty = a * B[1] / gm, tz = a * B[2] / gm;
+                    const T s2 = (T)2 / ((T)1 + tx * tx + ty * ty + tz * tz);
+                    const T sx = s2 * tx, sy = s2 * ty, sz = s2 * tz;
+                    const T upx = umx + (umy * tz - umz * ty);
+                    const T upy = umy + (umz * tx - umx * tz);
+                    const T upz = umz + (umx * ty - umy * tx);
+                    ux = umx + (upy * sz - upz * sy) + a * E[0];
+                    uy = umy + (upz * sx - upx * sz) + a * E[1];
+                    uz = umz + (upx * sy - upy * sx) + a * E[2];
                 }
+                const T gam = sqrt((T)1 + (ux * ux + uy * uy + uz * uz) * p.inv_c2);
+                vx = ux / gam;
+                vy = uy / gam;
+                vz = uz / gam;
             }
-            if (MODE == PASS_STEP) {
+            // ---- deposit J (phase 0: at x^{n+1/2} with v^{n+1/2}) and rho (phase 1:
+            // at x^{n+1}); DEPOSIT mode: both at the current x
+#pragma unroll
+            for (int phase = 0; phase < 2; ++phase) {
+                bool member = false;
+                int key = 0;
+                if (valid) {
+                    if (MODE == PASS_STEP) {
+                        drift_axis(ix, fx, (vx - p.vgal[0]) * p.hd[0], p.nx);
+                        drift_axis(iy, fy, (vy - p.vgal[1]) * p.hd[1], p.ny);
+                        drift_axis(iz, fz, (vz - p.vgal[2]) * p.hd[2], p.nz);
+                    }
+                    if (MODE == PASS_STEP || phase == 0) {
+                        SH::w(fx, wx);
+                        SH::w(fy, wy);
+                        SH::w(fz, wz);
+                    }
+                    T val[3];
+                    if (phase == 0) {
+                        val[0] = sp.qw_dv * vx;
+                        val[1] = sp.qw_dv * vy;
+                        val[2] = sp.qw_dv * vz;
+                    } else {
+                        val[0] = sp.qw_dv;
+                        val[1] = val[2] = (T)0;
+                    }
+                    const int rx = tile_start<NW>(ix - x0 + p.margin, p.nx, p.RX);
+                    const int ry = tile_start<NW>(iy - y0 + p.margin, p.ny, p.RY);
+                    const int rz = tile_start<NW>(iz - z0 + p.margin, p.nz, p.RZ);
+                    if (rx >= 0 && ry >= 0 && rz >= 0) {
+                        member = true;
+                        key = (rx * p.RY + ry) * p.RZ + rz;
+                        stage_record<T, NW>(myrec, wx, wy, wz, val, phase == 0 ? 3 : 1);
+                    } else {
+                        if (phase == 1) far++;
+                        if (phase == 0)
+                            deposit_global<T, NW, SH::J0>(p, ix, iy, iz, wx, wy, wz, 0, 3, val);
+                        else
+                            deposit_global<T, NW, SH::J0>(p, ix, iy, iz, wx, wy, wz, 3, 1, val);
+                    }
+                }
+                __syncwarp();
+                if (phase == 0)
+                    group_deposit<T, NW, 3>(p, sD, stage, member, key, lane);
+                else
+                    group_deposit<T, NW, 1>(p, sD, stage, member, key, lane);
+                __syncwarp();
+            }
+            if (valid && MODE == PASS_STEP) {
                 sp.cell[i] = (ix * p.ny + iy) * p.nz + iz;
                 sp.off[0][i] = fx;
                 sp.off[1][i] = fy;
@@ -315,12 +525,11 @@ __global__ void __launch_bounds__(256) particle_pass_kernel(PassK<T> p) {
     }
 
     if (MODE == PASS_STEP) {
-        // warp-aggregated counters
         for (int o = 16; o > 0; o >>= 1) {
             miss += __shfl_down_sync(0xffffffffu, miss, o);
             far += __shfl_down_sync(0xffffffffu, far, o);
         }
-        if ((threadIdx.x & 31) == 0) {
+        if (lane == 0) {
             if (miss) atomicAdd(&p.cnt[CNT_HOME_MISS], miss);
             if (far) atomicAdd(&p.cnt[CNT_FAR], far);
         }
@@ -407,57 +616,126 @@ __global__ void sanitize_kernel(int32_t* cell, T* ox, T* oy, T* oz, int64_t n, i
 }
 
 // ---------------------------------------------------------------------------
-// Bin sort (runs only when sort_needed(cnt))
+// Cell sort (runs only when sort_needed(cnt)). Key of a cell: its bin times
+// BX*BY*BZ plus its index inside the bin, so every bin is one key range.
 // ---------------------------------------------------------------------------
 struct BinGeom {
     int ny, nz, BX, BY, BZ, nby, nbz;
-    __device__ __forceinline__ int bin_of(int c) const {
+    __device__ __forceinline__ int key_of(int c) const {
         int ix = c / (ny * nz);
         int rem = c - ix * (ny * nz);
         int iy = rem / nz;
         int iz = rem - iy * nz;
-        return ((ix / BX) * nby + iy / BY) * nbz + iz / BZ;
+        int b = ((ix / BX) * nby + iy / BY) * nbz + iz / BZ;
+        int l = ((ix % BX) * BY + iy % BY) * BZ + iz % BZ;
+        return b * (BX * BY * BZ) + l;
     }
 };
 
-__global__ void sort_zero_kernel(int32_t* bin_cnt, int nb, const unsigned long long* cnt) {
+constexpr int SCAN_THREADS = 1024, SCAN_ITEMS = 8, SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+__global__ void sort_zero_kernel(int32_t* key_cnt, int64_t K, const unsigned long long* cnt) {
     if (!sort_needed(cnt)) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x)
-        bin_cnt[i] = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < K;
+         i += (int64_t)gridDim.x * blockDim.x)
+        key_cnt[i] = 0;
 }
 
 __global__ void sort_count_kernel(const int32_t* __restrict__ cell, int64_t n, int32_t* rank,
-                                  int32_t* bin_cnt, BinGeom g, const unsigned long long* cnt) {
+                                  int32_t* key_cnt, BinGeom g, const unsigned long long* cnt) {
     if (!sort_needed(cnt)) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        rank[i] = atomicAdd(&bin_cnt[g.bin_of(cell[i])], 1);
+        rank[i] = atomicAdd(&key_cnt[g.key_of(cell[i])], 1);
 }
 
-// Exclusive scan of the bin counts into bin_start[0 .. nb]; one block of 1024.
-__global__ void __launch_bounds__(1024) sort_scan_kernel(const int32_t* bin_cnt, int32_t* bin_start,
-                                                         int nb, const unsigned long long* cnt) {
-    if (!sort_needed(cnt)) return;
-    __shared__ int32_t part[1024];
-    const int per = (nb + 1023) / 1024;
-    const int lo = threadIdx.x * per;
-    const int hi = min(nb, lo + per);
-    int32_t s = 0;
-    for (int i = lo; i < hi; ++i) s += bin_cnt[i];
-    part[threadIdx.x] = s;
+// Block-wide exclusive scan of one value per thread (1024 threads); returns the
+// thread's exclusive prefix and writes the block total to *total.
+__device__ int32_t block_exclusive_scan(int32_t v, int32_t* sh, int32_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
     __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        int32_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
+    if (warp == 0) {
+        int32_t w = sh[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        sh[lane] = w;
     }
-    int32_t run = part[threadIdx.x] - s;
+    __syncthreads();
+    int32_t before = (warp > 0 ? sh[warp - 1] : 0) + x - v;
+    if (total) *total = sh[31];
+    __syncthreads();
+    return before;
+}
+
+// pass A: per-tile sums of the key counts
+__global__ void __launch_bounds__(SCAN_THREADS) scan_tiles_kernel(const int32_t* key_cnt, int64_t K,
+                                                                  int32_t* tile_sum,
+                                                                  const unsigned long long* cnt) {
+    if (!sort_needed(cnt)) return;
+    __shared__ int32_t sh[32];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    int32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j)
+        if (base + j < K) s += key_cnt[base + j];
+    int32_t tot;
+    block_exclusive_scan(s, sh, &tot);
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = tot;
+}
+
+// pass B: exclusive scan of the tile sums (one block)
+__global__ void __launch_bounds__(SCAN_THREADS) scan_sums_kernel(int32_t* tile_sum, int nt,
+                                                                 const unsigned long long* cnt) {
+    if (!sort_needed(cnt)) return;
+    __shared__ int32_t sh[32];
+    const int per = (nt + SCAN_THREADS - 1) / SCAN_THREADS;
+    const int lo = threadIdx.x * per, hi = min(nt, lo + per);
+    int32_t s = 0;
+    for (int i = lo; i < hi; ++i) s += tile_sum[i];
+    int32_t run = block_exclusive_scan(s, sh, nullptr);
     for (int i = lo; i < hi; ++i) {
-        bin_start[i] = run;
-        run += bin_cnt[i];
+        int32_t v = tile_sum[i];
+        tile_sum[i] = run;
+        run += v;
     }
-    if (threadIdx.x == 1023) bin_start[nb] = part[1023];
+}
+
+// pass C: exclusive key starts; the start of every bin's first key goes to bin_start
+__global__ void __launch_bounds__(SCAN_THREADS) scan_write_kernel(const int32_t* key_cnt, int64_t K,
+                                                                  const int32_t* tile_sum,
+                                                                  int32_t* key_start,
+                                                                  int32_t* bin_start, int bxyz,
+                                                                  int nbins, int64_t n,
+                                                                  const unsigned long long* cnt) {
+    if (!sort_needed(cnt)) return;
+    __shared__ int32_t sh[32];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    int32_t v[SCAN_ITEMS];
+    int32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        v[j] = (base + j < K) ? key_cnt[base + j] : 0;
+        s += v[j];
+    }
+    int32_t run = block_exclusive_scan(s, sh, nullptr) + tile_sum[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+        const int64_t k = base + j;
+        if (k < K) {
+            key_start[k] = run;
+            if (k % bxyz == 0) bin_start[k / bxyz] = run;
+        }
+        run += v[j];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) bin_start[nbins] = (int32_t)n;
 }
 
 template <typename T>
@@ -468,13 +746,13 @@ struct Ptr6 {
 template <typename T>
 __global__ void sort_scatter_kernel(const int32_t* __restrict__ cell, Ptr6<T> src, int64_t n,
                                     const int32_t* __restrict__ rank,
-                                    const int32_t* __restrict__ bin_start, int32_t* tcell,
+                                    const int32_t* __restrict__ key_start, int32_t* tcell,
                                     Ptr6<T> dst, BinGeom g, const unsigned long long* cnt) {
     if (!sort_needed(cnt)) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         int c = cell[i];
-        int64_t j = (int64_t)bin_start[g.bin_of(c)] + rank[i];
+        int64_t j = (int64_t)key_start[g.key_of(c)] + rank[i];
         tcell[j] = c;
 #pragma unroll
         for (int q = 0; q < 6; ++q) dst.p[q][j] = src.p[q][i];
@@ -516,6 +794,9 @@ int grid_for(int64_t n, int block) {
 template <typename T>
 int sort_typed(pic_sim* s, cudaStream_t st) {
     BinGeom g{s->d.ny, s->d.nz, s->d.BX, s->d.BY, s->d.BZ, s->d.nby, s->d.nbz};
+    const int bxyz = s->d.BX * s->d.BY * s->d.BZ;
+    const int64_t K = (int64_t)s->d.nbins * bxyz;
+    const int nt = (int)((K + SCAN_TILE - 1) / SCAN_TILE);
     Ptr6<T> tmp;
     for (int d = 0; d < 3; ++d) {
         tmp.p[d] = (T*)s->tmp_off[d];
@@ -524,17 +805,20 @@ int sort_typed(pic_sim* s, cudaStream_t st) {
     for (int k = 0; k < s->nspecies; ++k) {
         SpeciesDev& sp = s->sp[k];
         if (sp.n == 0) continue;
-        sort_zero_kernel<<<grid_for(s->d.nbins, 256), 256, 0, st>>>(s->bin_cnt, s->d.nbins, s->cnt);
+        sort_zero_kernel<<<grid_for(K, 256), 256, 0, st>>>(s->key_cnt, K, s->cnt);
         sort_count_kernel<<<grid_for(sp.n, 256), 256, 0, st>>>(sp.cell, sp.n, s->tmp_rank,
-                                                               s->bin_cnt, g, s->cnt);
-        sort_scan_kernel<<<1, 1024, 0, st>>>(s->bin_cnt, sp.bin_start, s->d.nbins, s->cnt);
+                                                               s->key_cnt, g, s->cnt);
+        scan_tiles_kernel<<<nt, SCAN_THREADS, 0, st>>>(s->key_cnt, K, s->tile_sum, s->cnt);
+        scan_sums_kernel<<<1, SCAN_THREADS, 0, st>>>(s->tile_sum, nt, s->cnt);
+        scan_write_kernel<<<nt, SCAN_THREADS, 0, st>>>(s->key_cnt, K, s->tile_sum, s->key_start,
+                                                       sp.bin_start, bxyz, s->d.nbins, sp.n, s->cnt);
         Ptr6<T> own;
         for (int d = 0; d < 3; ++d) {
             own.p[d] = (T*)sp.off[d];
             own.p[3 + d] = (T*)sp.u[d];
         }
         sort_scatter_kernel<T><<<grid_for(sp.n, 256), 256, 0, st>>>(
-            sp.cell, own, sp.n, s->tmp_rank, sp.bin_start, s->tmp_cell, tmp, g, s->cnt);
+            sp.cell, own, sp.n, s->tmp_rank, s->key_start, s->tmp_cell, tmp, g, s->cnt);
         sort_copyback_kernel<T><<<grid_for(sp.n, 256), 256, 0, st>>>(sp.cell, own, sp.n,
                                                                      s->tmp_cell, tmp, s->cnt);
     }
@@ -584,10 +868,10 @@ int pass_launch(pic_sim* s, cudaStream_t st) {
         p.sp[k].qdt2m = (T)(sp.q * c.dt / (2.0 * sp.m));
     }
     p.cnt = s->cnt;
-    size_t smem = (size_t)(MODE == PASS_STEP ? 10 : 4) * p.R * sizeof(T);
+    const PassSmem L(p.R, Shape<ORDER>::NW, sizeof(T), MODE == PASS_STEP);
     auto kern = particle_pass_kernel<T, ORDER, MODE>;
-    GP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<s->d.nbins, 256, smem, st>>>(p);
+    GP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+    kern<<<s->d.nbins, PASS_THREADS, L.total, st>>>(p);
     GP_CUDA(cudaGetLastError());
     return PIC_OK;
 }
@@ -606,9 +890,13 @@ int pass_order(pic_sim* s, cudaStream_t st) {
 size_t tile_bytes(const pic_config& c, const Dims& d, int mode) {
     int nw = c.shape_order == 1 ? 2 : 4;
     int span = nw - 1 + 2 * d.margin;
-    size_t R = (size_t)(d.BX + span) * (d.BY + span) * (d.BZ + span);
-    return (mode == PASS_STEP ? 10 : 4) * R * (c.precision == 64 ? 8 : 4);
+    int R = (d.BX + span) * (d.BY + span) * (d.BZ + span);
+    return PassSmem(R, nw, c.precision == 64 ? 8 : 4, mode == PASS_STEP).total;
 }
+
+int64_t sort_keys(const Dims& d) { return (int64_t)d.nbins * d.BX * d.BY * d.BZ; }
+
+int64_t sort_tiles(const Dims& d) { return (sort_keys(d) + SCAN_TILE - 1) / SCAN_TILE; }
 
 int launch_particle_pass(pic_sim* s, int mode, cudaStream_t st) {
     if (s->cfg.precision == 64)
@@ -616,6 +904,10 @@ int launch_particle_pass(pic_sim* s, int mode, cudaStream_t st) {
                                  : pass_order<double, PASS_DEPOSIT>(s, st);
     return mode == PASS_STEP ? pass_order<float, PASS_STEP>(s, st)
                              : pass_order<float, PASS_DEPOSIT>(s, st);
+}
+
+int launch_sort(pic_sim* s, cudaStream_t st) {
+    return s->cfg.precision == 64 ? sort_typed<double>(s, st) : sort_typed<float>(s, st);
 }
 
 int launch_sanitize(pic_sim* s, int k, cudaStream_t st) {
@@ -630,10 +922,6 @@ int launch_sanitize(pic_sim* s, int k, cudaStream_t st) {
                                                      (float*)sp.off[2], sp.n, s->d.N, s->status);
     GP_CUDA(cudaGetLastError());
     return PIC_OK;
-}
-
-int launch_sort(pic_sim* s, cudaStream_t st) {
-    return s->cfg.precision == 64 ? sort_typed<double>(s, st) : sort_typed<float>(s, st);
 }
 
 int launch_generate(pic_sim* s, int k, const pic_species* spec, cudaStream_t st) {
