@@ -261,9 +261,36 @@ def run_ours(args, rank, world, local_rank):
                                                 "build, sort, initial fields, K steps each with a D2H "
                                                 "read of the field energy"},
     }
+    if args.serving_requests > 0 and world == 1:
+        line["serving"] = serving_bench(args.serving_requests, args.serving_steps)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
+
+
+def serving_bench(n_req, steps, chunk=25, seed=4):
+    """Continuous batching vs serial execution of independent runs on one GPU: a burst
+    (all requests at t = 0) and a Poisson trace at twice the serial service rate."""
+    import galpic_inputs as gi
+    from paper_1608_00215_gb300 import serve
+    wls = gi.serving_requests(n_req, seed=seed, steps=steps)
+    burst = [serve.Request(i, wl, steps, 0.0) for i, wl in enumerate(wls)]
+    out = {"requests": n_req, "steps_per_run": steps, "chunk_steps": chunk,
+           "trace": "grids {32^3, 64^3, 64x64x128, 128x128x256}, gamma {5,10,30,130}, v_gal {0, v_drift}, "
+                    "1-8 ppc/species, FP32, linear shapes, seed 4"}
+    serial = serve.serve(burst, max_slots=1, chunk=chunk)
+    batched = serve.serve(burst, max_slots=64, chunk=chunk)
+    out["burst"] = {"serial": serial.summary(), "batched": batched.summary()}
+    mean_service = serial.makespan / max(1, n_req)
+    arr = gi.poisson_arrivals(n_req, rate=2.0 / mean_service, seed=seed)
+    trace = [serve.Request(i, wl, steps, float(a)) for i, (wl, a) in enumerate(zip(wls, arr))]
+    serial_p = serve.serve(trace, max_slots=1, chunk=chunk)
+    batched_p = serve.serve(trace, max_slots=64, chunk=chunk)
+    out["poisson"] = {"rate_per_s": 2.0 / mean_service, "serial": serial_p.summary(),
+                      "batched": batched_p.summary()}
+    out["speedup_runs_per_s"] = {"burst": batched.runs_per_s / serial.runs_per_s,
+                                 "poisson": batched_p.runs_per_s / serial_p.runs_per_s}
+    return out
 
 
 def e2e_run(gp, wl, steps):
@@ -319,6 +346,9 @@ def main():
     ap.add_argument("--grid", default=",".join(str(x) for x in GRID),
                     help="nx,ny,nz of the drifting plasma (default: the 256x256x512 workload)")
     ap.add_argument("--order", type=int, default=3, help="shape order (default 3)")
+    ap.add_argument("--serving-requests", type=int, default=32,
+                    help="requests of the serving leg (0 skips it)")
+    ap.add_argument("--serving-steps", type=int, default=50, help="steps per serving request")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -34,6 +34,35 @@ __device__ __forceinline__ int wrapi(int i, int n) {
     return i < 0 ? i + n : i;
 }
 
+// Periodic wrap for an index that is at most one period outside [0, n) (the
+// common case); anything further goes through the modulo.
+__device__ __forceinline__ int wrap_near(int i, int n) {
+    if (i < 0)
+        i += n;
+    else if (i >= n)
+        i -= n;
+    return (i >= 0 && i < n) ? i : wrapi(i, n);
+}
+
+// Division of a non-negative int32 by a fixed divisor d >= 1 with one 64-bit
+// multiply and a shift: q = (x * M) >> s with s = 31 + ceil(log2 d) and
+// M = ceil(2^s / d) < 2^32. For x < 2^31 the rounding error of M adds less than
+// x/2^s < 2^-ceil(log2 d) <= 1/d to x/d, which never carries past the next integer.
+struct FastDiv {
+    uint32_t d, M;
+    int s;
+    __host__ void init(uint32_t dd) {
+        d = dd;
+        int L = 0;
+        while ((1ull << L) < dd) ++L;
+        s = 31 + L;
+        M = (uint32_t)(((1ull << s) + dd - 1) / dd);
+    }
+    __device__ __forceinline__ int div(int x) const {
+        return (int)(((unsigned long long)(unsigned)x * M) >> s);
+    }
+};
+
 // Shape factors of order 1, 2, 3 (B-splines) for a particle at cell i with offset
 // f in [0, 1): node i + J0 + a gets weight w[a], a = 0 .. NW-1.
 template <int ORDER> struct Shape;
@@ -88,6 +117,16 @@ __device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
 }
 __device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c) {
     return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) {
+    unsigned long long ra = *reinterpret_cast<unsigned long long*>(&a);
+    unsigned long long rb = *reinterpret_cast<unsigned long long*>(&b);
+    unsigned long long rd;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    return *reinterpret_cast<float2*>(&rd);
+}
+__device__ __forceinline__ double2 pmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x, a.y * b.y);
 }
 
 template <typename T> struct Pair;
@@ -145,13 +184,37 @@ template <> struct FieldTile<double> {
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) / 16 * 16; }
 
-// Staging record of one particle for the grouped deposit (T words):
-// [0..3] values (J: q w v / dV in 0..2; rho: q w / dV in 0), [4..7] x weights
-// ordered (w0, w2, w1, w3) for NW = 4 (so (w_h, w_{h+2}) is one pair) or
-// (w0, w1) for NW = 2, [8 ..] y-z weight products wy[b] wz[c] at 8 + b*NW + c.
-template <int NW> struct Rec {
-    static constexpr int WORDS = 8 + NW * NW;
+// Per-warp staging area of the grouped deposit. For every lane:
+//   * values v0..v3 (J: q w v / dV in v0..v2; rho: q w / dV in v0) and x weights
+//     (w0, w2, w1, w3) for NW = 4 -- so that (w_h, w_{h+2}) is one pair -- or
+//     (w0, w1, 0, 0) for NW = 2, as 16-byte quads stored quad-major ([quad][lane]):
+//     the lanes' vector stores are contiguous and a read of one lane's quad by the
+//     whole warp is a broadcast;
+//   * the NW*NW products wy[b] wz[c] (element b*NW + c), one row of QR 16-byte
+//     quads per lane, quad k of lane l stored in slot k ^ ((l / (8/QR)) % QR). The
+//     swizzle spreads the 8 lanes of each quarter-warp store over 8 distinct bank
+//     groups; a read of one lane's row by 16 lanes still touches one contiguous row.
+template <typename T, int NW> struct Stage {
+    static constexpr int EPQ = 16 / (int)sizeof(T);   // elements per quad
+    static constexpr int NQ = 8 / EPQ;                // quads holding v0..v3, x weights
+    static constexpr int QR = NW * NW / EPQ;          // quads per y-z row
+    static constexpr size_t QUAD_BYTES = (size_t)32 * NQ * 16;
+    static constexpr size_t BYTES = QUAD_BYTES + (size_t)32 * QR * 16;
+    unsigned char* base;
+    __device__ T* elem(int m, int e) const {   // element e (0..7) of lane m
+        return reinterpret_cast<T*>(base + ((e / EPQ) * 32 + m) * 16) + (e % EPQ);
+    }
+    __device__ static int swz(int m) { return (m / (8 / QR > 0 ? 8 / QR : 1)) % QR; }
+    __device__ T* row_quad(int m, int k) const {   // quad k of lane m's y-z row
+        return reinterpret_cast<T*>(base + QUAD_BYTES + (size_t)(m * QR + (k ^ swz(m))) * 16);
+    }
+    __device__ T row(int m, int e) const { return row_quad(m, e / EPQ)[e % EPQ]; }
 };
+
+__host__ __device__ constexpr size_t stage_bytes(int NW, size_t T) {
+    return T == 4 ? (NW == 4 ? Stage<float, 4>::BYTES : Stage<float, 2>::BYTES)
+                  : (NW == 4 ? Stage<double, 4>::BYTES : Stage<double, 2>::BYTES);
+}
 
 // Shared-memory layout of one particle-pass CTA (bytes), shared with the host.
 struct PassSmem {
@@ -161,7 +224,7 @@ struct PassSmem {
         tile = 0;
         dep = align16(tb * (size_t)R);
         stage = align16(dep + 4 * (size_t)R * T);
-        total = align16(stage + (size_t)PASS_WARPS * 32 * (8 + NW * NW) * T);
+        total = align16(stage + (size_t)PASS_WARPS * stage_bytes(NW, T));
     }
 };
 
@@ -181,6 +244,7 @@ struct PassK {
     T* S;           // real Jx, Jy, Jz, rho (4N)
     int64_t N;
     int nx, ny, nz;
+    FastDiv div_nynz, div_nz, div_ryz, div_rz;
     int BX, BY, BZ, nbx, nby, nbz;
     int RX, RY, RZ, R;   // shared tile extent (nodes)
     int margin;
@@ -203,7 +267,7 @@ __device__ __forceinline__ void drift_axis(int& i, T& f, T d, int n) {
         f -= (T)1;
         si += 1;
     }
-    i = wrapi(i + si, n);
+    i = wrap_near(i + si, n);
 }
 
 // Tile index of the first stencil node of a particle in cell i along one axis
@@ -212,7 +276,7 @@ __device__ __forceinline__ void drift_axis(int& i, T& f, T d, int n) {
 // periodic axis length n); -1 if the tile does not hold the whole stencil.
 template <int NW>
 __device__ __forceinline__ int tile_start(int rel, int n, int extent) {
-    int r = wrapi(rel, n);
+    int r = wrap_near(rel, n);
     return (r + NW <= extent) ? r : -1;
 }
 
@@ -240,9 +304,9 @@ __device__ void deposit_global(const PassK<T>& p, int ix, int iy, int iz, const 
 // starts at tile node `key` (tile linear index). Q = 3 (J at q0 = 0) or 1 (rho at q0 = 3).
 // Every lane of the warp must call this (warp-collective).
 template <typename T, int NW, int Q>
-__device__ void group_deposit(const PassK<T>& p, T* sD, const T* stage, bool member, int key, int lane) {
+__device__ void group_deposit(const PassK<T>& p, T* sD, const Stage<T, NW>& stg, bool member, int key,
+                              int lane) {
     typedef typename Pair<T>::type P2;
-    constexpr int REC = Rec<NW>::WORDS;
     constexpr int q0 = (Q == 3) ? 0 : 3;
     const int R = p.R;
     unsigned pending = __ballot_sync(0xffffffffu, member);
@@ -261,12 +325,19 @@ __device__ void group_deposit(const PassK<T>& p, T* sD, const T* stage, bool mem
             while (g) {
                 const int m = __ffs(g) - 1;
                 g &= g - 1;
-                const T* r = stage + m * REC;
-                const P2 wx2 = *reinterpret_cast<const P2*>(r + 4 + 2 * h);
-                const T wyz = r[8 + bc];
-                const P2 w = Pair<T>::make(wx2.x * wyz, wx2.y * wyz);
+                const P2 wx2 = *reinterpret_cast<const P2*>(stg.elem(m, 4 + 2 * h));
+                const T wyz = stg.row(m, bc);
+                const P2 w = pmul(wx2, Pair<T>::make(wyz, wyz));
+                T v[4];
+                if (sizeof(T) == 4) {
+                    const float4 vv = *reinterpret_cast<const float4*>(stg.elem(m, 0));
+                    v[0] = vv.x; v[1] = vv.y; v[2] = vv.z; v[3] = vv.w;
+                } else {
 #pragma unroll
-                for (int q = 0; q < Q; ++q) acc[q] = pfma(w, Pair<T>::make(r[q], r[q]), acc[q]);
+                    for (int q = 0; q < Q; ++q) v[q] = *stg.elem(m, q);
+                }
+#pragma unroll
+                for (int q = 0; q < Q; ++q) acc[q] = pfma(w, Pair<T>::make(v[q], v[q]), acc[q]);
             }
             const int b = bc >> 2, c = bc & 3;
             const int n0 = gkey + (h * p.RY + b) * p.RZ + c;
@@ -286,8 +357,7 @@ __device__ void group_deposit(const PassK<T>& p, T* sD, const T* stage, bool mem
                 while (g) {
                     const int m = __ffs(g) - 1;
                     g &= g - 1;
-                    const T* r = stage + m * REC;
-                    acc = fma(r[4 + a] * r[8 + b * 2 + c], r[q], acc);
+                    acc = fma(*stg.elem(m, 4 + a) * stg.row(m, b * 2 + c), *stg.elem(m, q), acc);
                 }
                 atomicAdd(&sD[(q0 + q) * R + gkey + (a * p.RY + b) * p.RZ + c], acc);
             }
@@ -295,26 +365,40 @@ __device__ void group_deposit(const PassK<T>& p, T* sD, const T* stage, bool mem
     }
 }
 
-// Stage one particle's separable weights and values (Q values) for group_deposit.
+// Stage this lane's separable weights and values (Q values) for group_deposit.
 template <typename T, int NW>
-__device__ __forceinline__ void stage_record(T* r, const T* wx, const T* wy, const T* wz, const T* val,
-                                             int Q) {
-    for (int q = 0; q < 4; ++q) r[q] = q < Q ? val[q] : (T)0;
+__device__ __forceinline__ void stage_record(const Stage<T, NW>& stg, int lane, const T* wx, const T* wy,
+                                             const T* wz, const T* val, int Q) {
+    T e[8];
+    for (int q = 0; q < 4; ++q) e[q] = q < Q ? val[q] : (T)0;
     if (NW == 4) {
-        r[4] = wx[0];
-        r[5] = wx[2];
-        r[6] = wx[1];
-        r[7] = wx[3];
+        e[4] = wx[0]; e[5] = wx[2]; e[6] = wx[1]; e[7] = wx[3];
     } else {
-        r[4] = wx[0];
-        r[5] = wx[1];
-        r[6] = (T)0;
-        r[7] = (T)0;
+        e[4] = wx[0]; e[5] = wx[1]; e[6] = (T)0; e[7] = (T)0;
     }
+    if (sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(stg.elem(lane, 0)) = make_float4(e[0], e[1], e[2], e[3]);
+        *reinterpret_cast<float4*>(stg.elem(lane, 4)) = make_float4(e[4], e[5], e[6], e[7]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            *reinterpret_cast<double2*>(stg.elem(lane, 2 * k)) = make_double2(e[2 * k], e[2 * k + 1]);
+    }
+    T w[NW * NW];
 #pragma unroll
     for (int b = 0; b < NW; ++b)
 #pragma unroll
-        for (int c = 0; c < NW; ++c) r[8 + b * NW + c] = wy[b] * wz[c];
+        for (int c = 0; c < NW; ++c) w[b * NW + c] = wy[b] * wz[c];
+    if (sizeof(T) == 4) {
+#pragma unroll
+        for (int k = 0; k < NW * NW / 4; ++k)
+            *reinterpret_cast<float4*>(stg.row_quad(lane, k)) =
+                make_float4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < NW * NW / 2; ++k)
+            *reinterpret_cast<double2*>(stg.row_quad(lane, k)) = make_double2(w[2 * k], w[2 * k + 1]);
+    }
 }
 
 template <typename T, int ORDER, int MODE>
@@ -322,15 +406,14 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
     typedef Shape<ORDER> SH;
     typedef typename Pair<T>::type P2;
     constexpr int NW = SH::NW;
-    constexpr int REC = Rec<NW>::WORDS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const PassSmem L(p.R, NW, sizeof(T), MODE == PASS_STEP);
     FieldTile<T> tile;
     tile.init(smem_raw + L.tile, p.R);
     T* sD = reinterpret_cast<T*>(smem_raw + L.dep);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    T* stage = reinterpret_cast<T*>(smem_raw + L.stage) + warp * 32 * REC;
-    T* myrec = stage + lane * REC;
+    Stage<T, NW> stg;
+    stg.base = smem_raw + L.stage + warp * Stage<T, NW>::BYTES;
 
     const int b = blockIdx.x;
     const int bz = b % p.nbz, by = (b / p.nbz) % p.nby, bx = b / (p.nbz * p.nby);
@@ -341,10 +424,13 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
     const int64_t N = p.N;
 
     for (int idx = threadIdx.x; idx < R; idx += blockDim.x) {
-        int rz = idx % p.RZ, ry = (idx / p.RZ) % p.RY, rx = idx / (p.RZ * p.RY);
+        const int rx = p.div_ryz.div(idx);
+        const int rem = idx - rx * (p.RY * p.RZ);
+        const int ry = p.div_rz.div(rem);
+        const int rz = rem - ry * p.RZ;
         if (MODE == PASS_STEP) {
-            int64_t g = ((int64_t)wrapi(ox + rx, p.nx) * p.ny + wrapi(oy + ry, p.ny)) * p.nz +
-                        wrapi(oz + rz, p.nz);
+            int64_t g = ((int64_t)wrap_near(ox + rx, p.nx) * p.ny + wrap_near(oy + ry, p.ny)) * p.nz +
+                        wrap_near(oz + rz, p.nz);
             T v[6];
 #pragma unroll
             for (int q = 0; q < 6; ++q) v[q] = p.F[q * N + g];
@@ -368,9 +454,9 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
             T vx = 0, vy = 0, vz = 0;
             if (valid) {
                 const int c = sp.cell[i];
-                ix = c / (p.ny * p.nz);
+                ix = p.div_nynz.div(c);
                 const int rem = c - ix * (p.ny * p.nz);
-                iy = rem / p.nz;
+                iy = p.div_nz.div(rem);
                 iz = rem - iy * p.nz;
                 fx = sp.off[0][i];
                 fy = sp.off[1][i];
@@ -388,26 +474,36 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
                     const int ry = tile_start<NW>(iy - y0 + p.margin, p.ny, p.RY);
                     const int rz = tile_start<NW>(iz - z0 + p.margin, p.nz, p.RZ);
                     if (rx >= 0 && ry >= 0 && rz >= 0) {
-                        P2 a0 = Pair<T>::make(0, 0), a1 = a0, a2 = a0;
+                        // two interleaved accumulator sets (even / odd z node) for ILP
+                        P2 a0 = Pair<T>::make(0, 0), a1 = a0, a2 = a0, c0 = a0, c1 = a0, c2 = a0;
+                        P2 wzp[NW];
+#pragma unroll
+                        for (int cc = 0; cc < NW; ++cc) wzp[cc] = Pair<T>::make(wz[cc], wz[cc]);
 #pragma unroll
                         for (int a = 0; a < NW; ++a)
 #pragma unroll
                             for (int bb = 0; bb < NW; ++bb) {
                                 const T wxy = wx[a] * wy[bb];
+                                const P2 wxyp = Pair<T>::make(wxy, wxy);
                                 const int base_t = ((rx + a) * p.RY + (ry + bb)) * p.RZ + rz;
 #pragma unroll
                                 for (int cc = 0; cc < NW; ++cc) {
-                                    const T w = wxy * wz[cc];
-                                    const P2 w2 = Pair<T>::make(w, w);
+                                    const P2 w2 = pmul(wxyp, wzp[cc]);
                                     P2 f0, f1, f2;
                                     tile.load(base_t + cc, f0, f1, f2);
-                                    a0 = pfma(w2, f0, a0);
-                                    a1 = pfma(w2, f1, a1);
-                                    a2 = pfma(w2, f2, a2);
+                                    if (cc & 1) {
+                                        c0 = pfma(w2, f0, c0);
+                                        c1 = pfma(w2, f1, c1);
+                                        c2 = pfma(w2, f2, c2);
+                                    } else {
+                                        a0 = pfma(w2, f0, a0);
+                                        a1 = pfma(w2, f1, a1);
+                                        a2 = pfma(w2, f2, a2);
+                                    }
                                 }
                             }
-                        E[0] = a0.x; E[1] = a0.y; E[2] = a1.x;
-                        B[0] = a1.y; B[1] = a2.x; B[2] = a2.y;
+                        E[0] = a0.x + c0.x; E[1] = a0.y + c0.y; E[2] = a1.x + c1.x;
+                        B[0] = a1.y + c1.y; B[1] = a2.x + c2.x; B[2] = a2.y + c2.y;
                     } else {
                         far++;
                         for (int q = 0; q < 3; ++q) E[q] = B[q] = (T)0;
@@ -482,7 +578,7 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
                     if (rx >= 0 && ry >= 0 && rz >= 0) {
                         member = true;
                         key = (rx * p.RY + ry) * p.RZ + rz;
-                        stage_record<T, NW>(myrec, wx, wy, wz, val, phase == 0 ? 3 : 1);
+                        stage_record<T, NW>(stg, lane, wx, wy, wz, val, phase == 0 ? 3 : 1);
                     } else {
                         if (phase == 1) far++;
                         if (phase == 0)
@@ -493,9 +589,9 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
                 }
                 __syncwarp();
                 if (phase == 0)
-                    group_deposit<T, NW, 3>(p, sD, stage, member, key, lane);
+                    group_deposit<T, NW, 3>(p, sD, stg, member, key, lane);
                 else
-                    group_deposit<T, NW, 1>(p, sD, stage, member, key, lane);
+                    group_deposit<T, NW, 1>(p, sD, stg, member, key, lane);
                 __syncwarp();
             }
             if (valid && MODE == PASS_STEP) {
@@ -506,7 +602,8 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
                 sp.u[0][i] = ux;
                 sp.u[1][i] = uy;
                 sp.u[2][i] = uz;
-                if (ix / p.BX != bx || iy / p.BY != by || iz / p.BZ != bz) miss++;
+                if (ix < x0 || ix >= x0 + p.BX || iy < y0 || iy >= y0 + p.BY || iz < z0 || iz >= z0 + p.BZ)
+                    miss++;
             }
         }
     }
@@ -514,9 +611,12 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
 
     // add the tile to the global source grids
     for (int idx = threadIdx.x; idx < R; idx += blockDim.x) {
-        int rz = idx % p.RZ, ry = (idx / p.RZ) % p.RY, rx = idx / (p.RZ * p.RY);
-        int64_t g = ((int64_t)wrapi(ox + rx, p.nx) * p.ny + wrapi(oy + ry, p.ny)) * p.nz +
-                    wrapi(oz + rz, p.nz);
+        const int rx = p.div_ryz.div(idx);
+        const int rem = idx - rx * (p.RY * p.RZ);
+        const int ry = p.div_rz.div(rem);
+        const int rz = rem - ry * p.RZ;
+        int64_t g = ((int64_t)wrap_near(ox + rx, p.nx) * p.ny + wrap_near(oy + ry, p.ny)) * p.nz +
+                    wrap_near(oz + rz, p.nz);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             T v = sD[q * R + idx];
@@ -849,6 +949,10 @@ int pass_launch(pic_sim* s, cudaStream_t st) {
     p.RY = s->d.BY + span;
     p.RZ = s->d.BZ + span;
     p.R = p.RX * p.RY * p.RZ;
+    p.div_nynz.init((uint32_t)(s->d.ny * s->d.nz));
+    p.div_nz.init((uint32_t)s->d.nz);
+    p.div_ryz.init((uint32_t)(p.RY * p.RZ));
+    p.div_rz.init((uint32_t)p.RZ);
     p.inv_c2 = (T)(1.0 / (c.c * c.c));
     p.hd[0] = (T)(0.5 * c.dt / c.dx);
     p.hd[1] = (T)(0.5 * c.dt / c.dy);

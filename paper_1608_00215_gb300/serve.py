@@ -1,0 +1,185 @@
+"""Continuous-batching service for many independent Galilean-PSATD runs on one GPU.
+
+Requests (independent drifting-plasma runs of different grid sizes, gamma and
+v_gal) arrive over time. A request is admitted as soon as a slot is free and its
+device footprint (``pic_footprint``: particles, grids, spectra, tables, FFT work
+area) fits in the remaining HBM budget; its fields and particles then stay
+resident until it finishes. Every admitted run owns a CUDA stream, so the
+kernels of different runs overlap on the device; the scheduler advances each
+run in chunks of graph-replayed steps (``pic_step``) and polls events to
+retire finished runs and admit new ones while others are still on the GPU.
+
+All compute goes through the CUDA library (``galpic``); this module is host
+scheduling only.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence
+
+import torch
+
+from . import galpic as gp
+
+
+@dataclass
+class Request:
+    rid: int
+    workload: object          # duck-typed synthetic workload (see galpic.sim_from_workload)
+    steps: int
+    arrival: float            # seconds after the start of the service
+
+
+@dataclass
+class RunRecord:
+    rid: int
+    arrival: float
+    start: float = math.nan
+    finish: float = math.nan
+    footprint: int = 0
+    energy: float = math.nan
+    status: int = 0
+    error: Optional[str] = None
+
+    @property
+    def latency(self) -> float:
+        return self.finish - self.arrival
+
+
+@dataclass
+class _Active:
+    req: Request
+    sim: gp.Sim
+    stream: torch.cuda.Stream
+    done: int = 0
+    event: Optional[torch.cuda.Event] = None
+    rec: RunRecord = None
+
+
+def footprint(wl, precision: Optional[int] = None) -> int:
+    """Device bytes a run of this workload needs (asks the library)."""
+    import ctypes
+    prec = wl.precision if precision is None else precision
+    cfg = gp.make_config(wl.nx, wl.ny, wl.nz, dx=wl.dx, dy=wl.dy, dz=wl.dz, dt=wl.dt, vgal=wl.vgal,
+                         c=wl.c, eps0=wl.eps0, rho_bg=wl.rho_bg, beta_init=wl.beta_init,
+                         shape_order=wl.shape_order, precision=prec,
+                         current_correction=wl.current_correction, init_fields=wl.init_fields)
+    ncells = wl.nx * wl.ny * wl.nz
+    sp = [gp.generated_species(s.q, s.m, 1.0, ncells, s.ppc, s.u0, s.jitter, wl.seed, k)
+          for k, s in enumerate(wl.species)]
+    arr = (gp.PicSpecies * max(1, len(sp)))(*sp)
+    n = ctypes.c_size_t(0)
+    gp.check(gp.lib.pic_footprint(ctypes.byref(cfg), arr, len(sp), ctypes.byref(n)))
+    return int(n.value)
+
+
+@dataclass
+class ServeResult:
+    records: List[RunRecord]
+    makespan: float
+    max_concurrent: int
+    chunk: int
+
+    def latencies(self) -> List[float]:
+        return sorted(r.latency for r in self.records if r.error is None)
+
+    def percentile(self, q: float) -> float:
+        """Nearest-rank percentile of the run latencies."""
+        lat = self.latencies()
+        if not lat:
+            return math.nan
+        k = max(1, math.ceil(q / 100.0 * len(lat)))
+        return lat[k - 1]
+
+    @property
+    def runs_per_s(self) -> float:
+        ok = sum(1 for r in self.records if r.error is None)
+        return ok / self.makespan if self.makespan > 0 else math.nan
+
+    def summary(self) -> dict:
+        return {"runs": len(self.records), "failed": sum(1 for r in self.records if r.error),
+                "makespan_s": self.makespan, "runs_per_s": self.runs_per_s,
+                "p50_latency_s": self.percentile(50), "p99_latency_s": self.percentile(99),
+                "max_concurrent": self.max_concurrent, "chunk_steps": self.chunk}
+
+
+def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_slots: int = 64,
+          chunk: int = 25, precision: Optional[int] = None, device: str = "cuda",
+          sleep: float = 2e-4, keep_final_state: bool = False, on_retire=None) -> ServeResult:
+    """Run all requests with continuous batching; returns per-run records.
+
+    ``max_slots = 1`` gives the serial baseline on the same arrival trace.
+    ``hbm_budget`` defaults to 90 % of the free device memory at the start.
+    """
+    if hbm_budget is None:
+        free, _ = torch.cuda.mem_get_info()
+        hbm_budget = int(0.9 * free)
+    queue = sorted(requests, key=lambda r: r.arrival)
+    fps, records = {}, {}
+    for r in queue:
+        records[r.rid] = RunRecord(r.rid, r.arrival)
+        try:
+            fps[r.rid] = footprint(r.workload, precision)
+        except gp.GalpicError as e:       # invalid request: rejected, the others go on
+            records[r.rid].error = str(e)
+            continue
+        records[r.rid].footprint = fps[r.rid]
+        if fps[r.rid] > hbm_budget:
+            records[r.rid].error = f"footprint {fps[r.rid]} exceeds the HBM budget {hbm_budget}"
+    queue = [r for r in queue if records[r.rid].error is None]
+    active: List[_Active] = []
+    used = 0
+    max_conc = 0
+    t0 = time.perf_counter()
+    qi = 0
+    while qi < len(queue) or active:
+        now = time.perf_counter() - t0
+        # retire or advance
+        for a in list(active):
+            if a.event is not None and not a.event.query():
+                continue
+            if a.done >= a.req.steps:
+                a.rec.finish = time.perf_counter() - t0
+                a.rec.status = a.sim.status()
+                if keep_final_state and on_retire is not None:
+                    on_retire(a.req, a.sim)
+                a.sim.close()
+                used -= a.rec.footprint
+                active.remove(a)
+                continue
+            n = min(chunk, a.req.steps - a.done)
+            with torch.cuda.stream(a.stream):
+                a.sim.step(n)
+                a.event = torch.cuda.Event()
+                a.event.record(a.stream)
+            a.done += n
+        # admit: arrived, slot free, footprint fits
+        while qi < len(queue) and len(active) < max_slots and queue[qi].arrival <= now:
+            r = queue[qi]
+            if used + fps[r.rid] > hbm_budget:
+                break
+            rec = records[r.rid]
+            stream = torch.cuda.Stream()
+            try:
+                with torch.cuda.stream(stream):
+                    sim = gp.sim_from_workload(r.workload, precision=precision, stream=stream, device=device)
+            except Exception as e:            # allocation or validation failure: reject this run only
+                rec.error = str(e)
+                qi += 1
+                continue
+            rec.start = time.perf_counter() - t0
+            used += fps[r.rid]
+            active.append(_Active(r, sim, stream, 0, None, rec))
+            max_conc = max(max_conc, len(active))
+            qi += 1
+        if active and all(a.event is not None and not a.event.query() for a in active):
+            time.sleep(sleep)
+        elif not active and qi < len(queue):
+            wait = queue[qi].arrival - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(min(wait, 0.01))
+    torch.cuda.synchronize()
+    makespan = time.perf_counter() - t0
+    return ServeResult([records[k] for k in sorted(records)], makespan, max_conc, chunk)
