@@ -223,6 +223,28 @@ int pic_profile_read(pic_sim* sim, double ms[8], int64_t count[8]);
 /* Grid sizes of a run: N = nx*ny*nz and M = nx*ny*(nz/2+1). */
 int pic_sizes(pic_sim* sim, int64_t* n_cells, int64_t* n_modes);
 
+/* Field energy W = (eps0/2) sum (|E|^2 + c^2 |B|^2) dV of caller-provided fields,
+ * computed without allocating any device memory. The paper has no counterpart;
+ * this is a convenience for callers that cannot call cudaMalloc: plain host code
+ * with no device allocator of its own, processes whose device memory is already
+ * reserved by another allocator's pool, and code paths that must not allocate or
+ * synchronise (allocation can block on other streams).
+ *   fields:    DEVICE pointer to 6*n_cells values, E then B, each component a
+ *              contiguous [n_cells] array (the layout of PIC_BUF_E followed by
+ *              PIC_BUF_B), float (precision 32) or double (precision 64).
+ *   n_cells:   1 .. 2^30; anything else returns PIC_EINVAL with a message.
+ *   out_dev:   DEVICE address of one double that receives W.
+ * The per-block partial sums live in one fixed array inside the library (16 KiB
+ * of partial sums plus a status word, present on every device that loads the
+ * library until the process exits). Every call shares that array: calls whose
+ * kernels overlap on the GPU (different streams, or different threads on one
+ * device) race and give wrong results; serialise them. The first call on a
+ * device looks up the array's device address (once per device, with that device
+ * current) and should come before any stream capture on that device. Non-finite
+ * field values make W non-finite. Asynchronous on `stream`. */
+int pic_field_energy_noalloc(const void* fields, int64_t n_cells, int precision, double eps0, double c,
+                             double dV, double* out_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -176,6 +176,9 @@ int launch_kspace_update(pic_sim* s, cudaStream_t st);
 int launch_init_fields(pic_sim* s, cudaStream_t st);
 int launch_master_to_scratch(pic_sim* s, cudaStream_t st);
 int launch_energy(pic_sim* s, double* out_dev, cudaStream_t st);
+// Energy kernels on caller-given fields (real [6][N]) and partial-sum storage.
+int launch_energy_on(const void* F, int64_t N, int precision, double* part, int nb, int32_t* status,
+                     double se_scale, double sb_scale, double* out_dev, cudaStream_t st);
 int launch_generate(pic_sim* s, int species, const pic_species* spec, cudaStream_t st);
 int launch_sort(pic_sim* s, cudaStream_t st);
 int launch_sanitize(pic_sim* s, int species, cudaStream_t st);

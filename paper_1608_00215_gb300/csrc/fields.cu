@@ -467,6 +467,18 @@ int launch_master_to_scratch(pic_sim* s, cudaStream_t st) {
     return PIC_OK;
 }
 
+int launch_energy_on(const void* F, int64_t N, int precision, double* part, int nb, int32_t* status,
+                     double se_scale, double sb_scale, double* out_dev, cudaStream_t st) {
+    if (precision == 64)
+        energy_partial_kernel<double><<<nb, 256, 0, st>>>((const double*)F, N, part, status);
+    else
+        energy_partial_kernel<float><<<nb, 256, 0, st>>>((const float*)F, N, part, status);
+    GP_CUDA(cudaGetLastError());
+    energy_final_kernel<<<1, 256, 0, st>>>(part, nb, se_scale, sb_scale, out_dev);
+    GP_CUDA(cudaGetLastError());
+    return PIC_OK;
+}
+
 int launch_energy(pic_sim* s, double* out_dev, cudaStream_t st) {
     const pic_config& c = s->cfg;
     double dV = c.dx * c.dy * c.dz;

@@ -75,6 +75,7 @@ def _load():
         "pic_profile": (c_int, [P, c_int]),
         "pic_profile_read": (c_int, [P, POINTER(c_double), POINTER(c_int64)]),
         "pic_sizes": (c_int, [P, POINTER(c_int64), POINTER(c_int64)]),
+        "pic_field_energy_noalloc": (c_int, [P, c_int64, c_int, c_double, c_double, c_double, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -89,7 +90,8 @@ lib = _load()
 EXPORTS = ("pic_version", "pic_last_error", "pic_footprint", "pic_init", "pic_destroy", "pic_deposit",
            "pic_gather_push", "pic_field_update", "pic_step", "pic_step_many", "pic_diag_energy",
            "pic_get", "pic_set", "pic_get_particles", "pic_set_particles", "pic_status",
-           "pic_counters", "pic_sizes", "pic_profile", "pic_profile_read", "pic_sort")
+           "pic_counters", "pic_sizes", "pic_profile", "pic_profile_read", "pic_sort",
+           "pic_field_energy_noalloc")
 
 STAGES = ("sort", "particles", "fft_r2c", "kspace", "fft_c2r", "energy")
 
@@ -268,6 +270,13 @@ class Sim:
             self.close()
         except Exception:
             pass
+
+
+def field_energy_noalloc(fields: torch.Tensor, n_cells: int, precision: int, eps0: float, c: float,
+                         dV: float, out: torch.Tensor, stream=None):
+    """pic_field_energy_noalloc: W of device fields [6][n_cells] into the device double `out`."""
+    check(lib.pic_field_energy_noalloc(c_void_p(fields.data_ptr()), n_cells, precision, eps0, c, dV,
+                                       c_void_p(out.data_ptr()), _stream_ptr(stream)))
 
 
 def step_many(sims: Sequence[Sim], nsteps: int, stream=None):
