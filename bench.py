@@ -183,7 +183,7 @@ def run_ours(args, rank, world, local_rank):
     grid = tuple(int(x) for x in args.grid.split(","))
     wl = workload(grid, order=args.order)
     P, N = wl.nparticles, wl.ncells
-    sim = gp.sim_from_workload(wl, precision=32)
+    sim = gp.sim_from_workload(wl, precision=32, tile_margin=args.margin)
     torch.cuda.synchronize()
     for _ in range(args.warmup):
         sim.gather_push()
@@ -242,7 +242,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": wl.name + " (gamma=130 e-p plasma, 2x2x2 ppc/species, cubic shapes, "
                                          "v_gal=v_drift, FP32 with FP64-built tables)",
                    "grid": list(grid), "particles": P, "cells": N, "shape_order": args.order, "precision": 32,
-                   "parallelism": f"replicas x{world}",
+                   "parallelism": f"replicas x{world}", "tile_margin": args.margin,
                    "l2": "inputs larger than L2 (15 GB of particles, 0.8 GB of fields); no flush"},
         "cell_updates_per_s": N * args.steps * world / (ms_max * 1e-3),
         "stages_ms_per_step": {k: v["ms"] / max(1, v["count"]) for k, v in stages.items() if v["count"]},
@@ -291,6 +291,77 @@ def serving_bench(n_req, steps, chunk=25, seed=4):
     out["speedup_runs_per_s"] = {"burst": batched.runs_per_s / serial.runs_per_s,
                                  "poisson": batched_p.runs_per_s / serial_p.runs_per_s}
     return out
+
+
+def continuity_residual(gp, sim, rho_old_hat, wl):
+    """max_k |rho^{n+1} - theta^2 rho^n + i dt E1(k.v dt) k.J| / max_k |rho^{n+1}| over the
+    modes of the last step's deposited (uncorrected) sources (k = 0 and Nyquist excluded)."""
+    import numpy as np
+    from oracle import pic
+    src = sim.get(gp.BUF_SRC_HAT, device="cpu").to(torch_c128()).numpy()
+    cfg = pic.Config(wl.nx, wl.ny, wl.nz, wl.dx, wl.dy, wl.dz, wl.dt, tuple(wl.vgal), wl.c, wl.eps0)
+    r = pic.continuity_residual(cfg, rho_old_hat, src[3], src[:3])
+    ok = ~pic.nyquist_mask(cfg)
+    ok[0, 0, 0] = False
+    return float(np.abs(r[ok]).max() / max(np.abs(src[3][ok]).max(), 1e-300))
+
+
+def torch_c128():
+    import torch
+    return torch.complex128
+
+
+def long_run(args):
+    """FP32 (int cell + FP32 offset) against FP64 on the GPU for the gamma = 130 Galilean
+    plasma: field-energy drift, continuity residual of the deposited sources and the
+    relative L2 difference of E, B, every `--long-run-every` steps; the FP64 oracle
+    beside both for the first `--long-run-oracle` steps at the oracle-sized grid."""
+    import numpy as np
+    import torch
+    from paper_1608_00215_gb300 import build
+    build.build()
+    from paper_1608_00215_gb300 import galpic as gp
+    from oracle import pic
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import helpers
+    import galpic_inputs as gi
+    grid = tuple(int(x) for x in args.grid.split(","))
+    wl = gi.drifting_plasma(*grid, GAMMA, galilean=True, shape_order=1, precision=64, seed=1)
+    s32 = gp.sim_from_workload(wl, precision=32)
+    s64 = gp.sim_from_workload(wl, precision=64)
+    out = {"mode": "long_run", "grid": list(grid), "particles": wl.nparticles, "steps": args.steps,
+           "every": args.long_run_every, "curve": []}
+    if args.long_run_oracle > 0:
+        cfg, st = helpers.oracle_state_from_sim(s64, wl)
+        ref = {}
+        for k in range(args.long_run_oracle):
+            pic.step(cfg, st)
+        ref["E"], ref["B"] = st.E, st.B
+    W0_32, W0_64 = s32.energy(), s64.energy()
+    t0 = time.perf_counter()
+    done = 0
+    while done < args.steps:
+        n = min(args.long_run_every, args.steps - done)
+        s32.step(n - 1)
+        s64.step(n - 1)
+        rho32 = s32.get(gp.BUF_RHO_HAT, device="cpu").to(torch.complex128).numpy()
+        s32.step(1)
+        s64.step(1)
+        done += n
+        E32, B32 = helpers.gpu_fields(s32)
+        E64, B64 = helpers.gpu_fields(s64)
+        d = float(np.linalg.norm(np.concatenate([(E32 - E64).ravel(), (B32 - B64).ravel()])) /
+                  max(np.linalg.norm(np.concatenate([E64.ravel(), B64.ravel()])), 1e-300))
+        row = {"step": done, "W32_over_W0": s32.energy() / W0_32, "W64_over_W0": s64.energy() / W0_64,
+               "relL2_E_B_fp32_vs_fp64": d, "continuity_residual_fp32": continuity_residual(gp, s32, rho32, wl)}
+        if args.long_run_oracle and done == args.long_run_oracle:
+            row["relL2_fp64_vs_oracle"] = float(np.linalg.norm(np.concatenate([(E64 - ref["E"]).ravel(), (B64 - ref["B"]).ravel()])) /
+                                                np.linalg.norm(np.concatenate([ref["E"].ravel(), ref["B"].ravel()])))
+            row["relL2_fp32_vs_oracle"] = float(np.linalg.norm(np.concatenate([(E32 - ref["E"]).ravel(), (B32 - ref["B"]).ravel()])) /
+                                                np.linalg.norm(np.concatenate([ref["E"].ravel(), ref["B"].ravel()])))
+        out["curve"].append(row)
+    out["seconds"] = time.perf_counter() - t0
+    print(json.dumps(out), flush=True)
 
 
 def e2e_run(gp, wl, steps):
@@ -346,15 +417,24 @@ def main():
     ap.add_argument("--grid", default=",".join(str(x) for x in GRID),
                     help="nx,ny,nz of the drifting plasma (default: the 256x256x512 workload)")
     ap.add_argument("--order", type=int, default=3, help="shape order (default 3)")
+    ap.add_argument("--margin", type=int, default=1, help="particle tile margin in cells (0 or 1)")
     ap.add_argument("--serving-requests", type=int, default=32,
                     help="requests of the serving leg (0 skips it)")
     ap.add_argument("--serving-steps", type=int, default=50, help="steps per serving request")
+    ap.add_argument("--long-run", action="store_true",
+                    help="FP32 vs FP64 long-run precision study instead of the throughput line")
+    ap.add_argument("--long-run-every", type=int, default=100)
+    ap.add_argument("--long-run-oracle", type=int, default=0,
+                    help="also run the FP64 oracle for this many steps (small grids only)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.long_run:
+        long_run(args)
         return
     if world > 1:
         import torch

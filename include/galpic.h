@@ -85,7 +85,11 @@ typedef struct {
                                    equation per mode on J before the update           */
     int32_t init_fields;        /* 0: E = B = 0; 1: field of rho^0 moving rigidly at
                                    beta_init*c (boosted Coulomb, satisfies Gauss)     */
-    int32_t reserved;
+    int32_t tile_margin;        /* 0 or 1: cells of shared-memory tile kept around each
+                                   8x8x8 bin for particles that left it since the last
+                                   sort (0: smaller tiles, any particle outside its bin
+                                   takes the global-memory path and triggers a re-sort;
+                                   1: particles up to one cell out still use the tile) */
 } pic_config;
 
 /* One particle species. Particles are either generated on the device on a

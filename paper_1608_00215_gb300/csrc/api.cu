@@ -41,6 +41,7 @@ int validate(const pic_config* c, const pic_species* sp, int ns) {
                 c->beta_init[2] * c->beta_init[2];
     if (c->init_fields == 1 && !(b2 < 1.0)) return fail(PIC_EINVAL, "|beta_init| must be below 1");
     if (c->init_fields != 0 && c->init_fields != 1) return fail(PIC_EINVAL, "init_fields must be 0 or 1");
+    if (c->tile_margin != 0 && c->tile_margin != 1) return fail(PIC_EINVAL, "tile_margin must be 0 or 1");
     if (ns < 0 || ns > PIC_MAX_SPECIES) return fail(PIC_EINVAL, "nspecies out of range");
     if (ns > 0 && !sp) return fail(PIC_EINVAL, "species array is NULL");
     int64_t ncell = (int64_t)c->nx * c->ny * c->nz;
@@ -68,14 +69,12 @@ Dims make_dims(const pic_config& c) {
     d.nzh = c.nz / 2 + 1;
     d.N = (int64_t)c.nx * c.ny * c.nz;
     d.M = (int64_t)c.nx * c.ny * d.nzh;
-    d.BX = std::min(8, c.nx);
-    d.BY = std::min(8, c.ny);
-    d.BZ = std::min(8, c.nz);
+    d.BX = d.BY = d.BZ = 8;
     d.nbx = (c.nx + d.BX - 1) / d.BX;
     d.nby = (c.ny + d.BY - 1) / d.BY;
     d.nbz = (c.nz + d.BZ - 1) / d.BZ;
     d.nbins = d.nbx * d.nby * d.nbz;
-    d.margin = 1;
+    d.margin = c.tile_margin;
     return d;
 }
 

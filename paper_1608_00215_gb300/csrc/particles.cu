@@ -228,6 +228,15 @@ struct PassSmem {
     }
 };
 
+// Bins are BIN^3 cells; the shared tile of a bin covers its cells' stencils plus
+// MARGIN cells on every side, so particles that moved up to MARGIN cells out of
+// their bin since the last sort still use the tile.
+constexpr int BIN = 8;
+template <int NW, int MARGIN> struct TileGeom {
+    static constexpr int E = BIN + NW - 1 + 2 * MARGIN;   // tile extent per axis (nodes)
+    static constexpr int R = E * E * E;
+};
+
 template <typename T>
 struct SpeciesK {
     int32_t* cell;
@@ -244,10 +253,8 @@ struct PassK {
     T* S;           // real Jx, Jy, Jz, rho (4N)
     int64_t N;
     int nx, ny, nz;
-    FastDiv div_nynz, div_nz, div_ryz, div_rz;
-    int BX, BY, BZ, nbx, nby, nbz;
-    int RX, RY, RZ, R;   // shared tile extent (nodes)
-    int margin;
+    FastDiv div_nynz, div_nz;
+    int nbx, nby, nbz;
     T inv_c2;
     T hd[3];             // dt / (2 d) per axis
     T vgal[3];
@@ -303,12 +310,11 @@ __device__ void deposit_global(const PassK<T>& p, int ix, int iy, int iz, const 
 // Grouped deposit of one warp. `member`: this lane staged a record and its stencil
 // starts at tile node `key` (tile linear index). Q = 3 (J at q0 = 0) or 1 (rho at q0 = 3).
 // Every lane of the warp must call this (warp-collective).
-template <typename T, int NW, int Q>
-__device__ void group_deposit(const PassK<T>& p, T* sD, const Stage<T, NW>& stg, bool member, int key,
-                              int lane) {
+template <typename T, int NW, int Q, int TE>
+__device__ void group_deposit(T* sD, const Stage<T, NW>& stg, bool member, int key, int lane) {
     typedef typename Pair<T>::type P2;
     constexpr int q0 = (Q == 3) ? 0 : 3;
-    const int R = p.R;
+    constexpr int R = TE * TE * TE;
     unsigned pending = __ballot_sync(0xffffffffu, member);
     while (pending) {
         const int leader = __ffs(pending) - 1;
@@ -340,8 +346,8 @@ __device__ void group_deposit(const PassK<T>& p, T* sD, const Stage<T, NW>& stg,
                 for (int q = 0; q < Q; ++q) acc[q] = pfma(w, Pair<T>::make(v[q], v[q]), acc[q]);
             }
             const int b = bc >> 2, c = bc & 3;
-            const int n0 = gkey + (h * p.RY + b) * p.RZ + c;
-            const int n1 = n0 + 2 * p.RY * p.RZ;
+            const int n0 = gkey + (h * TE + b) * TE + c;
+            const int n1 = n0 + 2 * TE * TE;
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
                 atomicAdd(&sD[(q0 + q) * R + n0], acc[q].x);
@@ -359,7 +365,7 @@ __device__ void group_deposit(const PassK<T>& p, T* sD, const Stage<T, NW>& stg,
                     g &= g - 1;
                     acc = fma(*stg.elem(m, 4 + a) * stg.row(m, b * 2 + c), *stg.elem(m, q), acc);
                 }
-                atomicAdd(&sD[(q0 + q) * R + gkey + (a * p.RY + b) * p.RZ + c], acc);
+                atomicAdd(&sD[(q0 + q) * R + gkey + (a * TE + b) * TE + c], acc);
             }
         }
     }
@@ -401,15 +407,17 @@ __device__ __forceinline__ void stage_record(const Stage<T, NW>& stg, int lane, 
     }
 }
 
-template <typename T, int ORDER, int MODE>
+template <typename T, int ORDER, int MODE, int MARGIN>
 __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p) {
     typedef Shape<ORDER> SH;
     typedef typename Pair<T>::type P2;
     constexpr int NW = SH::NW;
+    constexpr int TE = TileGeom<NW, MARGIN>::E;
+    constexpr int R = TileGeom<NW, MARGIN>::R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const PassSmem L(p.R, NW, sizeof(T), MODE == PASS_STEP);
+    const PassSmem L(R, NW, sizeof(T), MODE == PASS_STEP);
     FieldTile<T> tile;
-    tile.init(smem_raw + L.tile, p.R);
+    tile.init(smem_raw + L.tile, R);
     T* sD = reinterpret_cast<T*>(smem_raw + L.dep);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     Stage<T, NW> stg;
@@ -417,17 +425,16 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
 
     const int b = blockIdx.x;
     const int bz = b % p.nbz, by = (b / p.nbz) % p.nby, bx = b / (p.nbz * p.nby);
-    const int x0 = bx * p.BX, y0 = by * p.BY, z0 = bz * p.BZ;
+    const int x0 = bx * BIN, y0 = by * BIN, z0 = bz * BIN;
     // global node of tile index 0 along each axis
-    const int ox = x0 + SH::J0 - p.margin, oy = y0 + SH::J0 - p.margin, oz = z0 + SH::J0 - p.margin;
-    const int R = p.R;
+    const int ox = x0 + SH::J0 - MARGIN, oy = y0 + SH::J0 - MARGIN, oz = z0 + SH::J0 - MARGIN;
     const int64_t N = p.N;
 
     for (int idx = threadIdx.x; idx < R; idx += blockDim.x) {
-        const int rx = p.div_ryz.div(idx);
-        const int rem = idx - rx * (p.RY * p.RZ);
-        const int ry = p.div_rz.div(rem);
-        const int rz = rem - ry * p.RZ;
+        const int rx = idx / (TE * TE);
+        const int rem = idx - rx * (TE * TE);
+        const int ry = rem / TE;
+        const int rz = rem - ry * TE;
         if (MODE == PASS_STEP) {
             int64_t g = ((int64_t)wrap_near(ox + rx, p.nx) * p.ny + wrap_near(oy + ry, p.ny)) * p.nz +
                         wrap_near(oz + rz, p.nz);
@@ -470,9 +477,9 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
                     SH::w(fy, wy);
                     SH::w(fz, wz);
                     T E[3], B[3];
-                    const int rx = tile_start<NW>(ix - x0 + p.margin, p.nx, p.RX);
-                    const int ry = tile_start<NW>(iy - y0 + p.margin, p.ny, p.RY);
-                    const int rz = tile_start<NW>(iz - z0 + p.margin, p.nz, p.RZ);
+                    const int rx = tile_start<NW>(ix - x0 + MARGIN, p.nx, TE);
+                    const int ry = tile_start<NW>(iy - y0 + MARGIN, p.ny, TE);
+                    const int rz = tile_start<NW>(iz - z0 + MARGIN, p.nz, TE);
                     if (rx >= 0 && ry >= 0 && rz >= 0) {
                         // two interleaved accumulator sets (even / odd z node) for ILP
                         P2 a0 = Pair<T>::make(0, 0), a1 = a0, a2 = a0, c0 = a0, c1 = a0, c2 = a0;
@@ -485,7 +492,7 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
                             for (int bb = 0; bb < NW; ++bb) {
                                 const T wxy = wx[a] * wy[bb];
                                 const P2 wxyp = Pair<T>::make(wxy, wxy);
-                                const int base_t = ((rx + a) * p.RY + (ry + bb)) * p.RZ + rz;
+                                const int base_t = ((rx + a) * TE + (ry + bb)) * TE + rz;
 #pragma unroll
                                 for (int cc = 0; cc < NW; ++cc) {
                                     const P2 w2 = pmul(wxyp, wzp[cc]);
@@ -530,8 +537,8 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
                     // ---- relativistic Boris push u^{n-1/2} -> u^{n+1/2}
                     const T a = sp.qdt2m;
                     const T umx = ux + a * E[0], umy = uy + a * E[1], umz = uz + a * E[2];
-                    const T gm = sqrt((T)1 + (umx * umx + umy * umy + umz * umz) * p.inv_c2);
-                    const T tx = a * B[0] / gm, ty = a * B[1] / gm, tz = a * B[2] / gm;
+                    const T igm = (T)1 / sqrt((T)1 + (umx * umx + umy * umy + umz * umz) * p.inv_c2);
+                    const T tx = a * B[0] * igm, ty = a * B[1] * igm, tz = a * B[2] * igm;
                     const T s2 = (T)2 / ((T)1 + tx * tx + ty * ty + tz * tz);
                     const T sx = s2 * tx, sy = s2 * ty, sz = s2 * tz;
                     const T upx = umx + (umy * tz - umz * ty);
@@ -541,10 +548,10 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
                     uy = umy + (upz * sx - upx * sz) + a * E[1];
                     uz = umz + (upx * sy - upy * sx) + a * E[2];
                 }
-                const T gam = sqrt((T)1 + (ux * ux + uy * uy + uz * uz) * p.inv_c2);
-                vx = ux / gam;
-                vy = uy / gam;
-                vz = uz / gam;
+                const T igam = (T)1 / sqrt((T)1 + (ux * ux + uy * uy + uz * uz) * p.inv_c2);
+                vx = ux * igam;
+                vy = uy * igam;
+                vz = uz * igam;
             }
             // ---- deposit J (phase 0: at x^{n+1/2} with v^{n+1/2}) and rho (phase 1:
             // at x^{n+1}); DEPOSIT mode: both at the current x
@@ -572,12 +579,12 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
                         val[0] = sp.qw_dv;
                         val[1] = val[2] = (T)0;
                     }
-                    const int rx = tile_start<NW>(ix - x0 + p.margin, p.nx, p.RX);
-                    const int ry = tile_start<NW>(iy - y0 + p.margin, p.ny, p.RY);
-                    const int rz = tile_start<NW>(iz - z0 + p.margin, p.nz, p.RZ);
+                    const int rx = tile_start<NW>(ix - x0 + MARGIN, p.nx, TE);
+                    const int ry = tile_start<NW>(iy - y0 + MARGIN, p.ny, TE);
+                    const int rz = tile_start<NW>(iz - z0 + MARGIN, p.nz, TE);
                     if (rx >= 0 && ry >= 0 && rz >= 0) {
                         member = true;
-                        key = (rx * p.RY + ry) * p.RZ + rz;
+                        key = (rx * TE + ry) * TE + rz;
                         stage_record<T, NW>(stg, lane, wx, wy, wz, val, phase == 0 ? 3 : 1);
                     } else {
                         if (phase == 1) far++;
@@ -589,9 +596,9 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
                 }
                 __syncwarp();
                 if (phase == 0)
-                    group_deposit<T, NW, 3>(p, sD, stg, member, key, lane);
+                    group_deposit<T, NW, 3, TE>(sD, stg, member, key, lane);
                 else
-                    group_deposit<T, NW, 1>(p, sD, stg, member, key, lane);
+                    group_deposit<T, NW, 1, TE>(sD, stg, member, key, lane);
                 __syncwarp();
             }
             if (valid && MODE == PASS_STEP) {
@@ -602,7 +609,7 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
                 sp.u[0][i] = ux;
                 sp.u[1][i] = uy;
                 sp.u[2][i] = uz;
-                if (ix < x0 || ix >= x0 + p.BX || iy < y0 || iy >= y0 + p.BY || iz < z0 || iz >= z0 + p.BZ)
+                if (ix < x0 || ix >= x0 + BIN || iy < y0 || iy >= y0 + BIN || iz < z0 || iz >= z0 + BIN)
                     miss++;
             }
         }
@@ -611,10 +618,10 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
 
     // add the tile to the global source grids
     for (int idx = threadIdx.x; idx < R; idx += blockDim.x) {
-        const int rx = p.div_ryz.div(idx);
-        const int rem = idx - rx * (p.RY * p.RZ);
-        const int ry = p.div_rz.div(rem);
-        const int rz = rem - ry * p.RZ;
+        const int rx = idx / (TE * TE);
+        const int rem = idx - rx * (TE * TE);
+        const int ry = rem / TE;
+        const int rz = rem - ry * TE;
         int64_t g = ((int64_t)wrap_near(ox + rx, p.nx) * p.ny + wrap_near(oy + ry, p.ny)) * p.nz +
                     wrap_near(oz + rz, p.nz);
 #pragma unroll
@@ -927,7 +934,7 @@ int sort_typed(pic_sim* s, cudaStream_t st) {
     return PIC_OK;
 }
 
-template <typename T, int ORDER, int MODE>
+template <typename T, int ORDER, int MODE, int MARGIN>
 int pass_launch(pic_sim* s, cudaStream_t st) {
     const pic_config& c = s->cfg;
     PassK<T> p;
@@ -937,22 +944,11 @@ int pass_launch(pic_sim* s, cudaStream_t st) {
     p.nx = s->d.nx;
     p.ny = s->d.ny;
     p.nz = s->d.nz;
-    p.BX = s->d.BX;
-    p.BY = s->d.BY;
-    p.BZ = s->d.BZ;
     p.nbx = s->d.nbx;
     p.nby = s->d.nby;
     p.nbz = s->d.nbz;
-    p.margin = s->d.margin;
-    const int span = Shape<ORDER>::NW - 1 + 2 * s->d.margin;
-    p.RX = s->d.BX + span;
-    p.RY = s->d.BY + span;
-    p.RZ = s->d.BZ + span;
-    p.R = p.RX * p.RY * p.RZ;
     p.div_nynz.init((uint32_t)(s->d.ny * s->d.nz));
     p.div_nz.init((uint32_t)s->d.nz);
-    p.div_ryz.init((uint32_t)(p.RY * p.RZ));
-    p.div_rz.init((uint32_t)p.RZ);
     p.inv_c2 = (T)(1.0 / (c.c * c.c));
     p.hd[0] = (T)(0.5 * c.dt / c.dx);
     p.hd[1] = (T)(0.5 * c.dt / c.dy);
@@ -972,30 +968,34 @@ int pass_launch(pic_sim* s, cudaStream_t st) {
         p.sp[k].qdt2m = (T)(sp.q * c.dt / (2.0 * sp.m));
     }
     p.cnt = s->cnt;
-    const PassSmem L(p.R, Shape<ORDER>::NW, sizeof(T), MODE == PASS_STEP);
-    auto kern = particle_pass_kernel<T, ORDER, MODE>;
+    const PassSmem L(TileGeom<Shape<ORDER>::NW, MARGIN>::R, Shape<ORDER>::NW, sizeof(T), MODE == PASS_STEP);
+    auto kern = particle_pass_kernel<T, ORDER, MODE, MARGIN>;
     GP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
     kern<<<s->d.nbins, PASS_THREADS, L.total, st>>>(p);
     GP_CUDA(cudaGetLastError());
     return PIC_OK;
 }
 
-template <typename T, int MODE>
+template <typename T, int MODE, int MARGIN>
 int pass_order(pic_sim* s, cudaStream_t st) {
     switch (s->cfg.shape_order) {
-        case 1: return pass_launch<T, 1, MODE>(s, st);
-        case 2: return pass_launch<T, 2, MODE>(s, st);
-        default: return pass_launch<T, 3, MODE>(s, st);
+        case 1: return pass_launch<T, 1, MODE, MARGIN>(s, st);
+        case 2: return pass_launch<T, 2, MODE, MARGIN>(s, st);
+        default: return pass_launch<T, 3, MODE, MARGIN>(s, st);
     }
+}
+
+template <typename T, int MODE>
+int pass_margin(pic_sim* s, cudaStream_t st) {
+    return s->d.margin == 0 ? pass_order<T, MODE, 0>(s, st) : pass_order<T, MODE, 1>(s, st);
 }
 
 }  // namespace
 
 size_t tile_bytes(const pic_config& c, const Dims& d, int mode) {
     int nw = c.shape_order == 1 ? 2 : 4;
-    int span = nw - 1 + 2 * d.margin;
-    int R = (d.BX + span) * (d.BY + span) * (d.BZ + span);
-    return PassSmem(R, nw, c.precision == 64 ? 8 : 4, mode == PASS_STEP).total;
+    int e = BIN + nw - 1 + 2 * d.margin;
+    return PassSmem(e * e * e, nw, c.precision == 64 ? 8 : 4, mode == PASS_STEP).total;
 }
 
 int64_t sort_keys(const Dims& d) { return (int64_t)d.nbins * d.BX * d.BY * d.BZ; }
@@ -1004,10 +1004,10 @@ int64_t sort_tiles(const Dims& d) { return (sort_keys(d) + SCAN_TILE - 1) / SCAN
 
 int launch_particle_pass(pic_sim* s, int mode, cudaStream_t st) {
     if (s->cfg.precision == 64)
-        return mode == PASS_STEP ? pass_order<double, PASS_STEP>(s, st)
-                                 : pass_order<double, PASS_DEPOSIT>(s, st);
-    return mode == PASS_STEP ? pass_order<float, PASS_STEP>(s, st)
-                             : pass_order<float, PASS_DEPOSIT>(s, st);
+        return mode == PASS_STEP ? pass_margin<double, PASS_STEP>(s, st)
+                                 : pass_margin<double, PASS_DEPOSIT>(s, st);
+    return mode == PASS_STEP ? pass_margin<float, PASS_STEP>(s, st)
+                             : pass_margin<float, PASS_DEPOSIT>(s, st);
 }
 
 int launch_sort(pic_sim* s, cudaStream_t st) {

@@ -32,7 +32,7 @@ class PicConfig(ctypes.Structure):
                 ("beta_init", c_double * 3),
                 ("nx", c_int32), ("ny", c_int32), ("nz", c_int32), ("shape_order", c_int32),
                 ("precision", c_int32), ("current_correction", c_int32), ("init_fields", c_int32),
-                ("reserved", c_int32)]
+                ("tile_margin", c_int32)]
 
 
 class PicSpecies(ctypes.Structure):
@@ -109,7 +109,7 @@ def _stream_ptr(stream: Optional[torch.cuda.Stream]) -> c_void_p:
 
 def make_config(nx: int, ny: int, nz: int, *, dx=1.0, dy=1.0, dz=1.0, dt=1.0, vgal=(0.0, 0.0, 0.0),
                 c=1.0, eps0=1.0, rho_bg=0.0, beta_init=(0.0, 0.0, 0.0), shape_order=1,
-                precision=32, current_correction=1, init_fields=1) -> PicConfig:
+                precision=32, current_correction=1, init_fields=1, tile_margin=1) -> PicConfig:
     cfg = PicConfig()
     cfg.dx, cfg.dy, cfg.dz, cfg.dt = dx, dy, dz, dt
     cfg.vgal[:] = list(vgal)
@@ -118,6 +118,7 @@ def make_config(nx: int, ny: int, nz: int, *, dx=1.0, dy=1.0, dz=1.0, dt=1.0, vg
     cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
     cfg.shape_order, cfg.precision = shape_order, precision
     cfg.current_correction, cfg.init_fields = current_correction, init_fields
+    cfg.tile_margin = tile_margin
     return cfg
 
 
@@ -284,14 +285,16 @@ def step_many(sims: Sequence[Sim], nsteps: int, stream=None):
     check(lib.pic_step_many(arr, len(sims), nsteps, _stream_ptr(stream)))
 
 
-def sim_from_workload(wl, precision: Optional[int] = None, stream=None, device="cuda") -> Sim:
+def sim_from_workload(wl, precision: Optional[int] = None, stream=None, device="cuda",
+                      tile_margin: int = 1) -> Sim:
     """A run of a synthetic workload (duck-typed: grid, units, v_gal, species with
     q, m, ppc, u0, jitter, density), particles generated on the device."""
     prec = wl.precision if precision is None else precision
     cfg = make_config(wl.nx, wl.ny, wl.nz, dx=wl.dx, dy=wl.dy, dz=wl.dz, dt=wl.dt, vgal=wl.vgal,
                       c=wl.c, eps0=wl.eps0, rho_bg=wl.rho_bg, beta_init=wl.beta_init,
                       shape_order=wl.shape_order, precision=prec,
-                      current_correction=wl.current_correction, init_fields=wl.init_fields)
+                      current_correction=wl.current_correction, init_fields=wl.init_fields,
+                      tile_margin=tile_margin)
     ncells = wl.nx * wl.ny * wl.nz
     sp = []
     for k, s in enumerate(wl.species):

@@ -59,7 +59,7 @@ PROBE = r"""
 #define F(T, f) printf(#T " " #f " %zu\n", offsetof(T, f))
 int main(void) {
   printf("pic_config size %zu\npic_species size %zu\n", sizeof(pic_config), sizeof(pic_species));
-  F(pic_config, vgal); F(pic_config, beta_init); F(pic_config, nx); F(pic_config, reserved);
+  F(pic_config, vgal); F(pic_config, beta_init); F(pic_config, nx); F(pic_config, tile_margin);
   F(pic_species, n); F(pic_species, ppc); F(pic_species, species_id); F(pic_species, cell);
   F(pic_species, off); F(pic_species, u);
   return 0;
