@@ -139,10 +139,12 @@ int pic_footprint(const pic_config* cfg, const pic_species* species, int nspecie
 /* Create a run: validate, carve the caller-owned device workspace (at least
  * pic_footprint() bytes, 256-byte aligned), build the FP64 coefficient
  * tables, load or generate the particles and sort them into cell bins,
- * deposit rho^0, and set the initial fields. Enqueued on `stream`, then
- * synchronises that stream: returns PIC_EINVAL (and no run) if copied
- * particles were out of range (PIC_STATUS_BADINPUT). The species array is
- * read during the call only. */
+ * deposit rho^0, and set the initial fields. Enqueued on `stream`. When any
+ * species is copied from caller arrays, the call then synchronises that stream
+ * and returns PIC_EINVAL (and no run) if the particles were out of range
+ * (PIC_STATUS_BADINPUT). The species array is read during the call only.
+ * cuFFT plans are created once per grid shape and precision and shared by all
+ * runs of that shape for the life of the process. */
 int pic_init(const pic_config* cfg, const pic_species* species, int nspecies,
              void* workspace, size_t ws_bytes, void* stream, pic_sim** out);
 

@@ -4,8 +4,12 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <memory>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 
 #include "common.cuh"
 
@@ -19,6 +23,16 @@ int fail(int code, const std::string& msg) {
     g_err = msg;
     return code;
 }
+
+// cuFFT plans, shared by every run of the same grid shape and precision on a device
+// for the life of the process (plan creation allocates and synchronises). A run
+// keeps its own work area in its workspace; the entry's mutex serialises the
+// set-stream / set-work-area / execute sequence of runs that share a plan.
+struct PlanEntry {
+    cufftHandle r2c = 0, c2r = 0;
+    size_t work = 0;
+    std::mutex mu;
+};
 
 namespace {
 
@@ -81,6 +95,32 @@ Dims make_dims(const pic_config& c) {
 int energy_blocks_for(int64_t N) {
     int64_t b = (N + 2047) / 2048;
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, 1216));
+}
+
+std::mutex g_plan_mu;
+std::map<std::tuple<int, int, int, int, int>, std::unique_ptr<PlanEntry>> g_plans;
+
+int make_plans(const pic_config& c, const Dims& d, cufftHandle* r2c, cufftHandle* c2r,
+               size_t* work);
+
+int shared_plans(const pic_config& c, const Dims& d, PlanEntry** out) {
+    int dev = 0;
+    GP_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto key = std::make_tuple(dev, c.nx, c.ny, c.nz, c.precision);
+    auto it = g_plans.find(key);
+    if (it == g_plans.end()) {
+        std::unique_ptr<PlanEntry> e(new PlanEntry());
+        int rc = make_plans(c, d, &e->r2c, &e->c2r, &e->work);
+        if (rc != PIC_OK) {
+            if (e->r2c) cufftDestroy(e->r2c);
+            if (e->c2r) cufftDestroy(e->c2r);
+            return rc;
+        }
+        it = g_plans.emplace(key, std::move(e)).first;
+    }
+    *out = it->second.get();
+    return PIC_OK;
 }
 
 int make_plans(const pic_config& c, const Dims& d, cufftHandle* r2c, cufftHandle* c2r,
@@ -149,6 +189,8 @@ int check_tile_fits(const pic_config& c, const Dims& d) {
 }
 
 int exec_r2c(pic_sim* s, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(s->plans->mu);
+    GP_CUFFT(cufftSetWorkArea(s->plan_r2c, s->fftwork));
     GP_CUFFT(cufftSetStream(s->plan_r2c, st));
     if (s->cfg.precision == 64)
         GP_CUFFT(cufftExecD2Z(s->plan_r2c, (cufftDoubleReal*)s->S, (cufftDoubleComplex*)s->Sh));
@@ -158,6 +200,8 @@ int exec_r2c(pic_sim* s, cudaStream_t st) {
 }
 
 int exec_c2r(pic_sim* s, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(s->plans->mu);
+    GP_CUFFT(cufftSetWorkArea(s->plan_c2r, s->fftwork));
     GP_CUFFT(cufftSetStream(s->plan_c2r, st));
     if (s->cfg.precision == 64)
         GP_CUFFT(cufftExecZ2D(s->plan_c2r, (cufftDoubleComplex*)s->EBs, (cufftDoubleReal*)s->F));
@@ -291,12 +335,9 @@ int pic_footprint(const pic_config* cfg, const pic_species* species, int nspecie
     GP_CHECK(validate(cfg, species, nspecies));
     if (!bytes_out) return fail(PIC_EINVAL, "bytes_out is NULL");
     Dims d = make_dims(*cfg);
-    cufftHandle a = 0, b = 0;
-    size_t work = 0;
-    int rc = make_plans(*cfg, d, &a, &b, &work);
-    if (a) cufftDestroy(a);
-    if (b) cufftDestroy(b);
-    if (rc != PIC_OK) return rc;
+    PlanEntry* pe = nullptr;
+    GP_CHECK(shared_plans(*cfg, d, &pe));
+    size_t work = pe->work;
     int64_t n[PIC_MAX_SPECIES];
     for (int k = 0; k < nspecies; ++k) n[k] = species[k].n;
     Layout L;
@@ -320,7 +361,12 @@ int pic_init(const pic_config* cfg, const pic_species* species, int nspecies, vo
     s->d = make_dims(*cfg);
     int rc = check_tile_fits(*cfg, s->d);
     size_t work = 0;
-    if (rc == PIC_OK) rc = make_plans(*cfg, s->d, &s->plan_r2c, &s->plan_c2r, &work);
+    if (rc == PIC_OK) rc = shared_plans(*cfg, s->d, &s->plans);
+    if (rc == PIC_OK) {
+        s->plan_r2c = s->plans->r2c;
+        s->plan_c2r = s->plans->c2r;
+        work = s->plans->work;
+    }
     if (rc != PIC_OK) {
         pic_destroy(s);
         return rc;
@@ -384,10 +430,6 @@ int pic_init(const pic_config* cfg, const pic_species* species, int nspecies, vo
         }                           \
     } while (0)
 
-    INIT_TRY(cufftSetWorkArea(s->plan_r2c, s->fftwork) == CUFFT_SUCCESS
-                 ? PIC_OK : fail(PIC_ECUFFT, "cufftSetWorkArea"));
-    INIT_TRY(cufftSetWorkArea(s->plan_c2r, s->fftwork) == CUFFT_SUCCESS
-                 ? PIC_OK : fail(PIC_ECUFFT, "cufftSetWorkArea"));
     {
         cudaError_t e = cudaStreamCreateWithFlags(&s->priv, cudaStreamNonBlocking);
         INIT_TRY(e == cudaSuccess ? PIC_OK : fail(PIC_ECUDA, cudaGetErrorString(e)));
@@ -438,7 +480,9 @@ int pic_init(const pic_config* cfg, const pic_species* species, int nspecies, vo
     INIT_TRY(launch_init_fields(s, st));
     INIT_TRY(launch_master_to_scratch(s, st));
     INIT_TRY(exec_c2r(s, st));
-    {
+    bool copied = false;
+    for (int k = 0; k < nspecies; ++k) copied |= species[k].n > 0 && species[k].ppc[0] <= 0;
+    if (copied) {   // report bad caller input now (the generator never produces any)
         int32_t stv = 0;
         cudaError_t e = cudaStreamSynchronize(st);
         if (e == cudaSuccess) e = cudaMemcpy(&stv, s->status, sizeof(stv), cudaMemcpyDeviceToHost);
@@ -460,8 +504,6 @@ int pic_destroy(pic_sim* s) {
         cudaEventDestroy(r.b);
     }
     for (auto e : s->event_pool) cudaEventDestroy(e);
-    if (s->plan_r2c) cufftDestroy(s->plan_r2c);
-    if (s->plan_c2r) cufftDestroy(s->plan_c2r);
     if (s->priv) cudaStreamDestroy(s->priv);
     delete s;
     return PIC_OK;

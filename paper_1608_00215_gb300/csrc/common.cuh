@@ -123,7 +123,7 @@ struct Dims {
     int margin;
 };
 
-struct pic_sim_impl;
+struct PlanEntry;
 
 }  // namespace galpic
 
@@ -154,7 +154,8 @@ struct pic_sim {
     int32_t* tile_sum;    // sort: scan partial sums
     unsigned long long* cnt;
     int32_t* status;
-    cufftHandle plan_r2c, plan_c2r;
+    cufftHandle plan_r2c, plan_c2r;   // shared by runs of the same shape (not owned)
+    galpic::PlanEntry* plans;
     cudaStream_t priv;
     cudaGraphExec_t graph;
     bool graph_ok;

@@ -184,31 +184,25 @@ template <> struct FieldTile<double> {
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) / 16 * 16; }
 
-// Per-warp staging area of the grouped deposit. For every lane:
-//   * values v0..v3 (J: q w v / dV in v0..v2; rho: q w / dV in v0) and x weights
-//     (w0, w2, w1, w3) for NW = 4 -- so that (w_h, w_{h+2}) is one pair -- or
-//     (w0, w1, 0, 0) for NW = 2, as 16-byte quads stored quad-major ([quad][lane]):
-//     the lanes' vector stores are contiguous and a read of one lane's quad by the
-//     whole warp is a broadcast;
-//   * the NW*NW products wy[b] wz[c] (element b*NW + c), one row of QR 16-byte
-//     quads per lane, quad k of lane l stored in slot k ^ ((l / (8/QR)) % QR). The
-//     swizzle spreads the 8 lanes of each quarter-warp store over 8 distinct bank
-//     groups; a read of one lane's row by 16 lanes still touches one contiguous row.
+// Per-warp staging area of the grouped deposit, transposed: one row per staged
+// quantity, indexed by lane. Rows 0..2 hold the velocity (J phase), then NW rows of
+// x weights wx[a], NW rows of y weights wy[b] and NW rows of z weights wz[c].
+// A group of lanes that share a stencil is summed two members at a time: the values
+// of lanes m and m+1 of one row are one aligned pair, loaded in one instruction and
+// fed to the packed FP32x2 multiply/FMA. The row stride RS = 34 elements keeps pairs
+// aligned and puts consecutive rows two banks apart, so the up-to-16 distinct rows a
+// warp reads at one lane index hit distinct banks; a lane's stores to its own column
+// are contiguous across the warp.
 template <typename T, int NW> struct Stage {
-    static constexpr int EPQ = 16 / (int)sizeof(T);   // elements per quad
-    static constexpr int NQ = 8 / EPQ;                // quads holding v0..v3, x weights
-    static constexpr int QR = NW * NW / EPQ;          // quads per y-z row
-    static constexpr size_t QUAD_BYTES = (size_t)32 * NQ * 16;
-    static constexpr size_t BYTES = QUAD_BYTES + (size_t)32 * QR * 16;
-    unsigned char* base;
-    __device__ T* elem(int m, int e) const {   // element e (0..7) of lane m
-        return reinterpret_cast<T*>(base + ((e / EPQ) * 32 + m) * 16) + (e % EPQ);
-    }
-    __device__ static int swz(int m) { return (m / (8 / QR > 0 ? 8 / QR : 1)) % QR; }
-    __device__ T* row_quad(int m, int k) const {   // quad k of lane m's y-z row
-        return reinterpret_cast<T*>(base + QUAD_BYTES + (size_t)(m * QR + (k ^ swz(m))) * 16);
-    }
-    __device__ T row(int m, int e) const { return row_quad(m, e / EPQ)[e % EPQ]; }
+    static constexpr int RS = 34;
+    static constexpr int ROWS = 3 + 3 * NW;
+    static constexpr size_t BYTES = align16((size_t)ROWS * RS * sizeof(T));   // per warp
+    T* base;
+    __device__ T* row(int r) const { return base + r * RS; }
+    __device__ T* vrow(int q) const { return row(q); }
+    __device__ T* xrow(int a) const { return row(3 + a); }
+    __device__ T* yrow(int b) const { return row(3 + NW + b); }
+    __device__ T* zrow(int c) const { return row(3 + 2 * NW + c); }
 };
 
 __host__ __device__ constexpr size_t stage_bytes(int NW, size_t T) {
@@ -307,103 +301,175 @@ __device__ void deposit_global(const PassK<T>& p, int ix, int iy, int iz, const 
         }
 }
 
-// Grouped deposit of one warp. `member`: this lane staged a record and its stencil
-// starts at tile node `key` (tile linear index). Q = 3 (J at q0 = 0) or 1 (rho at q0 = 3).
+// Adds K values to K distinct shared-memory words. Shared-memory floating-point
+// atomics are compare-and-swap loops on this GPU; issuing all K reads, then all K
+// compare-and-swaps, and retrying only the ones that lost a race keeps K round trips
+// in flight at once instead of K dependent ones.
+__device__ __forceinline__ unsigned as_bits(float x) { return __float_as_uint(x); }
+__device__ __forceinline__ unsigned long long as_bits(double x) { return (unsigned long long)__double_as_longlong(x); }
+__device__ __forceinline__ float from_bits(unsigned x) { return __uint_as_float(x); }
+__device__ __forceinline__ double from_bits(unsigned long long x) { return __longlong_as_double((long long)x); }
+
+template <typename T, int K>
+__device__ __forceinline__ void smem_add_batch(T* const (&addr)[K], const T (&val)[K]) {
+    typedef decltype(as_bits((T)0)) U;
+    U old[K];
+    bool done[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) old[k] = as_bits(*reinterpret_cast<volatile T*>(addr[k]));
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const U prev = atomicCAS(reinterpret_cast<U*>(addr[k]), old[k], as_bits(from_bits(old[k]) + val[k]));
+        done[k] = prev == old[k];
+        old[k] = prev;
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        while (!done[k]) {   // lost a race with another warp: retry (lock-free, always progresses)
+            const U prev = atomicCAS(reinterpret_cast<U*>(addr[k]), old[k], as_bits(from_bits(old[k]) + val[k]));
+            done[k] = prev == old[k];
+            old[k] = prev;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ typename Pair<T>::type ld2(const T* p) {
+    return *reinterpret_cast<const typename Pair<T>::type*>(p);
+}
+
+// Grouped deposit of one warp. `member`: this lane staged its weights (and, for J,
+// its velocity) and its stencil starts at tile node `key` (tile linear index).
+// Q = 3 (J, components q0 = 0..2) or 1 (rho, q0 = 3); every deposited value is
+// qw * (weight product) * (velocity component or 1). For each group of lanes with
+// one key, the lanes take (node, component) roles, sum over the group's members
+// (two at a time when the group is a contiguous run of lanes, the normal case for
+// cell-sorted particles) and add each role's sum to the shared tile once.
 // Every lane of the warp must call this (warp-collective).
 template <typename T, int NW, int Q, int TE>
-__device__ void group_deposit(T* sD, const Stage<T, NW>& stg, bool member, int key, int lane) {
+__device__ void group_deposit(T* sD, const Stage<T, NW>& stg, bool member, int key, int lane, T qw) {
     typedef typename Pair<T>::type P2;
     constexpr int q0 = (Q == 3) ? 0 : 3;
     constexpr int R = TE * TE * TE;
+    const P2 one = Pair<T>::make((T)1, (T)1);
+    const P2 zero = Pair<T>::make((T)0, (T)0);
     unsigned pending = __ballot_sync(0xffffffffu, member);
     while (pending) {
         const int leader = __ffs(pending) - 1;
         const int gkey = __shfl_sync(0xffffffffu, key, leader);
         const unsigned grp = __ballot_sync(0xffffffffu, member && key == gkey);
         pending &= ~grp;
+        const int lo = __ffs(grp) - 1;
+        const int len = __popc(grp);
+        const bool run = (grp >> lo) == (len == 32 ? 0xffffffffu : ((1u << len) - 1u));   // warp-uniform
         if (NW == 4) {
-            // lane -> y-z pair bc = lane & 15 and x nodes h, h + 2 (h = lane >> 4)
-            const int bc = lane & 15, h = lane >> 4;
-            P2 acc[Q];
+            // lane -> y-z node (b, c) = (bc >> 2, bc & 3), bc = lane & 15, and x nodes h, h + 2
+            const int bc = lane & 15, h = lane >> 4, b = bc >> 2, c = bc & 3;
+            const T* xh = stg.xrow(h);
+            const T* xh2 = stg.xrow(h + 2);
+            const T* yb = stg.yrow(b);
+            const T* zc = stg.zrow(c);
+            P2 A[Q], A2[Q];   // (even, odd member) partial sums for x nodes h and h + 2
 #pragma unroll
-            for (int q = 0; q < Q; ++q) acc[q] = Pair<T>::make((T)0, (T)0);
-            unsigned g = grp;
-            while (g) {
-                const int m = __ffs(g) - 1;
-                g &= g - 1;
-                const P2 wx2 = *reinterpret_cast<const P2*>(stg.elem(m, 4 + 2 * h));
-                const T wyz = stg.row(m, bc);
-                const P2 w = pmul(wx2, Pair<T>::make(wyz, wyz));
-                T v[4];
-                if (sizeof(T) == 4) {
-                    const float4 vv = *reinterpret_cast<const float4*>(stg.elem(m, 0));
-                    v[0] = vv.x; v[1] = vv.y; v[2] = vv.z; v[3] = vv.w;
-                } else {
+            for (int q = 0; q < Q; ++q) A[q] = A2[q] = zero;
+            auto single = [&](int m) {
+                const T wyz = yb[m] * zc[m];
+                const T w0 = xh[m] * wyz, w1 = xh2[m] * wyz;
 #pragma unroll
-                    for (int q = 0; q < Q; ++q) v[q] = *stg.elem(m, q);
+                for (int q = 0; q < Q; ++q) {
+                    const T v = (Q == 3) ? stg.vrow(q)[m] : (T)1;
+                    A[q].x = fma(w0, v, A[q].x);
+                    A2[q].x = fma(w1, v, A2[q].x);
                 }
+            };
+            auto pair = [&](int m) {
+                const P2 wyz = pmul(ld2(yb + m), ld2(zc + m));
+                const P2 w0 = pmul(ld2(xh + m), wyz);
+                const P2 w1 = pmul(ld2(xh2 + m), wyz);
 #pragma unroll
-                for (int q = 0; q < Q; ++q) acc[q] = pfma(w, Pair<T>::make(v[q], v[q]), acc[q]);
-            }
-            const int b = bc >> 2, c = bc & 3;
-            const int n0 = gkey + (h * TE + b) * TE + c;
-            const int n1 = n0 + 2 * TE * TE;
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                atomicAdd(&sD[(q0 + q) * R + n0], acc[q].x);
-                atomicAdd(&sD[(q0 + q) * R + n1], acc[q].y);
-            }
-        } else {
-            // NW == 2: lane -> (component q = lane / 8, node j = lane % 8)
-            if (lane < 8 * Q) {
-                const int q = lane >> 3, j = lane & 7;
-                const int a = j >> 2, b = (j >> 1) & 1, c = j & 1;
-                T acc = (T)0;
+                for (int q = 0; q < Q; ++q) {
+                    const P2 v = (Q == 3) ? ld2(stg.vrow(q) + m) : one;
+                    A[q] = pfma(w0, v, A[q]);
+                    A2[q] = pfma(w1, v, A2[q]);
+                }
+            };
+            if (run) {
+                int m = lo;
+                const int me = lo + len;
+                if (m & 1) single(m++);
+                for (; m + 1 < me; m += 2) pair(m);
+                if (m < me) single(m);
+            } else {
                 unsigned g = grp;
                 while (g) {
                     const int m = __ffs(g) - 1;
                     g &= g - 1;
-                    acc = fma(*stg.elem(m, 4 + a) * stg.row(m, b * 2 + c), *stg.elem(m, q), acc);
+                    single(m);
                 }
-                atomicAdd(&sD[(q0 + q) * R + gkey + (a * TE + b) * TE + c], acc);
+            }
+            const int n0 = gkey + (h * TE + b) * TE + c;
+            const int n1 = n0 + 2 * TE * TE;
+            T* addr[2 * Q];
+            T val[2 * Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                addr[2 * q] = &sD[(q0 + q) * R + n0];
+                addr[2 * q + 1] = &sD[(q0 + q) * R + n1];
+                val[2 * q] = (A[q].x + A[q].y) * qw;
+                val[2 * q + 1] = (A2[q].x + A2[q].y) * qw;
+            }
+            smem_add_batch<T, 2 * Q>(addr, val);
+        } else {
+            // NW == 2: lane -> (component q = lane / 8, node j = lane % 8)
+            if (lane < 8 * Q) {
+                const int q = lane >> 3, j = lane & 7;
+                const int ax = j >> 2, by = (j >> 1) & 1, cz = j & 1;
+                const T* xa = stg.xrow(ax);
+                const T* yb = stg.yrow(by);
+                const T* zc = stg.zrow(cz);
+                const T* vq = stg.vrow(Q == 3 ? q : 0);
+                P2 A = zero;
+                if (run) {
+                    int m = lo;
+                    const int me = lo + len;
+                    if (m & 1) {
+                        A.x = fma(xa[m] * yb[m] * zc[m], (Q == 3) ? vq[m] : (T)1, A.x);
+                        ++m;
+                    }
+                    for (; m + 1 < me; m += 2) {
+                        const P2 w = pmul(pmul(ld2(xa + m), ld2(yb + m)), ld2(zc + m));
+                        A = pfma(w, (Q == 3) ? ld2(vq + m) : one, A);
+                    }
+                    if (m < me) A.x = fma(xa[m] * yb[m] * zc[m], (Q == 3) ? vq[m] : (T)1, A.x);
+                } else {
+                    unsigned g = grp;
+                    while (g) {
+                        const int m = __ffs(g) - 1;
+                        g &= g - 1;
+                        A.x = fma(xa[m] * yb[m] * zc[m], (Q == 3) ? vq[m] : (T)1, A.x);
+                    }
+                }
+                T* addr[1] = {&sD[(q0 + q) * R + gkey + (ax * TE + by) * TE + cz]};
+                const T val[1] = {(A.x + A.y) * qw};
+                smem_add_batch<T, 1>(addr, val);
             }
         }
     }
 }
 
-// Stage this lane's separable weights and values (Q values) for group_deposit.
+// Stage this lane's weights (and, for J, its velocity) in its column of the rows.
 template <typename T, int NW>
 __device__ __forceinline__ void stage_record(const Stage<T, NW>& stg, int lane, const T* wx, const T* wy,
-                                             const T* wz, const T* val, int Q) {
-    T e[8];
-    for (int q = 0; q < 4; ++q) e[q] = q < Q ? val[q] : (T)0;
-    if (NW == 4) {
-        e[4] = wx[0]; e[5] = wx[2]; e[6] = wx[1]; e[7] = wx[3];
-    } else {
-        e[4] = wx[0]; e[5] = wx[1]; e[6] = (T)0; e[7] = (T)0;
+                                             const T* wz, const T* vel) {
+    if (vel) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) stg.vrow(q)[lane] = vel[q];
     }
-    if (sizeof(T) == 4) {
-        *reinterpret_cast<float4*>(stg.elem(lane, 0)) = make_float4(e[0], e[1], e[2], e[3]);
-        *reinterpret_cast<float4*>(stg.elem(lane, 4)) = make_float4(e[4], e[5], e[6], e[7]);
-    } else {
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-            *reinterpret_cast<double2*>(stg.elem(lane, 2 * k)) = make_double2(e[2 * k], e[2 * k + 1]);
-    }
-    T w[NW * NW];
-#pragma unroll
-    for (int b = 0; b < NW; ++b)
-#pragma unroll
-        for (int c = 0; c < NW; ++c) w[b * NW + c] = wy[b] * wz[c];
-    if (sizeof(T) == 4) {
-#pragma unroll
-        for (int k = 0; k < NW * NW / 4; ++k)
-            *reinterpret_cast<float4*>(stg.row_quad(lane, k)) =
-                make_float4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
-    } else {
-#pragma unroll
-        for (int k = 0; k < NW * NW / 2; ++k)
-            *reinterpret_cast<double2*>(stg.row_quad(lane, k)) = make_double2(w[2 * k], w[2 * k + 1]);
+    for (int a = 0; a < NW; ++a) {
+        stg.xrow(a)[lane] = wx[a];
+        stg.yrow(a)[lane] = wy[a];
+        stg.zrow(a)[lane] = wz[a];
     }
 }
 
@@ -421,7 +487,7 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
     T* sD = reinterpret_cast<T*>(smem_raw + L.dep);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     Stage<T, NW> stg;
-    stg.base = smem_raw + L.stage + warp * Stage<T, NW>::BYTES;
+    stg.base = reinterpret_cast<T*>(smem_raw + L.stage + warp * Stage<T, NW>::BYTES);
 
     const int b = blockIdx.x;
     const int bz = b % p.nbz, by = (b / p.nbz) % p.nby, bx = b / (p.nbz * p.nby);
@@ -452,25 +518,40 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
     for (int s = 0; s < p.nspecies; ++s) {
         const SpeciesK<T> sp = p.sp[s];
         const int beg = sp.bin_start[b], end = sp.bin_start[b + 1];
+        // the next chunk's particle is loaded while the current one is processed
+        int c_n = 0;
+        T f_n[3] = {0, 0, 0}, u_n[3] = {0, 0, 0};
+        if (beg + (int)threadIdx.x < end) {
+            const int j = beg + threadIdx.x;
+            c_n = sp.cell[j];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                f_n[d] = sp.off[d][j];
+                u_n[d] = sp.u[d][j];
+            }
+        }
         for (int base = beg; base < end; base += PASS_THREADS) {
             const int i = base + threadIdx.x;
             const bool valid = i < end;
             int ix = 0, iy = 0, iz = 0;
-            T fx = 0, fy = 0, fz = 0, ux = 0, uy = 0, uz = 0;
+            T fx = f_n[0], fy = f_n[1], fz = f_n[2], ux = u_n[0], uy = u_n[1], uz = u_n[2];
+            const int c = c_n;
+            if (i + PASS_THREADS < end) {
+                const int j = i + PASS_THREADS;
+                c_n = sp.cell[j];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    f_n[d] = sp.off[d][j];
+                    u_n[d] = sp.u[d][j];
+                }
+            }
             T wx[4], wy[4], wz[4];
             T vx = 0, vy = 0, vz = 0;
             if (valid) {
-                const int c = sp.cell[i];
                 ix = p.div_nynz.div(c);
                 const int rem = c - ix * (p.ny * p.nz);
                 iy = p.div_nz.div(rem);
                 iz = rem - iy * p.nz;
-                fx = sp.off[0][i];
-                fy = sp.off[1][i];
-                fz = sp.off[2][i];
-                ux = sp.u[0][i];
-                uy = sp.u[1][i];
-                uz = sp.u[2][i];
                 if (MODE == PASS_STEP) {
                     // ---- gather E^n, B^n at x^n
                     SH::w(fx, wx);
@@ -585,7 +666,8 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
                     if (rx >= 0 && ry >= 0 && rz >= 0) {
                         member = true;
                         key = (rx * TE + ry) * TE + rz;
-                        stage_record<T, NW>(stg, lane, wx, wy, wz, val, phase == 0 ? 3 : 1);
+                        const T vel[3] = {vx, vy, vz};
+                        stage_record<T, NW>(stg, lane, wx, wy, wz, phase == 0 ? vel : nullptr);
                     } else {
                         if (phase == 1) far++;
                         if (phase == 0)
@@ -596,9 +678,9 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
                 }
                 __syncwarp();
                 if (phase == 0)
-                    group_deposit<T, NW, 3, TE>(sD, stg, member, key, lane);
+                    group_deposit<T, NW, 3, TE>(sD, stg, member, key, lane, sp.qw_dv);
                 else
-                    group_deposit<T, NW, 1, TE>(sD, stg, member, key, lane);
+                    group_deposit<T, NW, 1, TE>(sD, stg, member, key, lane, sp.qw_dv);
                 __syncwarp();
             }
             if (valid && MODE == PASS_STEP) {
