@@ -341,7 +341,8 @@ def long_run(args):
     t0 = time.perf_counter()
     done = 0
     while done < args.steps:
-        n = min(args.long_run_every, args.steps - done)
+        seg = args.long_run_oracle if (done == 0 and args.long_run_oracle > 0) else args.long_run_every
+        n = min(seg, args.steps - done)
         s32.step(n - 1)
         s64.step(n - 1)
         rho32 = s32.get(gp.BUF_RHO_HAT, device="cpu").to(torch.complex128).numpy()

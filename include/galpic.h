@@ -121,7 +121,9 @@ enum pic_buffer {
     PIC_BUF_B_HAT = 5,    /* spectral B^n, 3*M complex                                 */
     PIC_BUF_RHO_HAT = 6,  /* spectral rho^n, M complex                                  */
     PIC_BUF_SRC_HAT = 7,  /* spectra of the last sources (Jx, Jy, Jz, rho), 4*M complex  */
-    PIC_BUF_TABLES = 8    /* per-mode factors T1, T2, T3, T4, A5, A6, 6*M complex        */
+    PIC_BUF_TABLES = 8,   /* per-mode factors T1, T2, T3, T4, A5, A6, 6*M complex        */
+    PIC_BUF_STATUS = 9    /* the device status word (int32, PIC_STATUS_* bits); reading it
+                             with pic_get does not clear it and does not synchronise     */
 };
 
 /* Library version string. */
@@ -148,8 +150,10 @@ int pic_footprint(const pic_config* cfg, const pic_species* species, int nspecie
 int pic_init(const pic_config* cfg, const pic_species* species, int nspecies,
              void* workspace, size_t ws_bytes, void* stream, pic_sim** out);
 
-/* Release the host handle, cuFFT plans, private stream and graph. The
- * workspace stays the caller's. Synchronises the run's work first. */
+/* Release the run's host handle, private stream, CUDA graph and events. The
+ * workspace stays the caller's, and so do the shared cuFFT plans. The caller
+ * must have completed (or synchronised) the work it enqueued for this run on its
+ * own streams; the call does not synchronise the device. */
 int pic_destroy(pic_sim* sim);
 
 /* Deposit rho and J = sum q w v S / dV at the current positions x^n with the

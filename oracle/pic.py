@@ -265,15 +265,16 @@ def deposit_J(cfg: Config, species: Sequence[Species], vel) -> np.ndarray:
 # Spectral stages
 # ----------------------------------------------------------------------------
 
-def current_correction(cfg: Config, J_hat, rho_old_hat, rho_new_hat):
+def current_correction(cfg: Config, J_hat, rho_old_hat, rho_new_hat, k=None):
     """J <- J + k (D - k.J)/k^2 with D = (theta^2 rho^n - rho^{n+1}) / (i dt E1(k.v dt)).
 
     D is the value of k.J that the Galilean continuity equation
     (d_t - v_gal.grad') rho + div' j = 0, integrated over one step with J
     constant in x', requires: rho^{n+1} = theta^2 rho^n - (theta^2 - 1) k.J/(k.v).
-    The k = 0 mode is left unchanged.
+    The k = 0 mode is left unchanged. ``k`` = (kx, ky, kz) selects other modes than
+    the whole grid (arrays broadcastable with the data).
     """
-    kx, ky, kz = kvectors(cfg)
+    kx, ky, kz = kvectors(cfg) if k is None else k
     k2 = kx * kx + ky * ky + kz * kz
     kv = kx * cfg.vgal[0] + ky * cfg.vgal[1] + kz * cfg.vgal[2]
     th2 = np.exp(1j * kv * cfg.dt)
@@ -284,15 +285,20 @@ def current_correction(cfg: Config, J_hat, rho_old_hat, rho_new_hat):
     return np.stack([J_hat[0] + kx * g, J_hat[1] + ky * g, J_hat[2] + kz * g])
 
 
-def field_update(cfg: Config, E_hat, B_hat, J_hat, rho_old_hat, rho_new_hat):
+def field_update(cfg: Config, E_hat, B_hat, J_hat, rho_old_hat, rho_new_hat, k=None):
     """The Galilean-PSATD update of spectral E and B from n to n+1 (paper's update equations):
 
     B^{n+1} = T1 B^n - T2 (i k x E^n) + T3 (i k x J^{n+1/2})
     E^{n+1} = T1 E^n + c^2 T2 (i k x B^n) + T4 J^{n+1/2} - (T5 rho^{n+1} - T6 rho^n) i k
-    with T1..T6 from ``oracle.coefficients``.
+    with T1..T6 from ``oracle.coefficients``. ``k`` = (kx, ky, kz) selects other modes
+    than the whole grid (1-D arrays of the modes, data of shape (3, nmodes) / (nmodes,)).
     """
-    t = tables(cfg)
-    kx, ky, kz = kvectors(cfg)
+    if k is None:
+        t = tables(cfg)
+        kx, ky, kz = kvectors(cfg)
+    else:
+        kx, ky, kz = k
+        t = coef.coefficients(kx, ky, kz, cfg.vgal, cfg.c, cfg.dt, cfg.eps0)
     kvec = np.stack(np.broadcast_arrays(kx, ky, kz)).astype(np.complex128)
     ik = 1j * kvec
     B_new = t["T1"] * B_hat - t["T2"] * cross(ik, E_hat) + t["T3"] * cross(ik, J_hat)

@@ -497,7 +497,9 @@ int pic_init(const pic_config* cfg, const pic_species* species, int nspecies, vo
 
 int pic_destroy(pic_sim* s) {
     if (!s) return PIC_OK;
-    cudaDeviceSynchronize();
+    // Only the run's own graph, private stream and events are released here; the
+    // caller has finished (or synchronised) the work it enqueued on its streams.
+    if (s->priv) cudaStreamSynchronize(s->priv);
     if (s->graph_ok) cudaGraphExecDestroy(s->graph);
     for (auto& r : s->recs) {
         cudaEventDestroy(r.a);
@@ -572,6 +574,7 @@ static int buffer_of(pic_sim* s, int which, char** ptr, size_t* bytes) {
         case PIC_BUF_RHO_HAT: *ptr = (char*)s->Rn; *bytes = M * 2 * T; break;
         case PIC_BUF_SRC_HAT: *ptr = (char*)s->Sh; *bytes = 4 * M * 2 * T; break;
         case PIC_BUF_TABLES: *ptr = (char*)s->Tab; *bytes = 6 * M * 2 * T; break;
+        case PIC_BUF_STATUS: *ptr = (char*)s->status; *bytes = sizeof(int32_t); break;
         default: return fail(PIC_EINVAL, "unknown buffer id " + std::to_string(which));
     }
     return PIC_OK;

@@ -258,8 +258,9 @@ struct PassK {
 };
 
 // Move (i, f) by d cells along an axis of n cells: offset back to [0, 1), periodic.
+// Returns the cell shift (before the periodic wrap).
 template <typename T>
-__device__ __forceinline__ void drift_axis(int& i, T& f, T d, int n) {
+__device__ __forceinline__ int drift_axis(int& i, T& f, T d, int n) {
     f += d;
     T s = floor(f);
     f -= s;
@@ -269,16 +270,18 @@ __device__ __forceinline__ void drift_axis(int& i, T& f, T d, int n) {
         si += 1;
     }
     i = wrap_near(i + si, n);
+    return si;
 }
 
-// Tile index of the first stencil node of a particle in cell i along one axis
-// (tile node t holds global node o + t with o = bin origin + J0 - margin, so the
-// stencil start i + J0 sits at t = i - bin origin + margin, taken modulo the
-// periodic axis length n); -1 if the tile does not hold the whole stencil.
-template <int NW>
-__device__ __forceinline__ int tile_start(int rel, int n, int extent) {
-    int r = wrap_near(rel, n);
-    return (r + NW <= extent) ? r : -1;
+// Tile coordinates: tile node t holds global node (o + t) mod n with
+// o = bin origin + J0 - margin, so the stencil of a particle in cell i starts at tile
+// index r = i - bin origin + margin; the pass tracks r through the drifts without
+// wrapping it (r + shift stays congruent to the new cell's index modulo n). The
+// stencil lies in the tile iff 0 <= r <= extent - NW; otherwise the particle takes
+// the global-memory path.
+template <int NW, int TE>
+__device__ __forceinline__ bool in_tile(int r) {
+    return (unsigned)r <= (unsigned)(TE - NW);
 }
 
 // Direct deposit of Q values at one particle's stencil into the global grids
@@ -533,7 +536,7 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
         for (int base = beg; base < end; base += PASS_THREADS) {
             const int i = base + threadIdx.x;
             const bool valid = i < end;
-            int ix = 0, iy = 0, iz = 0;
+            int ix = 0, iy = 0, iz = 0, rx = -1, ry = -1, rz = -1;
             T fx = f_n[0], fy = f_n[1], fz = f_n[2], ux = u_n[0], uy = u_n[1], uz = u_n[2];
             const int c = c_n;
             if (i + PASS_THREADS < end) {
@@ -552,16 +555,16 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
                 const int rem = c - ix * (p.ny * p.nz);
                 iy = p.div_nz.div(rem);
                 iz = rem - iy * p.nz;
+                rx = ix - x0 + MARGIN;
+                ry = iy - y0 + MARGIN;
+                rz = iz - z0 + MARGIN;
                 if (MODE == PASS_STEP) {
                     // ---- gather E^n, B^n at x^n
                     SH::w(fx, wx);
                     SH::w(fy, wy);
                     SH::w(fz, wz);
                     T E[3], B[3];
-                    const int rx = tile_start<NW>(ix - x0 + MARGIN, p.nx, TE);
-                    const int ry = tile_start<NW>(iy - y0 + MARGIN, p.ny, TE);
-                    const int rz = tile_start<NW>(iz - z0 + MARGIN, p.nz, TE);
-                    if (rx >= 0 && ry >= 0 && rz >= 0) {
+                    if (in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz)) {
                         // two interleaved accumulator sets (even / odd z node) for ILP
                         P2 a0 = Pair<T>::make(0, 0), a1 = a0, a2 = a0, c0 = a0, c1 = a0, c2 = a0;
                         P2 wzp[NW];
@@ -642,9 +645,9 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
                 int key = 0;
                 if (valid) {
                     if (MODE == PASS_STEP) {
-                        drift_axis(ix, fx, (vx - p.vgal[0]) * p.hd[0], p.nx);
-                        drift_axis(iy, fy, (vy - p.vgal[1]) * p.hd[1], p.ny);
-                        drift_axis(iz, fz, (vz - p.vgal[2]) * p.hd[2], p.nz);
+                        rx += drift_axis(ix, fx, (vx - p.vgal[0]) * p.hd[0], p.nx);
+                        ry += drift_axis(iy, fy, (vy - p.vgal[1]) * p.hd[1], p.ny);
+                        rz += drift_axis(iz, fz, (vz - p.vgal[2]) * p.hd[2], p.nz);
                     }
                     if (MODE == PASS_STEP || phase == 0) {
                         SH::w(fx, wx);
@@ -660,10 +663,7 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
                         val[0] = sp.qw_dv;
                         val[1] = val[2] = (T)0;
                     }
-                    const int rx = tile_start<NW>(ix - x0 + MARGIN, p.nx, TE);
-                    const int ry = tile_start<NW>(iy - y0 + MARGIN, p.ny, TE);
-                    const int rz = tile_start<NW>(iz - z0 + MARGIN, p.nz, TE);
-                    if (rx >= 0 && ry >= 0 && rz >= 0) {
+                    if (in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz)) {
                         member = true;
                         key = (rx * TE + ry) * TE + rz;
                         const T vel[3] = {vx, vy, vz};

@@ -23,7 +23,7 @@ ERRORS = {-1: "PIC_EINVAL", -2: "PIC_ENOMEM", -3: "PIC_ECUDA", -4: "PIC_ETIMEOUT
 PIC_MAX_SPECIES = 8
 PIC_STATUS_NONFINITE = 1
 
-BUF_E, BUF_B, BUF_J, BUF_RHO, BUF_E_HAT, BUF_B_HAT, BUF_RHO_HAT, BUF_SRC_HAT, BUF_TABLES = range(9)
+BUF_E, BUF_B, BUF_J, BUF_RHO, BUF_E_HAT, BUF_B_HAT, BUF_RHO_HAT, BUF_SRC_HAT, BUF_TABLES, BUF_STATUS = range(10)
 
 
 class PicConfig(ctypes.Structure):
@@ -261,8 +261,14 @@ class Sim:
         check(lib.pic_profile_read(self.handle, ms, cnt))
         return {name: {"ms": ms[i], "count": int(cnt[i])} for i, name in enumerate(STAGES)}
 
+    def status_async(self, out: torch.Tensor):
+        """Copy the device status word into the int32 tensor `out` (pinned host or
+        device) on the run's stream, without synchronising or clearing it."""
+        check(lib.pic_get(self.handle, BUF_STATUS, c_void_p(out.data_ptr()), 4, _stream_ptr(self.stream)))
+
     def close(self):
         if self.handle:
+            (self.stream if self.stream is not None else torch.cuda.current_stream()).synchronize()
             check(lib.pic_destroy(self.handle))
             self.handle = c_void_p()
 

@@ -56,6 +56,7 @@ class _Active:
     done: int = 0
     event: Optional[torch.cuda.Event] = None
     rec: RunRecord = None
+    status: Optional[torch.Tensor] = None     # pinned int32 copy of the device status word
 
 
 def footprint(wl, precision: Optional[int] = None) -> int:
@@ -142,7 +143,7 @@ def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_
                 continue
             if a.done >= a.req.steps:
                 a.rec.finish = time.perf_counter() - t0
-                a.rec.status = a.sim.status()
+                a.rec.status = int(a.status.item())     # copied when the last chunk was enqueued
                 if keep_final_state and on_retire is not None:
                     on_retire(a.req, a.sim)
                 a.sim.close()
@@ -152,6 +153,8 @@ def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_
             n = min(chunk, a.req.steps - a.done)
             with torch.cuda.stream(a.stream):
                 a.sim.step(n)
+                if a.done + n >= a.req.steps:
+                    a.sim.status_async(a.status)    # read without a device-wide synchronisation
                 a.event = torch.cuda.Event()
                 a.event.record(a.stream)
             a.done += n
@@ -171,7 +174,8 @@ def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_
                 continue
             rec.start = time.perf_counter() - t0
             used += fps[r.rid]
-            active.append(_Active(r, sim, stream, 0, None, rec))
+            active.append(_Active(r, sim, stream, 0, None, rec,
+                                  torch.zeros(1, dtype=torch.int32).pin_memory()))
             max_conc = max(max_conc, len(active))
             qi += 1
         if active and all(a.event is not None and not a.event.query() for a in active):

@@ -1,0 +1,144 @@
+"""Parity at the full size and launch configuration that bench.py times:
+256x256x512 cells, 536,870,912 particles, gamma = 130 e-p plasma, cubic shapes,
+FP32 with FP64-built tables, tile margin 1.
+
+The oracle cannot step this size, so it checks sampled outputs one by one and
+properties that hold at any size:
+  * 2048 particles per species: gather from the GPU's E, B, Boris push and both
+    Galilean half drifts against the oracle's functions;
+  * total charge and current of the deposited sources against the particle sums;
+  * the forward FFT of the GPU's own sources against SciPy on the whole grid;
+  * 512 sampled modes of the k-space update against the oracle's per-mode
+    current correction and Galilean-PSATD update (40-digit coefficients).
+"""
+import numpy as np
+import pytest
+import scipy.fft as sfft
+
+import galpic_inputs as gi
+from oracle import pic, problems
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1608_00215_gb300 import build
+    build.build()
+    from paper_1608_00215_gb300 import galpic
+    return galpic
+
+
+def _sample(p, idx):
+    return {"cell": p["cell"][idx].cpu().numpy(),
+            "off": [t[idx].double().cpu().numpy() for t in p["off"]],
+            "u": [t[idx].double().cpu().numpy() for t in p["u"]]}
+
+
+def test_bench_workload_sampled_parity(gp):
+    wl = gi.drifting_plasma(256, 256, 512, 130.0, galilean=True, shape_order=3, precision=32,
+                            ppc=(2, 2, 2), jitter=1e-3, seed=2)
+    cfg = problems.config_of(wl)
+    sim = gp.sim_from_workload(wl, precision=32, tile_margin=1)
+    sim.step(2)
+    sim.sort()
+    E = sim.get(gp.BUF_E, device="cpu").double().numpy()
+    B = sim.get(gp.BUF_B, device="cpu").double().numpy()
+    Eh0 = sim.get(gp.BUF_E_HAT)
+    Bh0 = sim.get(gp.BUF_B_HAT)
+    rh0 = sim.get(gp.BUF_RHO_HAT)
+    rng = np.random.default_rng(5)
+    before, idxs = [], []
+    for k in range(len(wl.species)):
+        p = sim.get_particles(k)
+        idx = torch.from_numpy(rng.choice(sim.n[k], 2048, replace=False)).cuda()
+        idxs.append(idx)
+        before.append(_sample(p, idx))
+        del p
+    torch.cuda.synchronize()
+
+    sim.gather_push()
+    J = sim.get(gp.BUF_J)
+    rho = sim.get(gp.BUF_RHO)
+    # particles: one by one against the oracle's gather, Boris and drift
+    sp_or, q_tot, j_tot, q_scale = [], 0.0, np.zeros(3), 0.0
+    for k, spec in enumerate(wl.species):
+        bf = before[k]
+        sp = problems.species_from_arrays(spec.q, spec.m, wl.weight(spec), bf["cell"], bf["off"], bf["u"],
+                                          wl.ny, wl.nz)
+        sp_or.append(sp)
+        p = sim.get_particles(k)
+        af = _sample(p, idxs[k])
+        # exact sums of charge and current over every particle of the species
+        u = torch.stack([t.double() for t in p["u"]])
+        gam = torch.sqrt(1 + (u * u).sum(0) / wl.c ** 2)
+        qw = spec.q * wl.weight(spec) / cfg.dV
+        q_tot += qw * sim.n[k]
+        j_tot += qw * (u / gam).sum(1).cpu().numpy()
+        q_scale += abs(qw) * sim.n[k]
+        del p, u, gam
+        sp.after = af
+    st = pic.State(sp_or, None, None, None, E, B)
+    vel = pic.push(cfg, st)
+    for sp, (vx, vy, vz) in zip(st.species, vel):
+        pic.drift(cfg, sp, vx, vy, vz, 0.5 * cfg.dt)
+        pic.drift(cfg, sp, vx, vy, vz, 0.5 * cfg.dt)
+        af = sp.after
+        cell = af["cell"].astype(np.int64)
+        ig = [cell // (wl.ny * wl.nz), (cell // wl.nz) % wl.ny, cell % wl.nz]
+        for d, (io, fo, n) in enumerate(((sp.ix, sp.fx, wl.nx), (sp.iy, sp.fy, wl.ny), (sp.iz, sp.fz, wl.nz))):
+            dd = np.abs((ig[d] + af["off"][d]) - (io + fo))
+            dd = np.minimum(dd, n - dd)
+            assert dd.max() < 1e-5, (d, dd.max())
+        ug = np.stack(af["u"])
+        uo = np.stack([sp.ux, sp.uy, sp.uz])
+        assert (np.linalg.norm(ug - uo, axis=0) / np.linalg.norm(uo, axis=0)).max() < 1e-5
+
+    # deposited totals: charge and current of every particle (the plasma is neutral,
+    # so both totals are cancellations; compare against one species' magnitude)
+    Q = float(rho.double().sum()) * cfg.dV
+    Jsum = J.double().sum(dim=(1, 2, 3)).cpu().numpy() * cfg.dV
+    assert abs(Q - q_tot * cfg.dV) < 1e-6 * q_scale * cfg.dV
+    assert np.abs(Jsum - j_tot * cfg.dV).max() < 1e-6 * q_scale * cfg.dV * wl.c
+
+    sim.field_update()
+    src = sim.get(gp.BUF_SRC_HAT)
+    Eh1 = sim.get(gp.BUF_E_HAT)
+    Bh1 = sim.get(gp.BUF_B_HAT)
+    torch.cuda.synchronize()
+    # forward FFT of the GPU's own real sources, whole grid
+    Jr = J.double().cpu().numpy()
+    for q in range(3):
+        want = sfft.rfftn(Jr[q], workers=-1)
+        got = src[q].to(torch.complex128).cpu().numpy()
+        assert np.linalg.norm(got - want) < 1e-5 * np.linalg.norm(want)
+    want = sfft.rfftn(rho.double().cpu().numpy(), workers=-1)
+    got = src[3].to(torch.complex128).cpu().numpy()
+    assert np.linalg.norm(got - want) < 1e-5 * np.linalg.norm(want)
+    del Jr, want, got
+
+    # sampled modes of the k-space update
+    nzh = wl.nz // 2 + 1
+    m = rng.choice(wl.nx * wl.ny * nzh, 512, replace=False)
+    mx, my, mz = m // (wl.ny * nzh), (m // nzh) % wl.ny, m % nzh
+    keep = (mx != wl.nx // 2) & (my != wl.ny // 2) & (mz != wl.nz // 2)
+    m, mx, my, mz = m[keep], mx[keep], my[keep], mz[keep]
+    kx = 2 * np.pi * np.fft.fftfreq(wl.nx, wl.dx)[mx]
+    ky = 2 * np.pi * np.fft.fftfreq(wl.ny, wl.dy)[my]
+    kz = 2 * np.pi * np.fft.rfftfreq(wl.nz, wl.dz)[mz]
+    mt = torch.from_numpy(m).cuda()
+
+    def pick(t, lead):
+        return t.reshape(lead, -1)[:, mt].to(torch.complex128).cpu().numpy() if lead else \
+            t.reshape(-1)[mt].to(torch.complex128).cpu().numpy()
+    E0, B0, r0 = pick(Eh0, 3), pick(Bh0, 3), pick(rh0, 0)
+    Jh, r1 = pick(src[:3], 3), pick(src[3], 0)
+    Jc = pic.current_correction(cfg, Jh, r0, r1, k=(kx, ky, kz))
+    E1, B1 = pic.field_update(cfg, E0, B0, Jc, r0, r1, k=(kx, ky, kz))
+    Eg, Bg = pick(Eh1, 3), pick(Bh1, 3)
+    assert np.linalg.norm(Eg - E1) < 1e-4 * np.linalg.norm(E1)
+    assert np.linalg.norm(Bg - B1) < 1e-4 * np.linalg.norm(B1)
+    sim.close()
