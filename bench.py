@@ -271,6 +271,7 @@ def run_ours(args, rank, world, local_rank):
 def serving_bench(n_req, steps, chunk=25, seed=4):
     """Continuous batching vs serial execution of independent runs on one GPU: a burst
     (all requests at t = 0) and a Poisson trace at twice the serial service rate."""
+    import torch
     import galpic_inputs as gi
     from paper_1608_00215_gb300 import serve
     wls = gi.serving_requests(n_req, seed=seed, steps=steps)
@@ -280,7 +281,10 @@ def serving_bench(n_req, steps, chunk=25, seed=4):
                     "1-8 ppc/species, FP32, linear shapes, seed 4"}
     serial = serve.serve(burst, max_slots=1, chunk=chunk)
     batched = serve.serve(burst, max_slots=64, chunk=chunk)
-    out["burst"] = {"serial": serial.summary(), "batched": batched.summary()}
+    even = serve.serve(burst, max_slots=64, chunk=chunk, priorities=False)
+    out["burst"] = {"serial": serial.summary(), "batched": batched.summary(),
+                    "batched_without_priorities": even.summary()}
+    out["stream_priority_range"] = list(torch.cuda.Stream.priority_range())
     mean_service = serial.makespan / max(1, n_req)
     arr = gi.poisson_arrivals(n_req, rate=2.0 / mean_service, seed=seed)
     trace = [serve.Request(i, wl, steps, float(a)) for i, (wl, a) in enumerate(zip(wls, arr))]
@@ -365,6 +369,57 @@ def long_run(args):
     print(json.dumps(out), flush=True)
 
 
+def lwfa_run(args):
+    """Boosted-frame laser-wakefield run (384x384x1536, gamma_boost = 10, a0 = 2 laser,
+    FP32, cubic): on-axis Ez and the field energy every `--lwfa-every` steps and the
+    time per step, on the Galilean grid and, with --lwfa-std, with v_gal = 0 beside it."""
+    import numpy as np
+    import torch
+    from paper_1608_00215_gb300 import build
+    build.build()
+    from paper_1608_00215_gb300 import galpic as gp
+    import galpic_inputs as gi
+    grid = tuple(int(x) for x in args.lwfa_grid.split(","))
+    out = {"mode": "lwfa_run", "grid": list(grid), "steps": args.steps, "every": args.lwfa_every,
+           "runs": {}}
+    for gal in ([True, False] if args.lwfa_std else [True]):
+        wl = gi.boosted_lwfa(*grid, galilean=gal, steps=args.steps)
+        t0 = time.perf_counter()
+        sim = gp.sim_from_workload(wl, precision=32, tile_margin=args.margin)
+        torch.cuda.synchronize()
+        init_s = time.perf_counter() - t0
+        xc, yc = wl.nx // 2, wl.ny // 2
+        W0 = sim.energy()
+        curve, ms = [], 0.0
+        done = 0
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        while done < args.steps:
+            n = min(args.lwfa_every, args.steps - done)
+            a.record(sim.stream)
+            sim.step(n)
+            b.record(sim.stream)
+            b.synchronize()
+            ms += a.elapsed_time(b)
+            done += n
+            E = sim.get(gp.BUF_E)
+            ez = E[2, xc, yc].double().cpu().numpy()
+            del E
+            W = sim.energy()
+            curve.append({"step": done, "W_over_W0": W / W0, "Ez_axis_max": float(np.abs(ez).max()),
+                          "Ez_axis_argmax_z": int(np.abs(ez).argmax()),
+                          "Ez_axis_rms": float(np.sqrt(np.mean(ez * ez)))})
+        cnt = sim.counters()
+        out["runs"]["galilean" if gal else "standard"] = {
+            "particles": wl.nparticles, "init_s": init_s, "ms_per_step": ms / args.steps,
+            "pushes_per_s": wl.nparticles * args.steps / (ms * 1e-3), "W0": W0, "curve": curve,
+            "sorts": cnt.get("sorts") if isinstance(cnt, dict) else None, "status": sim.status()}
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+
+
 def e2e_run(gp, wl, steps):
     import torch
     sim = gp.sim_from_workload(wl, precision=32)
@@ -427,6 +482,11 @@ def main():
     ap.add_argument("--long-run-every", type=int, default=100)
     ap.add_argument("--long-run-oracle", type=int, default=0,
                     help="also run the FP64 oracle for this many steps (small grids only)")
+    ap.add_argument("--lwfa", action="store_true",
+                    help="boosted-frame laser-wakefield run (on-axis Ez, field energy) instead")
+    ap.add_argument("--lwfa-grid", default="384,384,1536")
+    ap.add_argument("--lwfa-every", type=int, default=100)
+    ap.add_argument("--lwfa-std", action="store_true", help="also run the v_gal = 0 twin")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -436,6 +496,9 @@ def main():
         return
     if args.long_run:
         long_run(args)
+        return
+    if args.lwfa:
+        lwfa_run(args)
         return
     if world > 1:
         import torch

@@ -97,6 +97,7 @@ class Workload:
     current_correction: int = 1
     steps: int = 1
     seed: int = 1
+    laser: Optional["LaserSpec"] = None   # external field added to the initial state
 
     @property
     def ncells(self) -> int:
@@ -127,16 +128,19 @@ def drifting_plasma(nx: int, ny: int, nz: int, gamma: float, *, galilean: bool =
                     steps: int = 1, electron_only: bool = False,
                     name: Optional[str] = None, dx: float = 1.0, dy: float = 1.0,
                     dz: float = 1.0, dt: Optional[float] = None, c: float = 1.0,
-                    eps0: float = 1.0) -> Workload:
-    """Uniform electron(-proton) plasma drifting along +z at Lorentz factor ``gamma``.
+                    eps0: float = 1.0, direction: int = 1) -> Workload:
+    """Uniform electron(-proton) plasma drifting along +z (``direction`` = 1) or -z
+    (``direction`` = -1) at Lorentz factor ``gamma``.
 
     ``galilean`` selects v_gal = v_drift (True) or v_gal = 0 (False). With
     ``electron_only`` the protons are replaced by a uniform neutralising
     background charge that moves with the grid. The time step defaults to
     dt = dz / c.
     """
-    uz = drift_u(gamma, c)
-    vz = drift_v(gamma, c)
+    if direction not in (1, -1):
+        raise ValueError("direction must be +1 or -1")
+    uz = direction * drift_u(gamma, c)
+    vz = direction * drift_v(gamma, c)
     sp = [SpeciesSpec("electron", -1.0, 1.0, tuple(ppc), (0.0, 0.0, uz), jitter, n0)]
     rho_bg = 0.0
     if electron_only:
@@ -247,3 +251,109 @@ def serving_requests(n: int = 256, seed: int = 4, steps: int = 500,
                              name=f"run{r:03d}")
         out.append(wl)
     return out
+
+
+# ---------------------------------------------------------------------------
+# Boosted-frame laser-wakefield workload
+# ---------------------------------------------------------------------------
+
+@dataclass
+class LaserSpec:
+    """Gaussian laser pulse, linearly polarised along x, propagating along +z.
+
+    Its vector potential is A_x = (a0 m c / |q|) exp(-r^2/w0^2 - (z-z0)^2/L^2)
+    sin(k0 (z - z0)), r measured from the axis (xc, yc), at focus. The fields are
+    E = c dA_x/dz x_hat - c dA_x/dx z_hat and B = curl A = dA_x/dz y_hat - dA_x/dy z_hat,
+    a forward-travelling pulse whose E and B are both divergence-free.
+    """
+
+    a0: float            # peak normalised vector potential
+    waist: float         # w0 in units of dx
+    wavelength: float    # lambda in units of dz
+    length: float        # L (1/e half-length of the field envelope) in units of dz
+    z0: float            # centre along z, in units of dz
+    xc: float            # axis position, in units of dx / dy
+    yc: float
+    q: float = -1.0      # charge and mass of the particle a0 refers to (the electron)
+    m: float = 1.0
+
+
+# Lab-frame parameters of the paper's wakefield run: electron density 1e18 cm^-3 and
+# laser wavelength 800 nm give n_e / n_c = 1e18 / 1.742e21 (critical density at 800 nm).
+LAB_DENSITY_RATIO = 1e18 / 1.742e21
+
+
+def boosted_lwfa(nx: int = 384, ny: int = 384, nz: int = 1536, *, gamma_boost: float = 10.0,
+                 a0: float = 2.0, waist: float = 20.0, cells_per_lambda: float = 16.0,
+                 pulse_length: Optional[float] = None, ppc=(1, 1, 2), shape_order: int = 3,
+                 precision: int = 32, galilean: bool = True, jitter: float = 1e-3, seed: int = 3,
+                 steps: int = 2000, name: Optional[str] = None) -> Workload:
+    """Laser-wakefield run in a Lorentz-boosted frame: electrons streaming along -z at
+    gamma_boost over a background of immobile ions (a uniform charge static on the
+    grid, which moves with the plasma when ``galilean``), and a Gaussian laser pulse
+    travelling along +z. Cells are cubes of the boosted-frame wavelength / ``cells_per_lambda``.
+
+    The electron density follows from the paper's lab-frame plasma (n_e / n_c above):
+    the rest-frame plasma frequency is w_p = w0_lab sqrt(n_e/n_c) and the boosted
+    frame sees the laser at w0 = w0_lab / (gamma (1 + beta)), so w_p / w0 =
+    sqrt(n_e/n_c) gamma (1 + beta); the grid-frame density is gamma n_rest with
+    n_rest = eps0 m w_p^2 / q^2. The default pulse length is the paper's
+    c tau = 8 um = 10 lambda_lab stretched by gamma (1 + beta).
+    """
+    beta = drift_v(gamma_boost) / 1.0
+    dopp = gamma_boost * (1.0 + beta)
+    w0 = 2.0 * math.pi / cells_per_lambda          # boosted-frame laser frequency (c = dz = 1)
+    wp = w0 * math.sqrt(LAB_DENSITY_RATIO) * dopp
+    n_grid = gamma_boost * wp * wp                 # eps0 = m = |q| = 1
+    if pulse_length is None:
+        pulse_length = 10.0 * cells_per_lambda     # 8 um = 10 lambda_lab; both stretched by dopp
+    wl = drifting_plasma(nx, ny, nz, gamma_boost, galilean=galilean, shape_order=shape_order,
+                         precision=precision, ppc=ppc, n0=n_grid, jitter=jitter, seed=seed, steps=steps,
+                         electron_only=True, direction=-1,
+                         name=name or f"boosted_lwfa_{nx}x{ny}x{nz}_g{gamma_boost:g}")
+    wl.init_fields = 0          # neutral uniform plasma: zero plasma fields; the laser is added
+    wl.beta_init = (0.0, 0.0, 0.0)
+    wl.laser = LaserSpec(a0=a0, waist=waist, wavelength=cells_per_lambda, length=pulse_length,
+                         z0=nz / 2.0, xc=nx / 2.0, yc=ny / 2.0)
+    return wl
+
+
+def laser_box(wl: Workload, extent: float = 4.0, dtype=np.float64):
+    """Fields of ``wl.laser`` on the grid nodes where they are not negligible.
+
+    Returns ``(lo, E, B)``: ``lo`` = (x, y, z) node index of the box corner and
+    ``E``, ``B`` arrays of shape (3, bx, by, bz) for the nodes lo + (i, j, k) (taken
+    modulo the grid), over ``extent`` e-folding lengths of the envelope (the
+    envelope is below exp(-extent^2) outside; the box is clipped to one period).
+    """
+    L = wl.laser
+    amp = L.a0 * L.m * wl.c / abs(L.q)
+    k0 = 2.0 * math.pi / (L.wavelength * wl.dz)
+
+    def span(centre, half, n):
+        a = int(math.floor(centre - half))
+        b = int(math.ceil(centre + half)) + 1
+        if b - a >= n:
+            return 0, n
+        return a, b - a
+
+    x0, bx = span(L.xc, extent * L.waist, wl.nx)
+    y0, by = span(L.yc, extent * L.waist, wl.ny)
+    z0, bz = span(L.z0, extent * L.length, wl.nz)
+    x = (np.arange(x0, x0 + bx) - L.xc)[:, None, None] * wl.dx
+    y = (np.arange(y0, y0 + by) - L.yc)[None, :, None] * wl.dy
+    z = (np.arange(z0, z0 + bz) - L.z0)[None, None, :] * wl.dz
+    w = L.waist * wl.dx
+    ln = L.length * wl.dz
+    env = np.exp(-(x * x + y * y) / (w * w)) * np.exp(-(z * z) / (ln * ln))
+    s, co = np.sin(k0 * z), np.cos(k0 * z)
+    dAdz = amp * env * (k0 * co - 2.0 * z / (ln * ln) * s)
+    dAdx = amp * env * s * (-2.0 * x / (w * w))
+    dAdy = amp * env * s * (-2.0 * y / (w * w))
+    E = np.zeros((3, bx, by, bz), dtype=dtype)
+    B = np.zeros((3, bx, by, bz), dtype=dtype)
+    E[0] = wl.c * dAdz
+    E[2] = -wl.c * dAdx
+    B[1] = dAdz
+    B[2] = -dAdy
+    return (x0 % wl.nx, y0 % wl.ny, z0 % wl.nz), E, B

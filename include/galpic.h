@@ -192,6 +192,16 @@ int pic_get(pic_sim* sim, int which, void* dst, size_t bytes, void* stream);
  * from src (host or device). Setting E_HAT or B_HAT recomputes the real E, B. */
 int pic_set(pic_sim* sim, int which, const void* src, size_t bytes, void* stream);
 
+/* Add external real-space fields to E^n and B^n, e.g. the laser pulse of the
+ * boosted-frame wakefield runs (laser-plasma acceleration section of the paper).
+ * fields: 6 * nx*ny*nz reals of the run's precision (host or device), components
+ * Ex, Ey, Ez, Bx, By, Bz, each [nx][ny][nz] with z fastest; read, not kept. They
+ * are transformed with the forward FFT of the step, added to the spectral E, B
+ * (Nyquist modes stay zero) and the real E, B are recomputed. Particles, rho^n
+ * and the current are not touched. Errors: PIC_EINVAL for NULL arguments,
+ * PIC_ECUDA / PIC_ECUFFT from the copy or transforms. */
+int pic_add_fields(pic_sim* sim, const void* fields, void* stream);
+
 /* Copy one species' particles out (in the library's current order, which is
  * sorted by cell bin) to caller arrays (host or device). Any pointer may be
  * NULL to skip that array. */

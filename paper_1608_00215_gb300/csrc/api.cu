@@ -199,6 +199,18 @@ int exec_r2c(pic_sim* s, cudaStream_t st) {
     return PIC_OK;
 }
 
+// Forward transform of four real grids at `in` ([4][N]) into `out` ([4][M]).
+int exec_r2c_on(pic_sim* s, void* in, void* out, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(s->plans->mu);
+    GP_CUFFT(cufftSetWorkArea(s->plan_r2c, s->fftwork));
+    GP_CUFFT(cufftSetStream(s->plan_r2c, st));
+    if (s->cfg.precision == 64)
+        GP_CUFFT(cufftExecD2Z(s->plan_r2c, (cufftDoubleReal*)in, (cufftDoubleComplex*)out));
+    else
+        GP_CUFFT(cufftExecR2C(s->plan_r2c, (cufftReal*)in, (cufftComplex*)out));
+    return PIC_OK;
+}
+
 int exec_c2r(pic_sim* s, cudaStream_t st) {
     std::lock_guard<std::mutex> lk(s->plans->mu);
     GP_CUFFT(cufftSetWorkArea(s->plan_c2r, s->fftwork));
@@ -607,6 +619,23 @@ int pic_set(pic_sim* s, int which, const void* src, size_t bytes, void* stream) 
         GP_CHECK(launch_master_to_scratch(s, st));
         GP_CHECK(exec_c2r(s, st));
     }
+    return PIC_OK;
+}
+
+int pic_add_fields(pic_sim* s, const void* fields, void* stream) {
+    if (!s || !fields) return fail(PIC_EINVAL, "sim or fields is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t T = real_bytes(s);
+    const int64_t N = s->d.N, M = s->d.M;
+    // the real field grids are recomputed below, so they serve as the transform input
+    GP_CUDA(cudaMemcpyAsync(s->F, fields, 6 * N * T, cudaMemcpyDefault, st));
+    char* out = (char*)s->EBs;
+    GP_CHECK(exec_r2c_on(s, s->F, out, st));                                          // Ex Ey Ez Bx
+    GP_CHECK(exec_r2c_on(s, (char*)s->F + 2 * N * T, out + 2 * M * 2 * T, st));      // Ez Bx By Bz
+    count_launches(s, 2);
+    GP_CHECK(launch_add_spectra(s, s->EBs, st));
+    GP_CHECK(launch_master_to_scratch(s, st));
+    GP_CHECK(exec_c2r(s, st));
     return PIC_OK;
 }
 

@@ -176,6 +176,8 @@ int launch_build_tables(pic_sim* s, cudaStream_t st);
 int launch_kspace_update(pic_sim* s, cudaStream_t st);
 int launch_init_fields(pic_sim* s, cudaStream_t st);
 int launch_master_to_scratch(pic_sim* s, cudaStream_t st);
+// Adds six spectra (`add`, [6][M] complex) to the spectral master, Nyquist modes excluded.
+int launch_add_spectra(pic_sim* s, const void* add, cudaStream_t st);
 int launch_energy(pic_sim* s, double* out_dev, cudaStream_t st);
 // Energy kernels on caller-given fields (real [6][N]) and partial-sum storage.
 int launch_energy_on(const void* F, int64_t N, int precision, double* part, int nb, int32_t* status,

@@ -309,6 +309,21 @@ __global__ void init_fields_kernel(C* EBh, C* Rn, const C* Sh, int64_t M, int nx
     }
 }
 
+// Spectral master += added spectra (six components), Nyquist modes left at zero.
+template <typename C>
+__global__ void add_spectra_kernel(C* EBh, const C* add, int64_t M, int nx, int ny, int nz, int nzh) {
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M;
+         m += (int64_t)gridDim.x * blockDim.x) {
+        const int mz = (int)(m % nzh);
+        const int64_t r = m / nzh;
+        const int my = (int)(r % ny);
+        const int mx = (int)(r / ny);
+        if (is_nyquist(mx, my, mz, nx, ny, nz)) continue;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) EBh[q * M + m] = cadd(EBh[q * M + m], add[q * M + m]);
+    }
+}
+
 template <typename C, typename T>
 __global__ void scale_copy_kernel(C* dst, const C* src, int64_t n, T s) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -451,6 +466,18 @@ int launch_init_fields(pic_sim* s, cudaStream_t st) {
             (float2*)s->EBh, (float2*)s->Rn, (const float2*)s->Sh, s->d.M, s->d.nx, s->d.ny,
             s->d.nz, s->d.nzh, kfx, kfy, kfz, c.beta_init[0], c.beta_init[1], c.beta_init[2], c.c,
             c.eps0, c.init_fields);
+    GP_CUDA(cudaGetLastError());
+    return PIC_OK;
+}
+
+int launch_add_spectra(pic_sim* s, const void* add, cudaStream_t st) {
+    int grid = grid_for(s->d.M, 256);
+    if (s->cfg.precision == 64)
+        add_spectra_kernel<double2><<<grid, 256, 0, st>>>((double2*)s->EBh, (const double2*)add, s->d.M,
+                                                          s->d.nx, s->d.ny, s->d.nz, s->d.nzh);
+    else
+        add_spectra_kernel<float2><<<grid, 256, 0, st>>>((float2*)s->EBh, (const float2*)add, s->d.M,
+                                                         s->d.nx, s->d.ny, s->d.nz, s->d.nzh);
     GP_CUDA(cudaGetLastError());
     return PIC_OK;
 }

@@ -12,6 +12,7 @@ import os
 from ctypes import POINTER, c_char_p, c_double, c_int, c_int32, c_int64, c_size_t, c_uint64, c_void_p
 from typing import Dict, List, Optional, Sequence
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -67,6 +68,7 @@ def _load():
         "pic_diag_energy": (c_int, [P, P, P]),
         "pic_get": (c_int, [P, c_int, P, c_size_t, P]),
         "pic_set": (c_int, [P, c_int, P, c_size_t, P]),
+        "pic_add_fields": (c_int, [P, P, P]),
         "pic_get_particles": (c_int, [P, c_int, P, POINTER(P), POINTER(P), P]),
         "pic_set_particles": (c_int, [P, c_int, P, POINTER(P), POINTER(P), P]),
         "pic_sort": (c_int, [P, P]),
@@ -91,7 +93,7 @@ EXPORTS = ("pic_version", "pic_last_error", "pic_footprint", "pic_init", "pic_de
            "pic_gather_push", "pic_field_update", "pic_step", "pic_step_many", "pic_diag_energy",
            "pic_get", "pic_set", "pic_get_particles", "pic_set_particles", "pic_status",
            "pic_counters", "pic_sizes", "pic_profile", "pic_profile_read", "pic_sort",
-           "pic_field_energy_noalloc")
+           "pic_field_energy_noalloc", "pic_add_fields")
 
 STAGES = ("sort", "particles", "fft_r2c", "kspace", "fft_c2r", "energy")
 
@@ -217,6 +219,15 @@ class Sim:
                           _stream_ptr(self.stream)))
         self._pending = src
 
+    def add_fields(self, EB: torch.Tensor):
+        """Add real-space fields EB = [Ex, Ey, Ez, Bx, By, Bz] (shape (6, nx, ny, nz),
+        the run's real dtype, host or device) to E^n, B^n."""
+        if tuple(EB.shape) != (6, self.cfg.nx, self.cfg.ny, self.cfg.nz) or EB.dtype != self.real:
+            raise ValueError(f"fields must be (6, nx, ny, nz) of {self.real}")
+        EB = EB.contiguous()
+        check(lib.pic_add_fields(self.handle, c_void_p(EB.data_ptr()), _stream_ptr(self.stream)))
+        self._pending = EB
+
     def get_particles(self, k: int, device=None) -> Dict[str, torch.Tensor]:
         dev = device or self.device
         n = self.n[k]
@@ -306,4 +317,21 @@ def sim_from_workload(wl, precision: Optional[int] = None, stream=None, device="
     for k, s in enumerate(wl.species):
         w = s.density * wl.dx * wl.dy * wl.dz / (s.ppc[0] * s.ppc[1] * s.ppc[2])
         sp.append(generated_species(s.q, s.m, w, ncells, s.ppc, s.u0, s.jitter, wl.seed, k))
-    return Sim(cfg, sp, stream=stream, device=device)
+    sim = Sim(cfg, sp, stream=stream, device=device)
+    if getattr(wl, "laser", None) is not None:
+        add_laser(sim, wl)
+    return sim
+
+
+def add_laser(sim: "Sim", wl):
+    """Add the workload's laser pulse (fields from ``galpic_inputs.laser_box``) to a run."""
+    import galpic_inputs as gi
+    (x0, y0, z0), E, B = gi.laser_box(wl)
+    EB = torch.zeros((6, wl.nx, wl.ny, wl.nz), dtype=sim.real, device=sim.device)
+    box = torch.from_numpy(np.concatenate([E, B])).to(sim.real).to(sim.device)
+    ix = (torch.arange(E.shape[1], device=sim.device) + x0) % wl.nx
+    iy = (torch.arange(E.shape[2], device=sim.device) + y0) % wl.ny
+    iz = (torch.arange(E.shape[3], device=sim.device) + z0) % wl.nz
+    EB[:, ix[:, None, None], iy[None, :, None], iz[None, None, :]] = box
+    sim.add_fields(EB)
+    return EB

@@ -8,6 +8,10 @@ resident until it finishes. Every admitted run owns a CUDA stream, so the
 kernels of different runs overlap on the device; the scheduler advances each
 run in chunks of graph-replayed steps (``pic_step``) and polls events to
 retire finished runs and admit new ones while others are still on the GPU.
+Streams carry a priority class from the run's total particle pushes, so the
+block scheduler starts the kernels of small runs ahead of the queued blocks of
+large ones: a small run admitted beside a large one finishes in about its own
+time instead of sharing the device evenly with it.
 
 All compute goes through the CUDA library (``galpic``); this module is host
 scheduling only.
@@ -42,6 +46,7 @@ class RunRecord:
     energy: float = math.nan
     status: int = 0
     error: Optional[str] = None
+    priority: int = 0
 
     @property
     def latency(self) -> float:
@@ -76,6 +81,30 @@ def footprint(wl, precision: Optional[int] = None) -> int:
     return int(n.value)
 
 
+# Priority classes by total particle pushes (particles x steps): below 2^24,
+# 2^27, 2^30 pushes a run gets 3, 2, 1 levels above the largest runs.
+PRIORITY_BOUNDS = (1 << 24, 1 << 27, 1 << 30)
+
+
+def pushes(wl, steps: int) -> int:
+    """Particle pushes of a run: particles (cells x particles per cell, all species) x steps."""
+    cells = wl.nx * wl.ny * wl.nz
+    per_cell = sum(s.ppc[0] * s.ppc[1] * s.ppc[2] for s in wl.species)
+    return cells * per_cell * steps
+
+
+def priority_level(work: int) -> int:
+    """Levels above the lowest priority class (0 for the largest runs)."""
+    return sum(1 for b in PRIORITY_BOUNDS if work < b)
+
+
+def stream_priority(level: int, prange) -> int:
+    """CUDA stream priority for a level; prange = (least, greatest) as CUDA reports it
+    (lower numbers are higher priorities)."""
+    least, greatest = prange
+    return max(greatest, least - level)
+
+
 @dataclass
 class ServeResult:
     records: List[RunRecord]
@@ -108,12 +137,15 @@ class ServeResult:
 
 def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_slots: int = 64,
           chunk: int = 25, precision: Optional[int] = None, device: str = "cuda",
-          sleep: float = 2e-4, keep_final_state: bool = False, on_retire=None) -> ServeResult:
+          sleep: float = 2e-4, keep_final_state: bool = False, on_retire=None,
+          priorities: bool = True) -> ServeResult:
     """Run all requests with continuous batching; returns per-run records.
 
     ``max_slots = 1`` gives the serial baseline on the same arrival trace.
     ``hbm_budget`` defaults to 90 % of the free device memory at the start.
+    ``priorities``: give each run's stream the priority class of its size.
     """
+    prange = torch.cuda.Stream.priority_range() if priorities else (0, 0)
     if hbm_budget is None:
         free, _ = torch.cuda.mem_get_info()
         hbm_budget = int(0.9 * free)
@@ -135,7 +167,9 @@ def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_
     max_conc = 0
     t0 = time.perf_counter()
     qi = 0
-    while qi < len(queue) or active:
+    work = {r.rid: pushes(r.workload, r.steps) for r in queue}
+    waiting: List[Request] = []
+    while qi < len(queue) or active or waiting:
         now = time.perf_counter() - t0
         # retire or advance
         for a in list(active):
@@ -158,29 +192,39 @@ def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_
                 a.event = torch.cuda.Event()
                 a.event.record(a.stream)
             a.done += n
-        # admit: arrived, slot free, footprint fits
-        while qi < len(queue) and len(active) < max_slots and queue[qi].arrival <= now:
-            r = queue[qi]
+        # admit: arrived, slot free, footprint fits; with priorities the waiting runs
+        # are taken smallest first (a run that does not fit waits, smaller ones go on)
+        while qi < len(queue) and queue[qi].arrival <= now:
+            waiting.append(queue[qi])
+            qi += 1
+        if priorities and len(waiting) > 1:
+            waiting.sort(key=lambda r: (work[r.rid], r.arrival))
+        wi = 0
+        while wi < len(waiting) and len(active) < max_slots:
+            r = waiting[wi]
             if used + fps[r.rid] > hbm_budget:
-                break
+                if not priorities:
+                    break
+                wi += 1
+                continue
+            waiting.pop(wi)
             rec = records[r.rid]
-            stream = torch.cuda.Stream()
+            rec.priority = stream_priority(priority_level(pushes(r.workload, r.steps)), prange)
+            stream = torch.cuda.Stream(priority=rec.priority)
             try:
                 with torch.cuda.stream(stream):
                     sim = gp.sim_from_workload(r.workload, precision=precision, stream=stream, device=device)
             except Exception as e:            # allocation or validation failure: reject this run only
                 rec.error = str(e)
-                qi += 1
                 continue
             rec.start = time.perf_counter() - t0
             used += fps[r.rid]
             active.append(_Active(r, sim, stream, 0, None, rec,
                                   torch.zeros(1, dtype=torch.int32).pin_memory()))
             max_conc = max(max_conc, len(active))
-            qi += 1
         if active and all(a.event is not None and not a.event.query() for a in active):
             time.sleep(sleep)
-        elif not active and qi < len(queue):
+        elif not active and not waiting and qi < len(queue):
             wait = queue[qi].arrival - (time.perf_counter() - t0)
             if wait > 0:
                 time.sleep(min(wait, 0.01))

@@ -1,8 +1,10 @@
-"""Parity at the full size and launch configuration that bench.py times:
+"""Parity at full size in the launch configuration that bench.py times:
 256x256x512 cells, 536,870,912 particles, gamma = 130 e-p plasma, cubic shapes,
-FP32 with FP64-built tables, tile margin 1.
+FP32 with FP64-built tables, tile margin 1; and the boosted-frame wakefield run
+(384x384x1536 cells, 452,984,832 electrons streaming at gamma = 10 over immobile
+ions, Gaussian laser a0 = 2), cubic, FP32.
 
-The oracle cannot step this size, so it checks sampled outputs one by one and
+The oracle cannot step these sizes, so it checks sampled outputs one by one and
 properties that hold at any size:
   * 2048 particles per species: gather from the GPU's E, B, Boris push and both
     Galilean half drifts against the oracle's functions;
@@ -41,8 +43,16 @@ def _sample(p, idx):
 def test_bench_workload_sampled_parity(gp):
     wl = gi.drifting_plasma(256, 256, 512, 130.0, galilean=True, shape_order=3, precision=32,
                             ppc=(2, 2, 2), jitter=1e-3, seed=2)
+    _sampled_parity(gp, wl, margin=1)
+
+
+def test_boosted_lwfa_sampled_parity(gp):
+    _sampled_parity(gp, gi.boosted_lwfa(steps=2), margin=0)
+
+
+def _sampled_parity(gp, wl, margin):
     cfg = problems.config_of(wl)
-    sim = gp.sim_from_workload(wl, precision=32, tile_margin=1)
+    sim = gp.sim_from_workload(wl, precision=32, tile_margin=margin)
     sim.step(2)
     sim.sort()
     E = sim.get(gp.BUF_E, device="cpu").double().numpy()
