@@ -117,6 +117,39 @@ def particle_bytes(wl, precision):
     return P * 2 * (4 + 6 * T) + N * (6 * T + 4 * T)
 
 
+def particle_flops(order):
+    """Algorithmic FP32 flops of one particle in the particle pass (FMA = 2 flops), with
+    NW = 2 (linear) or 4 (quadratic, cubic) stencil nodes per axis:
+      shape weights  9 evaluations (3 positions x 3 axes): 4 flops (linear) / 18 (cubic);
+      gather         NW^2 x-y products, then per node one product and 6 FMAs;
+      Boris + 1/gamma 90; two half drifts 3 x 2 x 8 = 48;
+      deposit J      NW^2 x-y products, per node one product and 3 FMAs, 3 values q w v;
+      deposit rho    NW^2 x-y products, per node one product and one add."""
+    nw = 2 if order == 1 else 4
+    weights = 9 * (4 if order == 1 else 18)
+    gather = nw * nw + nw ** 3 * (1 + 12)
+    deposit = (nw * nw + nw ** 3 * (1 + 6) + 3) + (nw * nw + nw ** 3 * 2)
+    return weights + gather + 90 + 48 + deposit
+
+
+def fp32_peak_tflops():
+    """FP32 peak of the GPU from its unit counts and clock: 152 SMs x 128 FP32 lanes x
+    2 flops (FMA) x the maximum SM clock (2070 MHz unless MEASURED_PEAKS.json says otherwise)."""
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    except Exception:
+        pass
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+
+
+# DRAM bytes per particle and per cell of one particle-pass launch, from the ncu
+# capture summarised in profiles/particle_pass_cubic_fp32_64x64x128.md (current
+# kernel); scaled to a launch by the particles and cells it processes.
+PASS_TRAFFIC = {}
+
+
 def kspace_bytes(wl, precision):
     """Algorithmic HBM bytes of one k-space update: reads E, B, J, rho^{n+1}, rho^n and six
     factors; writes E, B twice (master and inverse-FFT copy) and rho^n (complex)."""
@@ -235,6 +268,18 @@ def run_ours(args, rank, world, local_rank):
     achieved = particle_bytes(wl, 32) / (part_ms * 1e-3) / 1e9
     ks_achieved = kspace_bytes(wl, 32) / (ks_ms * 1e-3) / 1e9
     value = P * args.steps * world / (ms_max * 1e-3)
+    kname = f"particle_pass_kernel<float,{args.order},STEP,{args.margin}>"
+    tr = PASS_TRAFFIC.get((args.order, 32, args.margin))
+    traffic = None if tr is None else tr[0] * P + tr[1] * N
+    roof_hbm = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": particle_bytes(wl, 32)}
+    fpk = fp32_peak_tflops()
+    flops = particle_flops(args.order) * P
+    alu = flops / (part_ms * 1e-3) / 1e12
+    roof_alu = {"bound": "alu", "kernel": kname, "achieved": alu, "peak": fpk, "unit": "TFLOP/s",
+                "frac": alu / fpk, "traffic": traffic, "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                "algorithmic_flops_per_launch": flops}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -246,10 +291,8 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "inputs larger than L2 (15 GB of particles, 0.8 GB of fields); no flush"},
         "cell_updates_per_s": N * args.steps * world / (ms_max * 1e-3),
         "stages_ms_per_step": {k: v["ms"] / max(1, v["count"]) for k, v in stages.items() if v["count"]},
-        "roofline": {"bound": "hbm", "kernel": f"particle_pass_kernel<float,{args.order},STEP>", "achieved": achieved,
-                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-                     "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_launch": particle_bytes(wl, 32)},
+        "roofline": roof_alu if args.order > 1 else roof_hbm,
+        "roofline_hbm" if args.order > 1 else "roofline_alu": roof_hbm if args.order > 1 else roof_alu,
         "roofline_kspace": {"bound": "hbm", "achieved": ks_achieved, "peak": hbm, "unit": "GB/s",
                             "frac": ks_achieved / hbm},
         "gpu_launches": launches,
@@ -317,9 +360,10 @@ def torch_c128():
 
 def long_run(args):
     """FP32 (int cell + FP32 offset) against FP64 on the GPU for the gamma = 130 Galilean
-    plasma: field-energy drift, continuity residual of the deposited sources and the
-    relative L2 difference of E, B, every `--long-run-every` steps; the FP64 oracle
-    beside both for the first `--long-run-oracle` steps at the oracle-sized grid."""
+    plasma (linear shapes) at `--grid`: field-energy drift, continuity residual of the
+    deposited sources and the relative L2 difference of E, B every `--long-run-every`
+    steps. Beside it, both precisions against the FP64 oracle for `--long-run-oracle`
+    steps at the oracle-sized `--long-run-oracle-grid`."""
     import numpy as np
     import torch
     from paper_1608_00215_gb300 import build
@@ -329,24 +373,46 @@ def long_run(args):
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     import helpers
     import galpic_inputs as gi
+
+    def rel(E, B, E0, B0):
+        return float(np.linalg.norm(np.concatenate([(E - E0).ravel(), (B - B0).ravel()])) /
+                     max(np.linalg.norm(np.concatenate([E0.ravel(), B0.ravel()])), 1e-300))
+
     grid = tuple(int(x) for x in args.grid.split(","))
+    out = {"mode": "long_run", "grid": list(grid), "steps": args.steps, "every": args.long_run_every}
+    if args.long_run_oracle > 0:
+        og = tuple(int(x) for x in args.long_run_oracle_grid.split(","))
+        wlo = gi.drifting_plasma(*og, GAMMA, galilean=True, shape_order=1, precision=64, seed=1)
+        o32 = gp.sim_from_workload(wlo, precision=32)
+        o64 = gp.sim_from_workload(wlo, precision=64)
+        cfg, st = helpers.oracle_state_from_sim(o64, wlo)
+        t1 = time.perf_counter()
+        for _ in range(args.long_run_oracle):
+            pic.step(cfg, st)
+        t_or = time.perf_counter() - t1
+        o32.step(args.long_run_oracle)
+        o64.step(args.long_run_oracle)
+        E32, B32 = helpers.gpu_fields(o32)
+        E64, B64 = helpers.gpu_fields(o64)
+        out["oracle_check"] = {"grid": list(og), "particles": wlo.nparticles, "steps": args.long_run_oracle,
+                               "relL2_fp64_vs_oracle": rel(E64, B64, st.E, st.B),
+                               "relL2_fp32_vs_oracle": rel(E32, B32, st.E, st.B),
+                               "W_fp64_over_oracle": o64.energy() / pic.energy(cfg, st.E, st.B),
+                               "oracle_seconds": t_or}
+        o32.close()
+        o64.close()
+        del o32, o64
+        torch.cuda.empty_cache()
     wl = gi.drifting_plasma(*grid, GAMMA, galilean=True, shape_order=1, precision=64, seed=1)
     s32 = gp.sim_from_workload(wl, precision=32)
     s64 = gp.sim_from_workload(wl, precision=64)
-    out = {"mode": "long_run", "grid": list(grid), "particles": wl.nparticles, "steps": args.steps,
-           "every": args.long_run_every, "curve": []}
-    if args.long_run_oracle > 0:
-        cfg, st = helpers.oracle_state_from_sim(s64, wl)
-        ref = {}
-        for k in range(args.long_run_oracle):
-            pic.step(cfg, st)
-        ref["E"], ref["B"] = st.E, st.B
+    out["particles"] = wl.nparticles
+    out["curve"] = []
     W0_32, W0_64 = s32.energy(), s64.energy()
     t0 = time.perf_counter()
     done = 0
     while done < args.steps:
-        seg = args.long_run_oracle if (done == 0 and args.long_run_oracle > 0) else args.long_run_every
-        n = min(seg, args.steps - done)
+        n = min(args.long_run_every, args.steps - done)
         s32.step(n - 1)
         s64.step(n - 1)
         rho32 = s32.get(gp.BUF_RHO_HAT, device="cpu").to(torch.complex128).numpy()
@@ -355,17 +421,12 @@ def long_run(args):
         done += n
         E32, B32 = helpers.gpu_fields(s32)
         E64, B64 = helpers.gpu_fields(s64)
-        d = float(np.linalg.norm(np.concatenate([(E32 - E64).ravel(), (B32 - B64).ravel()])) /
-                  max(np.linalg.norm(np.concatenate([E64.ravel(), B64.ravel()])), 1e-300))
-        row = {"step": done, "W32_over_W0": s32.energy() / W0_32, "W64_over_W0": s64.energy() / W0_64,
-               "relL2_E_B_fp32_vs_fp64": d, "continuity_residual_fp32": continuity_residual(gp, s32, rho32, wl)}
-        if args.long_run_oracle and done == args.long_run_oracle:
-            row["relL2_fp64_vs_oracle"] = float(np.linalg.norm(np.concatenate([(E64 - ref["E"]).ravel(), (B64 - ref["B"]).ravel()])) /
-                                                np.linalg.norm(np.concatenate([ref["E"].ravel(), ref["B"].ravel()])))
-            row["relL2_fp32_vs_oracle"] = float(np.linalg.norm(np.concatenate([(E32 - ref["E"]).ravel(), (B32 - ref["B"]).ravel()])) /
-                                                np.linalg.norm(np.concatenate([ref["E"].ravel(), ref["B"].ravel()])))
-        out["curve"].append(row)
+        out["curve"].append({"step": done, "W32_over_W0": s32.energy() / W0_32,
+                             "W64_over_W0": s64.energy() / W0_64,
+                             "relL2_E_B_fp32_vs_fp64": rel(E32, B32, E64, B64),
+                             "continuity_residual_fp32": continuity_residual(gp, s32, rho32, wl)})
     out["seconds"] = time.perf_counter() - t0
+    out["status"] = [s32.status(), s64.status()]
     print(json.dumps(out), flush=True)
 
 
@@ -481,7 +542,8 @@ def main():
                     help="FP32 vs FP64 long-run precision study instead of the throughput line")
     ap.add_argument("--long-run-every", type=int, default=100)
     ap.add_argument("--long-run-oracle", type=int, default=0,
-                    help="also run the FP64 oracle for this many steps (small grids only)")
+                    help="also compare both precisions with the FP64 oracle for this many steps")
+    ap.add_argument("--long-run-oracle-grid", default="32,32,64", help="grid of the oracle comparison")
     ap.add_argument("--lwfa", action="store_true",
                     help="boosted-frame laser-wakefield run (on-axis Ez, field energy) instead")
     ap.add_argument("--lwfa-grid", default="384,384,1536")

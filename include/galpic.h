@@ -192,6 +192,15 @@ int pic_get(pic_sim* sim, int which, void* dst, size_t bytes, void* stream);
  * from src (host or device). Setting E_HAT or B_HAT recomputes the real E, B. */
 int pic_set(pic_sim* sim, int which, const void* src, size_t bytes, void* stream);
 
+/* Re-sort policy. Particles are kept sorted by bin so that a CTA finds them in its
+ * shared-memory tile; a particle outside the tile takes a slower global-memory path
+ * (correct at any distance). The pass counts particles outside their bin and
+ * outside their tile; the next pass re-sorts first when the first count exceeds
+ * home_miss_threshold or the second exceeds far_threshold (defaults: 1/32 and
+ * 1/1024 of all particles). A negative value keeps that threshold. Asynchronous on
+ * `stream`. Errors: PIC_EINVAL (NULL sim), PIC_ECUDA. */
+int pic_sort_policy(pic_sim* sim, int64_t home_miss_threshold, int64_t far_threshold, void* stream);
+
 /* Add external real-space fields to E^n and B^n, e.g. the laser pulse of the
  * boosted-frame wakefield runs (laser-plasma acceleration section of the paper).
  * fields: 6 * nx*ny*nz reals of the run's precision (host or device), components

@@ -453,9 +453,12 @@ int pic_init(const pic_config* cfg, const pic_species* species, int nspecies, vo
     {
         int64_t ntot = 0;
         for (int k = 0; k < nspecies; ++k) ntot += n[k];
-        static thread_local unsigned long long thr;
-        thr = (unsigned long long)std::max<int64_t>(0, ntot / 32);
-        INIT_TRY(cudaMemcpyAsync(s->cnt + CNT_THRESHOLD, &thr, sizeof(thr), cudaMemcpyHostToDevice,
+        // re-sort when more than 1/32 of the particles left their bin or more than
+        // 1/1024 left their tile (a pageable source is staged before the copy returns)
+        static thread_local unsigned long long thr[2];
+        thr[0] = (unsigned long long)std::max<int64_t>(0, ntot / 32);
+        thr[1] = (unsigned long long)std::max<int64_t>(0, ntot / 1024);
+        INIT_TRY(cudaMemcpyAsync(s->cnt + CNT_THRESHOLD, thr, sizeof(thr), cudaMemcpyHostToDevice,
                                  st) == cudaSuccess ? PIC_OK : fail(PIC_ECUDA, "threshold"));
     }
     const size_t Tb = real_bytes(s);
@@ -620,6 +623,21 @@ int pic_set(pic_sim* s, int which, const void* src, size_t bytes, void* stream) 
         GP_CHECK(exec_c2r(s, st));
     }
     return PIC_OK;
+}
+
+int pic_sort_policy(pic_sim* s, int64_t home_miss_threshold, int64_t far_threshold, void* stream) {
+    if (!s) return fail(PIC_EINVAL, "sim is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    static thread_local unsigned long long v[2];
+    if (home_miss_threshold >= 0) {
+        v[0] = (unsigned long long)home_miss_threshold;
+        GP_CUDA(cudaMemcpyAsync(s->cnt + CNT_THRESHOLD, &v[0], sizeof(v[0]), cudaMemcpyHostToDevice, st));
+    }
+    if (far_threshold >= 0) {
+        v[1] = (unsigned long long)far_threshold;
+        GP_CUDA(cudaMemcpyAsync(s->cnt + CNT_FAR_THRESHOLD, &v[1], sizeof(v[1]), cudaMemcpyHostToDevice, st));
+    }
+    return PIC_OK;   // pageable sources are staged before the copies return
 }
 
 int pic_add_fields(pic_sim* s, const void* fields, void* stream) {

@@ -72,13 +72,16 @@ enum {
     CNT_HOME_MISS = 2,    // particles outside their bin after the last pass
     CNT_FAR = 3,          // particles that took the out-of-tile path in the last pass
     CNT_THRESHOLD = 4,    // re-sort when HOME_MISS exceeds this
+    CNT_FAR_THRESHOLD = 5,   // re-sort when FAR exceeds this
     CNT_COUNT = 8
 };
 
 // Decision shared by every re-sort kernel: identical for all of them because
 // none of them writes the words it reads (the final kernel clears FORCE last).
+// Particles outside their tile are handled correctly by the global-memory path at
+// any distance, so a re-sort is only a matter of speed.
 __device__ __forceinline__ bool sort_needed(const unsigned long long* cnt) {
-    return cnt[CNT_FORCE_SORT] != 0ull || cnt[CNT_FAR] != 0ull ||
+    return cnt[CNT_FORCE_SORT] != 0ull || cnt[CNT_FAR] > cnt[CNT_FAR_THRESHOLD] ||
            cnt[CNT_HOME_MISS] > cnt[CNT_THRESHOLD];
 }
 

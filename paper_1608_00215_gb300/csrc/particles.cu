@@ -193,9 +193,11 @@ __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) / 16 * 
 // aligned and puts consecutive rows two banks apart, so the up-to-16 distinct rows a
 // warp reads at one lane index hit distinct banks; a lane's stores to its own column
 // are contiguous across the warp.
+// Linear stencils (NW = 2) add a flag row and rows of the x^{n+1} (rho) weights for
+// the combined J and rho deposit.
 template <typename T, int NW> struct Stage {
     static constexpr int RS = 34;
-    static constexpr int ROWS = 3 + 3 * NW;
+    static constexpr int ROWS = NW == 2 ? 4 + 6 * NW : 3 + 3 * NW;
     static constexpr size_t BYTES = align16((size_t)ROWS * RS * sizeof(T));   // per warp
     T* base;
     __device__ T* row(int r) const { return base + r * RS; }
@@ -203,6 +205,10 @@ template <typename T, int NW> struct Stage {
     __device__ T* xrow(int a) const { return row(3 + a); }
     __device__ T* yrow(int b) const { return row(3 + NW + b); }
     __device__ T* zrow(int c) const { return row(3 + 2 * NW + c); }
+    __device__ T* frow() const { return row(3 + 3 * NW); }
+    __device__ T* xRrow(int a) const { return row(4 + 3 * NW + a); }
+    __device__ T* yRrow(int b) const { return row(4 + 4 * NW + b); }
+    __device__ T* zRrow(int c) const { return row(4 + 5 * NW + c); }
 };
 
 __host__ __device__ constexpr size_t stage_bytes(int NW, size_t T) {
@@ -460,6 +466,61 @@ __device__ void group_deposit(T* sD, const Stage<T, NW>& stg, bool member, int k
     }
 }
 
+// Combined J and rho deposit of one warp for linear stencils (NW = 2). Members are
+// grouped by the start `key` of their J stencil; lane q * 8 + j takes component q
+// (Jx, Jy, Jz, rho) at node j = (a, b, c) of the 2x2x2 stencil, so every lane works
+// on every group. The rho lanes read the x^{n+1} weights and, as the value, the
+// member's flag: 1 when its rho stencil starts at its J stencil's node (the normal
+// case), 0 otherwise (that member's rho goes through a separate rho-only pass).
+// Every lane of the warp must call this (warp-collective).
+template <typename T, int TE>
+__device__ void group_deposit_jr(T* sD, const Stage<T, 2>& stg, bool member, int key, int lane, T qw) {
+    typedef typename Pair<T>::type P2;
+    constexpr int R = TE * TE * TE;
+    const int q = lane >> 3, j = lane & 7;
+    const int ax = j >> 2, by = (j >> 1) & 1, cz = j & 1;
+    const bool rho = q == 3;
+    const T* xa = rho ? stg.xRrow(ax) : stg.xrow(ax);
+    const T* yb = rho ? stg.yRrow(by) : stg.yrow(by);
+    const T* zc = rho ? stg.zRrow(cz) : stg.zrow(cz);
+    const T* vq = rho ? stg.frow() : stg.vrow(q);
+    T* const dst = sD + q * R + (ax * TE + by) * TE + cz;
+    unsigned pending = __ballot_sync(0xffffffffu, member);
+    while (pending) {
+        const int leader = __ffs(pending) - 1;
+        const int gkey = __shfl_sync(0xffffffffu, key, leader);
+        const unsigned grp = __ballot_sync(0xffffffffu, member && key == gkey);
+        pending &= ~grp;
+        const int lo = __ffs(grp) - 1;
+        const int len = __popc(grp);
+        const bool run = (grp >> lo) == (len == 32 ? 0xffffffffu : ((1u << len) - 1u));   // warp-uniform
+        P2 A = Pair<T>::make((T)0, (T)0);
+        if (run) {
+            int m = lo;
+            const int me = lo + len;
+            if (m & 1) {
+                A.x = fma(xa[m] * yb[m] * zc[m], vq[m], A.x);
+                ++m;
+            }
+            for (; m + 1 < me; m += 2) {
+                const P2 w = pmul(pmul(ld2(xa + m), ld2(yb + m)), ld2(zc + m));
+                A = pfma(w, ld2(vq + m), A);
+            }
+            if (m < me) A.x = fma(xa[m] * yb[m] * zc[m], vq[m], A.x);
+        } else {
+            unsigned g = grp;
+            while (g) {
+                const int m = __ffs(g) - 1;
+                g &= g - 1;
+                A.x = fma(xa[m] * yb[m] * zc[m], vq[m], A.x);
+            }
+        }
+        T* addr[1] = {dst + gkey};
+        const T val[1] = {(A.x + A.y) * qw};
+        smem_add_batch<T, 1>(addr, val);
+    }
+}
+
 // Stage this lane's weights (and, for J, its velocity) in its column of the rows.
 template <typename T, int NW>
 __device__ __forceinline__ void stage_record(const Stage<T, NW>& stg, int lane, const T* wx, const T* wy,
@@ -477,7 +538,7 @@ __device__ __forceinline__ void stage_record(const Stage<T, NW>& stg, int lane, 
 }
 
 template <typename T, int ORDER, int MODE, int MARGIN>
-__global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p) {
+__device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
     typedef Shape<ORDER> SH;
     typedef typename Pair<T>::type P2;
     constexpr int NW = SH::NW;
@@ -639,6 +700,75 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
             }
             // ---- deposit J (phase 0: at x^{n+1/2} with v^{n+1/2}) and rho (phase 1:
             // at x^{n+1}); DEPOSIT mode: both at the current x
+            if constexpr (NW == 2) {
+                // linear: both stencils first, then one combined pass (see group_deposit_jr)
+                bool mJ = false, mR = false, same = false;
+                int keyJ = 0, keyR = 0;
+                T wxR[2], wyR[2], wzR[2];
+                if (valid) {
+                    if (MODE == PASS_STEP) {
+                        rx += drift_axis(ix, fx, (vx - p.vgal[0]) * p.hd[0], p.nx);
+                        ry += drift_axis(iy, fy, (vy - p.vgal[1]) * p.hd[1], p.ny);
+                        rz += drift_axis(iz, fz, (vz - p.vgal[2]) * p.hd[2], p.nz);
+                    }
+                    SH::w(fx, wx);
+                    SH::w(fy, wy);
+                    SH::w(fz, wz);
+                    mJ = in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz);
+                    if (mJ) {
+                        keyJ = (rx * TE + ry) * TE + rz;
+                    } else {
+                        const T val[3] = {sp.qw_dv * vx, sp.qw_dv * vy, sp.qw_dv * vz};
+                        deposit_global<T, NW, SH::J0>(p, ix, iy, iz, wx, wy, wz, 0, 3, val);
+                    }
+                    if (MODE == PASS_STEP) {
+                        rx += drift_axis(ix, fx, (vx - p.vgal[0]) * p.hd[0], p.nx);
+                        ry += drift_axis(iy, fy, (vy - p.vgal[1]) * p.hd[1], p.ny);
+                        rz += drift_axis(iz, fz, (vz - p.vgal[2]) * p.hd[2], p.nz);
+                        SH::w(fx, wxR);
+                        SH::w(fy, wyR);
+                        SH::w(fz, wzR);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < NW; ++q) {
+                            wxR[q] = wx[q];
+                            wyR[q] = wy[q];
+                            wzR[q] = wz[q];
+                        }
+                    }
+                    mR = in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz);
+                    if (mR) {
+                        keyR = (rx * TE + ry) * TE + rz;
+                    } else {
+                        far++;
+                        const T val[1] = {sp.qw_dv};
+                        deposit_global<T, NW, SH::J0>(p, ix, iy, iz, wxR, wyR, wzR, 3, 1, val);
+                    }
+                    same = mJ && mR && keyR == keyJ;
+                    if (mJ) {
+                        const T vel[3] = {vx, vy, vz};
+                        stage_record<T, NW>(stg, lane, wx, wy, wz, vel);
+                        stg.frow()[lane] = same ? (T)1 : (T)0;
+#pragma unroll
+                        for (int a = 0; a < NW; ++a) {
+                            stg.xRrow(a)[lane] = wxR[a];
+                            stg.yRrow(a)[lane] = wyR[a];
+                            stg.zRrow(a)[lane] = wzR[a];
+                        }
+                    }
+                }
+                __syncwarp();
+                group_deposit_jr<T, TE>(sD, stg, mJ, keyJ, lane, sp.qw_dv);
+                __syncwarp();
+                // rho of members whose rho stencil starts elsewhere
+                const bool restR = mR && !same;
+                if (__any_sync(0xffffffffu, restR)) {
+                    if (restR) stage_record<T, NW>(stg, lane, wxR, wyR, wzR, nullptr);
+                    __syncwarp();
+                    group_deposit<T, NW, 1, TE>(sD, stg, restR, keyR, lane, sp.qw_dv);
+                    __syncwarp();
+                }
+            } else
 #pragma unroll
             for (int phase = 0; phase < 2; ++phase) {
                 bool member = false;
@@ -723,6 +853,19 @@ __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p)
             if (far) atomicAdd(&p.cnt[CNT_FAR], far);
         }
     }
+}
+
+// One CTA per bin. FP32 linear passes fit three CTAs per SM by shared memory and
+// have their registers held to that; the others are left to the compiler (FP32
+// quadratic and cubic passes come out at 128 registers, two CTAs per SM).
+template <typename T, int ORDER, int MODE, int MARGIN>
+__global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p) {
+    particle_pass_body<T, ORDER, MODE, MARGIN>(p);
+}
+
+template <typename T, int ORDER, int MODE, int MARGIN>
+__global__ void __launch_bounds__(PASS_THREADS, 3) particle_pass_kernel_3(PassK<T> p) {
+    particle_pass_body<T, ORDER, MODE, MARGIN>(p);
 }
 
 // ---------------------------------------------------------------------------
@@ -1051,7 +1194,11 @@ int pass_launch(pic_sim* s, cudaStream_t st) {
     }
     p.cnt = s->cnt;
     const PassSmem L(TileGeom<Shape<ORDER>::NW, MARGIN>::R, Shape<ORDER>::NW, sizeof(T), MODE == PASS_STEP);
-    auto kern = particle_pass_kernel<T, ORDER, MODE, MARGIN>;
+    void (*kern)(PassK<T>);
+    if constexpr (sizeof(T) == 4 && ORDER == 1)
+        kern = particle_pass_kernel_3<T, ORDER, MODE, MARGIN>;
+    else
+        kern = particle_pass_kernel<T, ORDER, MODE, MARGIN>;
     GP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
     kern<<<s->d.nbins, PASS_THREADS, L.total, st>>>(p);
     GP_CUDA(cudaGetLastError());

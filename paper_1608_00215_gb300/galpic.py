@@ -69,6 +69,7 @@ def _load():
         "pic_get": (c_int, [P, c_int, P, c_size_t, P]),
         "pic_set": (c_int, [P, c_int, P, c_size_t, P]),
         "pic_add_fields": (c_int, [P, P, P]),
+        "pic_sort_policy": (c_int, [P, c_int64, c_int64, P]),
         "pic_get_particles": (c_int, [P, c_int, P, POINTER(P), POINTER(P), P]),
         "pic_set_particles": (c_int, [P, c_int, P, POINTER(P), POINTER(P), P]),
         "pic_sort": (c_int, [P, P]),
@@ -93,7 +94,7 @@ EXPORTS = ("pic_version", "pic_last_error", "pic_footprint", "pic_init", "pic_de
            "pic_gather_push", "pic_field_update", "pic_step", "pic_step_many", "pic_diag_energy",
            "pic_get", "pic_set", "pic_get_particles", "pic_set_particles", "pic_status",
            "pic_counters", "pic_sizes", "pic_profile", "pic_profile_read", "pic_sort",
-           "pic_field_energy_noalloc", "pic_add_fields")
+           "pic_field_energy_noalloc", "pic_add_fields", "pic_sort_policy")
 
 STAGES = ("sort", "particles", "fft_r2c", "kspace", "fft_c2r", "energy")
 
@@ -218,6 +219,11 @@ class Sim:
         check(lib.pic_set(self.handle, which, c_void_p(src.data_ptr()), src.numel() * src.element_size(),
                           _stream_ptr(self.stream)))
         self._pending = src
+
+    def sort_policy(self, home_miss_threshold: int = -1, far_threshold: int = -1):
+        """Re-sort thresholds (particles outside their bin / their tile); -1 keeps one."""
+        check(lib.pic_sort_policy(self.handle, int(home_miss_threshold), int(far_threshold),
+                                  _stream_ptr(self.stream)))
 
     def add_fields(self, EB: torch.Tensor):
         """Add real-space fields EB = [Ex, Ey, Ez, Bx, By, Bz] (shape (6, nx, ny, nz),

@@ -168,6 +168,18 @@ def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_
     t0 = time.perf_counter()
     qi = 0
     work = {r.rid: pushes(r.workload, r.steps) for r in queue}
+
+    def advance(a: _Active):
+        """Enqueue the run's next chunk of graph-replayed steps and an event after it."""
+        n = min(chunk, a.req.steps - a.done)
+        with torch.cuda.stream(a.stream):
+            a.sim.step(n)
+            if a.done + n >= a.req.steps:
+                a.sim.status_async(a.status)    # read without a device-wide synchronisation
+            a.event = torch.cuda.Event()
+            a.event.record(a.stream)
+        a.done += n
+
     waiting: List[Request] = []
     while qi < len(queue) or active or waiting:
         now = time.perf_counter() - t0
@@ -184,14 +196,7 @@ def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_
                 used -= a.rec.footprint
                 active.remove(a)
                 continue
-            n = min(chunk, a.req.steps - a.done)
-            with torch.cuda.stream(a.stream):
-                a.sim.step(n)
-                if a.done + n >= a.req.steps:
-                    a.sim.status_async(a.status)    # read without a device-wide synchronisation
-                a.event = torch.cuda.Event()
-                a.event.record(a.stream)
-            a.done += n
+            advance(a)
         # admit: arrived, slot free, footprint fits; with priorities the waiting runs
         # are taken smallest first (a run that does not fit waits, smaller ones go on)
         while qi < len(queue) and queue[qi].arrival <= now:
@@ -219,9 +224,11 @@ def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_
                 continue
             rec.start = time.perf_counter() - t0
             used += fps[r.rid]
-            active.append(_Active(r, sim, stream, 0, None, rec,
-                                  torch.zeros(1, dtype=torch.int32).pin_memory()))
+            a = _Active(r, sim, stream, 0, None, rec, torch.zeros(1, dtype=torch.int32).pin_memory())
+            active.append(a)
             max_conc = max(max_conc, len(active))
+            if r.steps > 0:
+                advance(a)     # its first chunk starts while the next runs are admitted
         if active and all(a.event is not None and not a.event.query() for a in active):
             time.sleep(sleep)
         elif not active and not waiting and qi < len(queue):
