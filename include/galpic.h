@@ -88,8 +88,13 @@ typedef struct {
     int32_t tile_margin;        /* 0 or 1: cells of shared-memory tile kept around each
                                    8x8x8 bin for particles that left it since the last
                                    sort (0: smaller tiles, any particle outside its bin
-                                   takes the global-memory path and triggers a re-sort;
-                                   1: particles up to one cell out still use the tile) */
+                                   takes the global-memory path and counts toward the
+                                   re-sort threshold; 1: particles up to one cell out
+                                   still use the tile)                                 */
+    int32_t deposit;            /* deposit strategy of FP32 quadratic/cubic passes:
+                                   0: grouped by cell (fastest with many particles per
+                                   cell), 1: by stencil row (fastest with few); other
+                                   passes always group by cell. pic_tune picks one.   */
 } pic_config;
 
 /* One particle species. Particles are either generated on the device on a
@@ -191,6 +196,16 @@ int pic_get(pic_sim* sim, int which, void* dst, size_t bytes, void* stream);
 /* Overwrite the spectral E^n, B^n or rho^n (PIC_BUF_E_HAT, _B_HAT, _RHO_HAT)
  * from src (host or device). Setting E_HAT or B_HAT recomputes the real E, B. */
 int pic_set(pic_sim* sim, int which, const void* src, size_t bytes, void* stream);
+
+/* Autotuner: times the particle pass of this run for each tile margin (0, 1) and,
+ * for FP32 quadratic/cubic runs, each deposit strategy (pic_config.deposit), on the
+ * run's own particles and fields, keeps the fastest for all later steps (the step
+ * graph is re-captured) and writes it to chosen[0] (margin) and chosen[1]
+ * (strategy); chosen may be NULL. Each candidate takes three real, complete steps
+ * (one to settle, two timed), so the run advances by 6 or 12 steps, exactly as
+ * pic_step would advance it. Synchronises `stream`. Errors: PIC_EINVAL, PIC_ECUDA,
+ * PIC_ECUFFT (the run keeps its previous choice). */
+int pic_tune(pic_sim* sim, int32_t chosen[2], void* stream);
 
 /* Re-sort policy. Particles are kept sorted by bin so that a CTA finds them in its
  * shared-memory tile; a particle outside the tile takes a slower global-memory path

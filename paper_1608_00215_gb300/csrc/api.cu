@@ -56,6 +56,7 @@ int validate(const pic_config* c, const pic_species* sp, int ns) {
     if (c->init_fields == 1 && !(b2 < 1.0)) return fail(PIC_EINVAL, "|beta_init| must be below 1");
     if (c->init_fields != 0 && c->init_fields != 1) return fail(PIC_EINVAL, "init_fields must be 0 or 1");
     if (c->tile_margin != 0 && c->tile_margin != 1) return fail(PIC_EINVAL, "tile_margin must be 0 or 1");
+    if (c->deposit != 0 && c->deposit != 1) return fail(PIC_EINVAL, "deposit must be 0 or 1");
     if (ns < 0 || ns > PIC_MAX_SPECIES) return fail(PIC_EINVAL, "nspecies out of range");
     if (ns > 0 && !sp) return fail(PIC_EINVAL, "species array is NULL");
     int64_t ncell = (int64_t)c->nx * c->ny * c->nz;
@@ -621,6 +622,67 @@ int pic_set(pic_sim* s, int which, const void* src, size_t bytes, void* stream) 
         count_launches(s, 1);
         GP_CHECK(launch_master_to_scratch(s, st));
         GP_CHECK(exec_c2r(s, st));
+    }
+    return PIC_OK;
+}
+
+int pic_tune(pic_sim* s, int32_t chosen[2], void* stream) {
+    if (!s) return fail(PIC_EINVAL, "sim is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    struct Ev {
+        cudaEvent_t e = nullptr;
+        ~Ev() { if (e) cudaEventDestroy(e); }
+    } a, b;
+    GP_CUDA(cudaEventCreate(&a.e));
+    GP_CUDA(cudaEventCreate(&b.e));
+    const int nstrat = (s->cfg.precision == 32 && s->cfg.shape_order >= 2) ? 2 : 1;
+    const int keep_m = s->d.margin, keep_d = s->cfg.deposit;
+    int best_m = keep_m, best_d = keep_d;
+    float tbest = 0.f;
+    bool first = true;
+    for (int m = 0; m < 2; ++m)
+        for (int k = 0; k < nstrat; ++k) {
+            s->d.margin = m;
+            s->cfg.deposit = k;
+            // one full step to settle (a re-sort may be due), then two timed ones;
+            // only the particle pass (with its re-sort) is timed
+            int rc = gather_push(s, st);
+            if (rc == PIC_OK) rc = field_update(s, st);
+            float ms = 0.f;
+            for (int r = 0; r < 2 && rc == PIC_OK; ++r) {
+                float t = 0.f;
+                if (cudaEventRecord(a.e, st) != cudaSuccess) rc = fail(PIC_ECUDA, "event");
+                if (rc == PIC_OK) rc = gather_push(s, st);
+                if (rc == PIC_OK && cudaEventRecord(b.e, st) != cudaSuccess) rc = fail(PIC_ECUDA, "event");
+                if (rc == PIC_OK) rc = field_update(s, st);
+                if (rc == PIC_OK && (cudaEventSynchronize(b.e) != cudaSuccess ||
+                                     cudaEventElapsedTime(&t, a.e, b.e) != cudaSuccess))
+                    rc = fail(PIC_ECUDA, "tuning timing");
+                ms += t;
+            }
+            if (rc != PIC_OK) {
+                s->d.margin = keep_m;
+                s->cfg.deposit = keep_d;
+                return rc;
+            }
+            s->steps += 3;
+            if (first || ms < tbest) {
+                tbest = ms;
+                best_m = m;
+                best_d = k;
+                first = false;
+            }
+        }
+    s->d.margin = best_m;
+    s->cfg.tile_margin = best_m;
+    s->cfg.deposit = best_d;
+    if (s->graph_ok) {   // the captured step uses the previous choice
+        cudaGraphExecDestroy(s->graph);
+        s->graph_ok = false;
+    }
+    if (chosen) {
+        chosen[0] = best_m;
+        chosen[1] = best_d;
     }
     return PIC_OK;
 }

@@ -77,18 +77,25 @@ __device__ __forceinline__ double sinc_d(double a, double sa) { return a == 0.0 
 //   which is the paper's update applied to the corrected current, simplified
 //   exactly (Gauss's law is then carried from rho^n to rho^{n+1} per mode).
 // k = 0: T1 = 1, T2 = dt, T4 = -dt/eps0, T3 = A5 = A6 = 0 (B unchanged, E -= dt J/eps0).
+// The factors depend on k only through |k| and k.v_gal, so with v_gal,x = 0 (fx = 1)
+// the modes kx and -kx share them, and likewise along y: the kernel then evaluates
+// one representative mx <= nx/2 (my <= ny/2) and writes its mirrors too.
 template <typename C>
 __global__ void build_tables_kernel(C* __restrict__ tab, int nx, int ny, int nz, int nzh, int64_t M,
                                     double dx, double dy, double dz, double dt, double vx, double vy,
-                                    double vz, double c, double eps0, int cc, GaussLegendre gl) {
+                                    double vz, double c, double eps0, int cc, GaussLegendre gl, int fx,
+                                    int fy) {
     const double two_pi = 2.0 * M_PI;
     const double inx = 1.0 / (nx * dx), iny = 1.0 / (ny * dy), inz = 1.0 / (nz * dz);
-    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M;
-         m += (int64_t)gridDim.x * blockDim.x) {
-        int mz = (int)(m % nzh);
-        int64_t r = m / nzh;
-        int my = (int)(r % ny);
-        int mx = (int)(r / ny);
+    const int X = fx ? nx / 2 + 1 : nx, Y = fy ? ny / 2 + 1 : ny;
+    const int64_t Mrep = (int64_t)X * Y * nzh;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < Mrep;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int mz = (int)(q % nzh);
+        int64_t r = q / nzh;
+        int my = (int)(r % Y);
+        int mx = (int)(r / Y);
+        const int64_t m = ((int64_t)mx * ny + my) * nzh + mz;
         double kx = two_pi * (signed_index(mx, nx) * inx);
         double ky = two_pi * (signed_index(my, ny) * iny);
         double kz = two_pi * (mz * inz);
@@ -154,12 +161,19 @@ __global__ void build_tables_kernel(C* __restrict__ tab, int nx, int ny, int nz,
                 A6 = cscale(ctimesi(cmul(th2, chi3)), 1.0 / (eps0 * k2));
             }
         }
-        tab[0 * M + m] = mk<C>(T1.x, T1.y);
-        tab[1 * M + m] = mk<C>(T2.x, T2.y);
-        tab[2 * M + m] = mk<C>(T3.x, T3.y);
-        tab[3 * M + m] = mk<C>(T4.x, T4.y);
-        tab[4 * M + m] = mk<C>(A5.x, A5.y);
-        tab[5 * M + m] = mk<C>(A6.x, A6.y);
+        const C v[6] = {mk<C>(T1.x, T1.y), mk<C>(T2.x, T2.y), mk<C>(T3.x, T3.y),
+                        mk<C>(T4.x, T4.y), mk<C>(A5.x, A5.y), mk<C>(A6.x, A6.y)};
+        const bool mirx = fx && mx != 0 && 2 * mx != nx, miry = fy && my != 0 && 2 * my != ny;
+        const int64_t mxx = ((int64_t)(nx - mx) * ny + my) * nzh + mz;
+        const int64_t myy = ((int64_t)mx * ny + (ny - my)) * nzh + mz;
+        const int64_t mxy = ((int64_t)(nx - mx) * ny + (ny - my)) * nzh + mz;
+#pragma unroll
+        for (int t = 0; t < 6; ++t) {
+            tab[t * M + m] = v[t];
+            if (mirx) tab[t * M + mxx] = v[t];
+            if (miry) tab[t * M + myy] = v[t];
+            if (mirx && miry) tab[t * M + mxy] = v[t];
+        }
     }
 }
 
@@ -407,15 +421,17 @@ int grid_for(int64_t n, int block) {
 int launch_build_tables(pic_sim* s, cudaStream_t st) {
     const pic_config& c = s->cfg;
     GaussLegendre gl = gauss_legendre();
-    int grid = grid_for(s->d.M, 128);
+    const int fx = c.vgal[0] == 0.0, fy = c.vgal[1] == 0.0;
+    const int64_t rep = (int64_t)(fx ? s->d.nx / 2 + 1 : s->d.nx) * (fy ? s->d.ny / 2 + 1 : s->d.ny) * s->d.nzh;
+    int grid = grid_for(rep, 128);
     if (c.precision == 64)
         build_tables_kernel<double2><<<grid, 128, 0, st>>>(
             (double2*)s->Tab, s->d.nx, s->d.ny, s->d.nz, s->d.nzh, s->d.M, c.dx, c.dy, c.dz, c.dt,
-            c.vgal[0], c.vgal[1], c.vgal[2], c.c, c.eps0, c.current_correction, gl);
+            c.vgal[0], c.vgal[1], c.vgal[2], c.c, c.eps0, c.current_correction, gl, fx, fy);
     else
         build_tables_kernel<float2><<<grid, 128, 0, st>>>(
             (float2*)s->Tab, s->d.nx, s->d.ny, s->d.nz, s->d.nzh, s->d.M, c.dx, c.dy, c.dz, c.dt,
-            c.vgal[0], c.vgal[1], c.vgal[2], c.c, c.eps0, c.current_correction, gl);
+            c.vgal[0], c.vgal[1], c.vgal[2], c.c, c.eps0, c.current_correction, gl, fx, fy);
     GP_CUDA(cudaGetLastError());
     return PIC_OK;
 }

@@ -211,20 +211,39 @@ template <typename T, int NW> struct Stage {
     __device__ T* zRrow(int c) const { return row(4 + 5 * NW + c); }
 };
 
-__host__ __device__ constexpr size_t stage_bytes(int NW, size_t T) {
-    return T == 4 ? (NW == 4 ? Stage<float, 4>::BYTES : Stage<float, 2>::BYTES)
-                  : (NW == 4 ? Stage<double, 4>::BYTES : Stage<double, 2>::BYTES);
+// Per-warp staging area of the row deposit (FP32, quadratic/cubic): one block of 52
+// floats per lane (member) m at m * 52, in two halves h = 0 (the lanes that own Jx,
+// Jy) and h = 1 (Jz, rho), each of pairs ready for the packed multiply/FMA:
+//   XV[h][a]: h = 0 (wxJ[a] qw vx, wxJ[a] qw vy), h = 1 (wxJ[a] qw vz, wxR[a] qw);
+//   Y[h][b]:  h = 0 (wyJ[b], wyJ[b]),             h = 1 (wyJ[b], wyR[b]);
+//   Z[h][c]:  h = 0 (wzJ[c], wzJ[c]),             h = 1 (wzJ[c], wzR[c]);
+// J is the stencil at x^{n+1/2}, R the one at x^{n+1}. The 208-byte stride puts
+// the eight lanes of a quarter-warp 16-byte store on distinct banks.
+struct RowStage {
+    static constexpr int MEMBER = 52;
+    static constexpr int XV = 0, Y = 16, Z = 32;
+    static constexpr size_t BYTES = 32 * MEMBER * sizeof(float);
+};
+
+// Deposit strategies: grouped by cell (all passes) or by stencil row (FP32, NW = 4).
+enum { DEP_GROUP = 0, DEP_ROW = 1 };
+
+__host__ __device__ constexpr size_t stage_bytes(int NW, size_t T, int dep) {
+    return (T == 4 && NW == 4 && dep == DEP_ROW)
+               ? RowStage::BYTES
+               : T == 4 ? (NW == 4 ? Stage<float, 4>::BYTES : Stage<float, 2>::BYTES)
+                        : (NW == 4 ? Stage<double, 4>::BYTES : Stage<double, 2>::BYTES);
 }
 
 // Shared-memory layout of one particle-pass CTA (bytes), shared with the host.
 struct PassSmem {
     size_t tile, dep, stage, total;
-    __host__ __device__ PassSmem(int R, int NW, size_t T, bool step) {
+    __host__ __device__ PassSmem(int R, int NW, size_t T, bool step, int strategy) {
         size_t tb = step ? (T == 4 ? FieldTile<float>::bytes_per_node : FieldTile<double>::bytes_per_node) : 0;
         tile = 0;
         dep = align16(tb * (size_t)R);
         stage = align16(dep + 4 * (size_t)R * T);
-        total = align16(stage + (size_t)PASS_WARPS * stage_bytes(NW, T));
+        total = align16(stage + (size_t)PASS_WARPS * stage_bytes(NW, T, strategy));
     }
 };
 
@@ -300,11 +319,11 @@ __device__ void deposit_global(const PassK<T>& p, int ix, int iy, int iz, const 
 #pragma unroll
         for (int b = 0; b < NW; ++b) {
             T wxy = wx[a] * wy[b];
-            int64_t base = ((int64_t)wrapi(ix + J0 + a, p.nx) * p.ny + wrapi(iy + J0 + b, p.ny)) * p.nz;
+            int64_t base = ((int64_t)wrap_near(ix + J0 + a, p.nx) * p.ny + wrap_near(iy + J0 + b, p.ny)) * p.nz;
 #pragma unroll
             for (int c = 0; c < NW; ++c) {
                 T w = wxy * wz[c];
-                int64_t g = base + wrapi(iz + J0 + c, p.nz);
+                int64_t g = base + wrap_near(iz + J0 + c, p.nz);
                 for (int q = 0; q < Q; ++q) atomicAdd(&p.S[(q0 + q) * p.N + g], w * val[q]);
             }
         }
@@ -537,7 +556,163 @@ __device__ __forceinline__ void stage_record(const Stage<T, NW>& stg, int lane, 
     }
 }
 
-template <typename T, int ORDER, int MODE, int MARGIN>
+// Stage this lane's block of the row deposit (see RowStage).
+__device__ __forceinline__ void row_record(float* blk, const float* wxJ, const float* wyJ, const float* wzJ,
+                                           const float* wxR, const float* wyR, const float* wzR,
+                                           float qvx, float qvy, float qvz, float qw) {
+    float4* q = reinterpret_cast<float4*>(blk);
+#pragma unroll
+    for (int a = 0; a < 4; a += 2) {
+        q[a / 2] = make_float4(wxJ[a] * qvx, wxJ[a] * qvy, wxJ[a + 1] * qvx, wxJ[a + 1] * qvy);
+        q[2 + a / 2] = make_float4(wxJ[a] * qvz, wxR[a] * qw, wxJ[a + 1] * qvz, wxR[a + 1] * qw);
+        q[4 + a / 2] = make_float4(wyJ[a], wyJ[a], wyJ[a + 1], wyJ[a + 1]);
+        q[6 + a / 2] = make_float4(wyJ[a], wyR[a], wyJ[a + 1], wyR[a + 1]);
+        q[8 + a / 2] = make_float4(wzJ[a], wzJ[a], wzJ[a + 1], wzJ[a + 1]);
+        q[10 + a / 2] = make_float4(wzJ[a], wzR[a], wzJ[a + 1], wzR[a + 1]);
+    }
+}
+
+// Adds acc[z].x / acc[z].y to two shared-memory rows p0[z], p1[z] for z in
+// [zlo, zhi], in chunks of four nodes: all reads, then all compare-and-swaps, then
+// the retries of those that lost a race (shared-memory float atomics are
+// compare-and-swap loops on this GPU).
+template <int TE>
+__device__ __forceinline__ void row_flush(unsigned* p0, unsigned* p1, const float2 (&acc)[TE], int zlo, int zhi) {
+#pragma unroll
+    for (int z0 = 0; z0 < TE; z0 += 4) {
+        unsigned o0[4], o1[4];
+        bool d0[4], d1[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int z = z0 + k;
+            d0[k] = d1[k] = true;
+            if (z < TE && z >= zlo && z <= zhi) {
+                o0[k] = *reinterpret_cast<volatile unsigned*>(p0 + z);
+                o1[k] = *reinterpret_cast<volatile unsigned*>(p1 + z);
+                d0[k] = d1[k] = false;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int z = z0 + k;
+            if (z < TE && !d0[k]) {
+                unsigned prev = atomicCAS(p0 + z, o0[k], __float_as_uint(__uint_as_float(o0[k]) + acc[z].x));
+                d0[k] = prev == o0[k];
+                o0[k] = prev;
+                prev = atomicCAS(p1 + z, o1[k], __float_as_uint(__uint_as_float(o1[k]) + acc[z].y));
+                d1[k] = prev == o1[k];
+                o1[k] = prev;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int z = z0 + k;
+            if (z >= TE) continue;
+            while (!d0[k]) {   // lost a race with another warp: retry (lock-free, always progresses)
+                const unsigned prev = atomicCAS(p0 + z, o0[k], __float_as_uint(__uint_as_float(o0[k]) + acc[z].x));
+                d0[k] = prev == o0[k];
+                o0[k] = prev;
+            }
+            while (!d1[k]) {
+                const unsigned prev = atomicCAS(p1 + z, o1[k], __float_as_uint(__uint_as_float(o1[k]) + acc[z].y));
+                d1[k] = prev == o1[k];
+                o1[k] = prev;
+            }
+        }
+    }
+}
+
+// Row deposit of one warp (FP32, NW = 4, tile extent TE): the strategy for few
+// particles per cell. Members are grouped by the (x, y) start of their stencil in
+// the tile (`row` = rx * TE + ry), so the particles of a whole row of cells form
+// one group. For a row, lane (h, a, b) = (lane >> 4, (lane >> 2) & 3, lane & 3)
+// owns the tile nodes (rx + a, ry + b, z) for every z and two components, (Jx, Jy)
+// for h = 0 and (Jz, rho) for h = 1, summed in registers as packed pairs: a member
+// whose stencil starts at z node j adds its staged x-weight-times-value pair times
+// its y-weight pair times z-weight pair c to node j + c (one packed multiply, four
+// packed FMAs). J (stencil at x^{n+1/2}) and rho (at x^{n+1}) of a particle normally
+// start at the same node; where they do not, the particle joins two (row, j) groups
+// with the other part zeroed. Each row's sums go to the shared tile once, over the
+// z range it touched. mJ / mR: this lane's J / rho stencil lies in the tile; zJ /
+// zR: its z start. Every lane of the warp must call this (warp-collective).
+template <int TE>
+__device__ void row_deposit(float* sD, const float* stg, bool mJ, int rowJ, int zJ, bool mR, int rowR, int zR,
+                            int lane) {
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int R = TE * TE * TE;
+    constexpr int NS = TE - 3;   // stencil starts along z
+    constexpr int M = RowStage::MEMBER;
+    const int h = lane >> 4, a = (lane >> 2) & 3, b = lane & 3;
+    const bool hi = h != 0;
+    const float* sx = stg + RowStage::XV + 8 * h + 2 * a;
+    const float* sy = stg + RowStage::Y + 8 * h + 2 * b;
+    const float* sz = stg + RowStage::Z + 8 * h;
+    unsigned pendJ = __ballot_sync(FULL, mJ), pendR = __ballot_sync(FULL, mR);
+    while (pendJ | pendR) {
+        const int leader = __ffs(pendJ ? pendJ : pendR) - 1;
+        const int cur = __shfl_sync(FULL, pendJ ? rowJ : rowR, leader);
+        const bool inJ = mJ && rowJ == cur, inR = mR && rowR == cur;
+        const unsigned gJ = __ballot_sync(FULL, inJ), gR = __ballot_sync(FULL, inR);
+        pendJ &= ~gJ;
+        pendR &= ~gR;
+        const unsigned zs = __reduce_or_sync(FULL, (inJ ? 1u << zJ : 0u) | (inR ? 1u << zR : 0u));
+        float2 acc[TE];
+#pragma unroll
+        for (int z = 0; z < TE; ++z) acc[z] = make_float2(0.f, 0.f);
+        auto coef = [&](int m) { return pmul(ld2(sx + m * M), ld2(sy + m * M)); };
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+            if (!((zs >> j) & 1u)) continue;
+            const unsigned sJ = __ballot_sync(FULL, inJ && zJ == j);
+            const unsigned sR = __ballot_sync(FULL, inR && zR == j);
+            auto add = [&](int m, float2 c) {
+                const float4 z01 = *reinterpret_cast<const float4*>(sz + m * M);
+                const float4 z23 = *reinterpret_cast<const float4*>(sz + m * M + 4);
+                acc[j + 0] = pfma(c, make_float2(z01.x, z01.y), acc[j + 0]);
+                acc[j + 1] = pfma(c, make_float2(z01.z, z01.w), acc[j + 1]);
+                acc[j + 2] = pfma(c, make_float2(z23.x, z23.y), acc[j + 2]);
+                acc[j + 3] = pfma(c, make_float2(z23.z, z23.w), acc[j + 3]);
+            };
+            // members whose J and rho both start here, two at a time; cell-sorted
+            // particles make them one run of consecutive lanes
+            unsigned mm = sJ & sR;
+            if (mm) {
+                const int lo = __ffs(mm) - 1, len = __popc(mm);
+                if ((mm >> lo) == (len == 32 ? FULL : ((1u << len) - 1u))) {
+                    int m = lo;
+                    const int me = lo + len;
+                    for (; m + 1 < me; m += 2) {
+                        const float2 c1 = coef(m), c2 = coef(m + 1);
+                        add(m, c1);
+                        add(m + 1, c2);
+                    }
+                    if (m < me) add(m, coef(m));
+                } else {
+                    while (mm) {
+                        const int m = __ffs(mm) - 1;
+                        mm &= mm - 1;
+                        add(m, coef(m));
+                    }
+                }
+            }
+            // members with only one of J, rho starting here: zero the other part
+            unsigned rr = (sJ | sR) & ~(sJ & sR);
+            while (rr) {
+                const int k = __ffs(rr) - 1;
+                rr &= rr - 1;
+                const float fJ = ((sJ >> k) & 1u) ? 1.f : 0.f, fR = ((sR >> k) & 1u) ? 1.f : 0.f;
+                add(k, pmul(coef(k), make_float2(fJ, hi ? fR : fJ)));
+            }
+        }
+        // add the row to the tile: nodes (rx + a, ry + b, z) over the touched z range
+        const int zlo = __ffs(zs) - 1, zhi = 31 - __clz(zs) + 3;
+        const int node0 = (cur + a * TE + b) * TE;
+        row_flush<TE>(reinterpret_cast<unsigned*>(sD + (2 * h) * R + node0),
+                      reinterpret_cast<unsigned*>(sD + (2 * h + 1) * R + node0), acc, zlo, zhi);
+    }
+}
+
+template <typename T, int ORDER, int MODE, int MARGIN, int DEP>
 __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
     typedef Shape<ORDER> SH;
     typedef typename Pair<T>::type P2;
@@ -545,13 +720,15 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
     constexpr int TE = TileGeom<NW, MARGIN>::E;
     constexpr int R = TileGeom<NW, MARGIN>::R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const PassSmem L(R, NW, sizeof(T), MODE == PASS_STEP);
+    const PassSmem L(R, NW, sizeof(T), MODE == PASS_STEP, DEP);
+    static_assert(DEP == DEP_GROUP || (sizeof(T) == 4 && NW == 4), "row deposit: FP32, NW = 4 only");
     FieldTile<T> tile;
     tile.init(smem_raw + L.tile, R);
     T* sD = reinterpret_cast<T*>(smem_raw + L.dep);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     Stage<T, NW> stg;
-    stg.base = reinterpret_cast<T*>(smem_raw + L.stage + warp * Stage<T, NW>::BYTES);
+    stg.base = reinterpret_cast<T*>(smem_raw + L.stage + warp * stage_bytes(NW, sizeof(T), DEP));
+    float* const rstg = reinterpret_cast<float*>(stg.base);
 
     const int b = blockIdx.x;
     const int bz = b % p.nbz, by = (b / p.nbz) % p.nby, bx = b / (p.nbz * p.nby);
@@ -664,12 +841,12 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
 #pragma unroll
                             for (int bb = 0; bb < NW; ++bb) {
                                 const T wxy = wx[a] * wy[bb];
-                                const int64_t gb = ((int64_t)wrapi(ix + SH::J0 + a, p.nx) * p.ny +
-                                                    wrapi(iy + SH::J0 + bb, p.ny)) * p.nz;
+                                const int64_t gb = ((int64_t)wrap_near(ix + SH::J0 + a, p.nx) * p.ny +
+                                                    wrap_near(iy + SH::J0 + bb, p.ny)) * p.nz;
 #pragma unroll
                                 for (int cc = 0; cc < NW; ++cc) {
                                     const T w = wxy * wz[cc];
-                                    const int64_t g = gb + wrapi(iz + SH::J0 + cc, p.nz);
+                                    const int64_t g = gb + wrap_near(iz + SH::J0 + cc, p.nz);
                                     E[0] += w * p.F[0 * N + g];
                                     E[1] += w * p.F[1 * N + g];
                                     E[2] += w * p.F[2 * N + g];
@@ -768,6 +945,61 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
                     group_deposit<T, NW, 1, TE>(sD, stg, restR, keyR, lane, sp.qw_dv);
                     __syncwarp();
                 }
+            } else if constexpr (DEP == DEP_ROW) {
+                // few particles per cell: both stencils first, then one pass by stencil row
+                bool mJ = false, mR = false;
+                int rowJ = 0, zJ = 0, rowR = 0, zR = 0;
+                if (valid) {
+                    if (MODE == PASS_STEP) {
+                        rx += drift_axis(ix, fx, (vx - p.vgal[0]) * p.hd[0], p.nx);
+                        ry += drift_axis(iy, fy, (vy - p.vgal[1]) * p.hd[1], p.ny);
+                        rz += drift_axis(iz, fz, (vz - p.vgal[2]) * p.hd[2], p.nz);
+                    }
+                    SH::w(fx, wx);
+                    SH::w(fy, wy);
+                    SH::w(fz, wz);
+                    const T qvx = sp.qw_dv * vx, qvy = sp.qw_dv * vy, qvz = sp.qw_dv * vz;
+                    mJ = in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz);
+                    if (mJ) {
+                        rowJ = rx * TE + ry;
+                        zJ = rz;
+                    } else {
+                        const T val[3] = {qvx, qvy, qvz};
+                        deposit_global<T, NW, SH::J0>(p, ix, iy, iz, wx, wy, wz, 0, 3, val);
+                    }
+                    T wxR[NW], wyR[NW], wzR[NW];
+                    if (MODE == PASS_STEP) {
+                        rx += drift_axis(ix, fx, (vx - p.vgal[0]) * p.hd[0], p.nx);
+                        ry += drift_axis(iy, fy, (vy - p.vgal[1]) * p.hd[1], p.ny);
+                        rz += drift_axis(iz, fz, (vz - p.vgal[2]) * p.hd[2], p.nz);
+                        SH::w(fx, wxR);
+                        SH::w(fy, wyR);
+                        SH::w(fz, wzR);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < NW; ++q) {
+                            wxR[q] = wx[q];
+                            wyR[q] = wy[q];
+                            wzR[q] = wz[q];
+                        }
+                    }
+                    mR = in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz);
+                    if (mR) {
+                        rowR = rx * TE + ry;
+                        zR = rz;
+                    } else {
+                        far++;
+                        const T val[1] = {sp.qw_dv};
+                        deposit_global<T, NW, SH::J0>(p, ix, iy, iz, wxR, wyR, wzR, 3, 1, val);
+                    }
+                    if (mJ || mR)
+                        row_record(rstg + lane * RowStage::MEMBER, (const float*)wx, (const float*)wy,
+                                   (const float*)wz, (const float*)wxR, (const float*)wyR, (const float*)wzR,
+                                   (float)qvx, (float)qvy, (float)qvz, (float)sp.qw_dv);
+                }
+                __syncwarp();
+                row_deposit<TE>(reinterpret_cast<float*>(sD), rstg, mJ, rowJ, zJ, mR, rowR, zR, lane);
+                __syncwarp();
             } else
 #pragma unroll
             for (int phase = 0; phase < 2; ++phase) {
@@ -856,16 +1088,22 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
 }
 
 // One CTA per bin. FP32 linear passes fit three CTAs per SM by shared memory and
-// have their registers held to that; the others are left to the compiler (FP32
-// quadratic and cubic passes come out at 128 registers, two CTAs per SM).
-template <typename T, int ORDER, int MODE, int MARGIN>
+// have their registers held to that; row-deposit passes are held to two; the others
+// are left to the compiler (the FP32 quadratic and cubic grouped passes come out
+// below 128 registers, two CTAs per SM).
+template <typename T, int ORDER, int MODE, int MARGIN, int DEP>
 __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p) {
-    particle_pass_body<T, ORDER, MODE, MARGIN>(p);
+    particle_pass_body<T, ORDER, MODE, MARGIN, DEP>(p);
 }
 
-template <typename T, int ORDER, int MODE, int MARGIN>
+template <typename T, int ORDER, int MODE, int MARGIN, int DEP>
 __global__ void __launch_bounds__(PASS_THREADS, 3) particle_pass_kernel_3(PassK<T> p) {
-    particle_pass_body<T, ORDER, MODE, MARGIN>(p);
+    particle_pass_body<T, ORDER, MODE, MARGIN, DEP>(p);
+}
+
+template <typename T, int ORDER, int MODE, int MARGIN, int DEP>
+__global__ void __launch_bounds__(PASS_THREADS, 2) particle_pass_kernel_2(PassK<T> p) {
+    particle_pass_body<T, ORDER, MODE, MARGIN, DEP>(p);
 }
 
 // ---------------------------------------------------------------------------
@@ -1159,7 +1397,7 @@ int sort_typed(pic_sim* s, cudaStream_t st) {
     return PIC_OK;
 }
 
-template <typename T, int ORDER, int MODE, int MARGIN>
+template <typename T, int ORDER, int MODE, int MARGIN, int DEP>
 int pass_launch(pic_sim* s, cudaStream_t st) {
     const pic_config& c = s->cfg;
     PassK<T> p;
@@ -1193,24 +1431,34 @@ int pass_launch(pic_sim* s, cudaStream_t st) {
         p.sp[k].qdt2m = (T)(sp.q * c.dt / (2.0 * sp.m));
     }
     p.cnt = s->cnt;
-    const PassSmem L(TileGeom<Shape<ORDER>::NW, MARGIN>::R, Shape<ORDER>::NW, sizeof(T), MODE == PASS_STEP);
+    const PassSmem L(TileGeom<Shape<ORDER>::NW, MARGIN>::R, Shape<ORDER>::NW, sizeof(T), MODE == PASS_STEP, DEP);
     void (*kern)(PassK<T>);
     if constexpr (sizeof(T) == 4 && ORDER == 1)
-        kern = particle_pass_kernel_3<T, ORDER, MODE, MARGIN>;
+        kern = particle_pass_kernel_3<T, ORDER, MODE, MARGIN, DEP>;
+    else if constexpr (DEP == DEP_ROW)
+        kern = particle_pass_kernel_2<T, ORDER, MODE, MARGIN, DEP>;
     else
-        kern = particle_pass_kernel<T, ORDER, MODE, MARGIN>;
+        kern = particle_pass_kernel<T, ORDER, MODE, MARGIN, DEP>;
     GP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
     kern<<<s->d.nbins, PASS_THREADS, L.total, st>>>(p);
     GP_CUDA(cudaGetLastError());
     return PIC_OK;
 }
 
+template <typename T, int ORDER, int MODE, int MARGIN>
+int pass_strategy(pic_sim* s, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        if (s->cfg.deposit == DEP_ROW) return pass_launch<T, ORDER, MODE, MARGIN, DEP_ROW>(s, st);
+    }
+    return pass_launch<T, ORDER, MODE, MARGIN, DEP_GROUP>(s, st);
+}
+
 template <typename T, int MODE, int MARGIN>
 int pass_order(pic_sim* s, cudaStream_t st) {
     switch (s->cfg.shape_order) {
-        case 1: return pass_launch<T, 1, MODE, MARGIN>(s, st);
-        case 2: return pass_launch<T, 2, MODE, MARGIN>(s, st);
-        default: return pass_launch<T, 3, MODE, MARGIN>(s, st);
+        case 1: return pass_launch<T, 1, MODE, MARGIN, DEP_GROUP>(s, st);
+        case 2: return pass_strategy<T, 2, MODE, MARGIN>(s, st);
+        default: return pass_strategy<T, 3, MODE, MARGIN>(s, st);
     }
 }
 
@@ -1224,7 +1472,7 @@ int pass_margin(pic_sim* s, cudaStream_t st) {
 size_t tile_bytes(const pic_config& c, const Dims& d, int mode) {
     int nw = c.shape_order == 1 ? 2 : 4;
     int e = BIN + nw - 1 + 2 * d.margin;
-    return PassSmem(e * e * e, nw, c.precision == 64 ? 8 : 4, mode == PASS_STEP).total;
+    return PassSmem(e * e * e, nw, c.precision == 64 ? 8 : 4, mode == PASS_STEP, c.deposit).total;
 }
 
 int64_t sort_keys(const Dims& d) { return (int64_t)d.nbins * d.BX * d.BY * d.BZ; }

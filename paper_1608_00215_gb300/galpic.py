@@ -33,7 +33,7 @@ class PicConfig(ctypes.Structure):
                 ("beta_init", c_double * 3),
                 ("nx", c_int32), ("ny", c_int32), ("nz", c_int32), ("shape_order", c_int32),
                 ("precision", c_int32), ("current_correction", c_int32), ("init_fields", c_int32),
-                ("tile_margin", c_int32)]
+                ("tile_margin", c_int32), ("deposit", c_int32)]
 
 
 class PicSpecies(ctypes.Structure):
@@ -70,6 +70,7 @@ def _load():
         "pic_set": (c_int, [P, c_int, P, c_size_t, P]),
         "pic_add_fields": (c_int, [P, P, P]),
         "pic_sort_policy": (c_int, [P, c_int64, c_int64, P]),
+        "pic_tune": (c_int, [P, P, P]),
         "pic_get_particles": (c_int, [P, c_int, P, POINTER(P), POINTER(P), P]),
         "pic_set_particles": (c_int, [P, c_int, P, POINTER(P), POINTER(P), P]),
         "pic_sort": (c_int, [P, P]),
@@ -94,7 +95,7 @@ EXPORTS = ("pic_version", "pic_last_error", "pic_footprint", "pic_init", "pic_de
            "pic_gather_push", "pic_field_update", "pic_step", "pic_step_many", "pic_diag_energy",
            "pic_get", "pic_set", "pic_get_particles", "pic_set_particles", "pic_status",
            "pic_counters", "pic_sizes", "pic_profile", "pic_profile_read", "pic_sort",
-           "pic_field_energy_noalloc", "pic_add_fields", "pic_sort_policy")
+           "pic_field_energy_noalloc", "pic_add_fields", "pic_sort_policy", "pic_tune")
 
 STAGES = ("sort", "particles", "fft_r2c", "kspace", "fft_c2r", "energy")
 
@@ -112,7 +113,7 @@ def _stream_ptr(stream: Optional[torch.cuda.Stream]) -> c_void_p:
 
 def make_config(nx: int, ny: int, nz: int, *, dx=1.0, dy=1.0, dz=1.0, dt=1.0, vgal=(0.0, 0.0, 0.0),
                 c=1.0, eps0=1.0, rho_bg=0.0, beta_init=(0.0, 0.0, 0.0), shape_order=1,
-                precision=32, current_correction=1, init_fields=1, tile_margin=1) -> PicConfig:
+                precision=32, current_correction=1, init_fields=1, tile_margin=1, deposit=0) -> PicConfig:
     cfg = PicConfig()
     cfg.dx, cfg.dy, cfg.dz, cfg.dt = dx, dy, dz, dt
     cfg.vgal[:] = list(vgal)
@@ -122,6 +123,7 @@ def make_config(nx: int, ny: int, nz: int, *, dx=1.0, dy=1.0, dz=1.0, dt=1.0, vg
     cfg.shape_order, cfg.precision = shape_order, precision
     cfg.current_correction, cfg.init_fields = current_correction, init_fields
     cfg.tile_margin = tile_margin
+    cfg.deposit = deposit
     return cfg
 
 
@@ -220,6 +222,14 @@ class Sim:
                           _stream_ptr(self.stream)))
         self._pending = src
 
+    def tune(self) -> Dict[str, int]:
+        """Time the particle pass for each tile margin and deposit strategy (0: grouped
+        by cell, 1: by stencil row) on this run and keep the fastest. Takes real steps:
+        the run advances by 6 or 12 steps. Returns {"tile_margin": m, "deposit": d}."""
+        out = (c_int32 * 2)()
+        check(lib.pic_tune(self.handle, out, _stream_ptr(self.stream)))
+        return {"tile_margin": int(out[0]), "deposit": int(out[1])}
+
     def sort_policy(self, home_miss_threshold: int = -1, far_threshold: int = -1):
         """Re-sort thresholds (particles outside their bin / their tile); -1 keeps one."""
         check(lib.pic_sort_policy(self.handle, int(home_miss_threshold), int(far_threshold),
@@ -309,7 +319,7 @@ def step_many(sims: Sequence[Sim], nsteps: int, stream=None):
 
 
 def sim_from_workload(wl, precision: Optional[int] = None, stream=None, device="cuda",
-                      tile_margin: int = 1) -> Sim:
+                      tile_margin: int = 1, deposit: int = 0) -> Sim:
     """A run of a synthetic workload (duck-typed: grid, units, v_gal, species with
     q, m, ppc, u0, jitter, density), particles generated on the device."""
     prec = wl.precision if precision is None else precision
@@ -317,7 +327,7 @@ def sim_from_workload(wl, precision: Optional[int] = None, stream=None, device="
                       c=wl.c, eps0=wl.eps0, rho_bg=wl.rho_bg, beta_init=wl.beta_init,
                       shape_order=wl.shape_order, precision=prec,
                       current_correction=wl.current_correction, init_fields=wl.init_fields,
-                      tile_margin=tile_margin)
+                      tile_margin=tile_margin, deposit=deposit)
     ncells = wl.nx * wl.ny * wl.nz
     sp = []
     for k, s in enumerate(wl.species):

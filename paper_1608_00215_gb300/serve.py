@@ -138,12 +138,16 @@ class ServeResult:
 def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_slots: int = 64,
           chunk: int = 25, precision: Optional[int] = None, device: str = "cuda",
           sleep: float = 2e-4, keep_final_state: bool = False, on_retire=None,
-          priorities: bool = True) -> ServeResult:
+          priorities: bool = True, admit_per_poll: int = 1) -> ServeResult:
     """Run all requests with continuous batching; returns per-run records.
 
     ``max_slots = 1`` gives the serial baseline on the same arrival trace.
     ``hbm_budget`` defaults to 90 % of the free device memory at the start.
     ``priorities``: give each run's stream the priority class of its size.
+    ``admit_per_poll``: runs admitted between two polls of the active runs (admission
+    builds tables and may create FFT plans, so finished runs are retired in between).
+    A run's finish time is taken on the device: the event after its last chunk,
+    measured against an event recorded at the start.
     """
     prange = torch.cuda.Stream.priority_range() if priorities else (0, 0)
     if hbm_budget is None:
@@ -165,6 +169,9 @@ def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_
     active: List[_Active] = []
     used = 0
     max_conc = 0
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
     t0 = time.perf_counter()
     qi = 0
     work = {r.rid: pushes(r.workload, r.steps) for r in queue}
@@ -176,7 +183,7 @@ def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_
             a.sim.step(n)
             if a.done + n >= a.req.steps:
                 a.sim.status_async(a.status)    # read without a device-wide synchronisation
-            a.event = torch.cuda.Event()
+            a.event = torch.cuda.Event(enable_timing=True)
             a.event.record(a.stream)
         a.done += n
 
@@ -188,7 +195,8 @@ def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_
             if a.event is not None and not a.event.query():
                 continue
             if a.done >= a.req.steps:
-                a.rec.finish = time.perf_counter() - t0
+                a.rec.finish = (ev0.elapsed_time(a.event) * 1e-3 if a.event is not None
+                                else time.perf_counter() - t0)
                 a.rec.status = int(a.status.item())     # copied when the last chunk was enqueued
                 if keep_final_state and on_retire is not None:
                     on_retire(a.req, a.sim)
@@ -205,7 +213,8 @@ def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_
         if priorities and len(waiting) > 1:
             waiting.sort(key=lambda r: (work[r.rid], r.arrival))
         wi = 0
-        while wi < len(waiting) and len(active) < max_slots:
+        admitted = 0
+        while wi < len(waiting) and len(active) < max_slots and admitted < admit_per_poll:
             r = waiting[wi]
             if used + fps[r.rid] > hbm_budget:
                 if not priorities:
@@ -226,10 +235,11 @@ def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_
             used += fps[r.rid]
             a = _Active(r, sim, stream, 0, None, rec, torch.zeros(1, dtype=torch.int32).pin_memory())
             active.append(a)
+            admitted += 1
             max_conc = max(max_conc, len(active))
             if r.steps > 0:
                 advance(a)     # its first chunk starts while the next runs are admitted
-        if active and all(a.event is not None and not a.event.query() for a in active):
+        if active and not admitted and all(a.event is not None and not a.event.query() for a in active):
             time.sleep(sleep)
         elif not active and not waiting and qi < len(queue):
             wait = queue[qi].arrival - (time.perf_counter() - t0)

@@ -59,6 +59,9 @@ TABLE_CASES = [
     dict(n=(8, 8, 16), vgal=(0.0, 0.0, gi.drift_v(130.0)), cc=1),
     dict(n=(4, 4, 1536), vgal=(0.0, 0.0, gi.drift_v(130.0)), cc=0),   # worst-conditioned modes
     dict(n=(6, 5, 8), vgal=(0.3, -0.4, 0.5), cc=0, units=dict(c=1.7, dt=0.45, eps0=2.3, dx=0.8, dy=1.3, dz=0.6)),
+    # mirror-symmetric builds: odd and even sizes along folded axes
+    dict(n=(7, 6, 10), vgal=(0.0, 0.0, 0.6), cc=1, units=dict(c=1.3, dt=0.7, eps0=0.9, dx=1.1, dy=0.7, dz=0.9)),
+    dict(n=(6, 9, 8), vgal=(0.35, 0.0, -0.5), cc=0),
 ]
 
 
@@ -105,14 +108,17 @@ def test_tables_match_literal_formulas(gp, case):
     sim.close()
 
 
-@pytest.mark.parametrize("margin", [0, 1])
-@pytest.mark.parametrize("order", [1, 2, 3])
-@pytest.mark.parametrize("precision", [64, 32])
-def test_deposit_matches_oracle(gp, order, precision, margin):
+DEPOSIT_CASES = [(p, o, m, 0) for p in (64, 32) for o in (1, 2, 3) for m in (0, 1)] + \
+    [(32, o, m, 1) for o in (2, 3) for m in (0, 1)]
+
+
+@pytest.mark.parametrize("precision,order,margin,strategy", DEPOSIT_CASES)
+def test_deposit_matches_oracle(gp, order, precision, margin, strategy):
     """rho and J = sum q w v S / dV at random positions (random momenta), several bins
-    and a ragged edge, against the oracle's deposit; both tile margins."""
+    and a ragged edge, against the oracle's deposit; both tile margins and, for FP32
+    quadratic/cubic passes, both deposit strategies."""
     wl = gi.drifting_plasma(12, 10, 18, 5.0, precision=precision, shape_order=order, jitter=0.0)
-    sim = gp.sim_from_workload(wl, tile_margin=margin)
+    sim = gp.sim_from_workload(wl, tile_margin=margin, deposit=strategy)
     rng = np.random.default_rng(order + precision)
     dt = torch.float64 if precision == 64 else torch.float32
     for k, spec in enumerate(wl.species):
@@ -273,7 +279,7 @@ def _plane_wave_spectra(wl, amp=1.0, m=(1, 2, 3)):
     return np.fft.rfftn(E, axes=(1, 2, 3)), np.fft.rfftn(B, axes=(1, 2, 3))
 
 
-def _fixture(gp, name, galilean, precision, order, margin=1):
+def _fixture(gp, name, galilean, precision, order, margin=1, strategy=0):
     """FP32 parity fixtures with O(1) fields.
     F1: gamma = 130 neutral drifting plasma plus a unit-amplitude vacuum plane wave.
     F2: electron-only gamma = 30 plasma with a 10 % sinusoidal density modulation along z
@@ -281,7 +287,7 @@ def _fixture(gp, name, galilean, precision, order, margin=1):
     if name == "F1":
         wl = gi.drifting_plasma(16, 16, 32, 130.0, galilean=galilean, shape_order=order, precision=precision,
                                 jitter=0.05)
-        sim = gp.sim_from_workload(wl, tile_margin=margin)
+        sim = gp.sim_from_workload(wl, tile_margin=margin, deposit=strategy)
         Eh, Bh = _plane_wave_spectra(wl)
         dt = sim.cplx
         E = sim.get(gp.BUF_E_HAT, device="cpu").to(torch.complex128) + torch.from_numpy(Eh)
@@ -303,7 +309,8 @@ def _fixture(gp, name, galilean, precision, order, margin=1):
     off = [torch.from_numpy(a).to(rdt) for a in (p.fx, p.fy, fz)]
     u = [torch.from_numpy(a).to(rdt) for a in (p.ux, p.uy, p.uz)]
     cfg = gp.make_config(wl.nx, wl.ny, wl.nz, vgal=wl.vgal, rho_bg=wl.rho_bg, beta_init=wl.beta_init,
-                         shape_order=order, precision=precision, init_fields=1, tile_margin=margin)
+                         shape_order=order, precision=precision, init_fields=1, tile_margin=margin,
+                         deposit=strategy)
     spec = wl.species[0]
     sp = gp.copied_species(spec.q, spec.m, wl.weight(spec), cell, off, u)
     return wl, gp.Sim(cfg, [sp])
@@ -332,14 +339,16 @@ def test_fp32_parity(gp, fixture, galilean):
     sim.close()
 
 
+@pytest.mark.parametrize("strategy", [0, 1])
 @pytest.mark.parametrize("margin", [0, 1])
 @pytest.mark.parametrize("galilean", [True, False])
 @pytest.mark.parametrize("order", [2, 3])
-def test_fp32_step_parity_tile_margins(gp, order, galilean, margin):
-    """FP32 cubic and quadratic steps at both tile margins, with and without the
-    Galilean frame (without it every particle crosses a z cell per step and some
-    leave their bin): one step within 1e-5 of the oracle, five within 1e-4."""
-    wl, sim = _fixture(gp, "F1", galilean, 32, order, margin)
+def test_fp32_step_parity_tile_margins(gp, order, galilean, margin, strategy):
+    """FP32 cubic and quadratic steps at both tile margins and with both deposit
+    strategies, with and without the Galilean frame (without it every particle
+    crosses a z cell per step and some leave their bin): one step within 1e-5 of the
+    oracle, five within 1e-4."""
+    wl, sim = _fixture(gp, "F1", galilean, 32, order, margin, strategy)
     sim.step(2)
     sim.sort()
     cfg, st = oracle_state_from_sim(sim, wl)
@@ -376,4 +385,37 @@ def test_deferred_resort_matches_oracle(gp, precision, order):
     assert c["sorts"] == s0 and c["far"] > 0
     err = field_rel_l2(sim, st)
     assert err < (1e-10 if precision == 64 else 1e-4), err
+    sim.close()
+
+
+@pytest.mark.parametrize("precision,order", [(32, 3), (32, 1), (64, 3)])
+def test_tune_takes_real_steps_and_keeps_results(gp, precision, order):
+    """pic_tune times real steps for each tile margin (and, FP32 quadratic/cubic,
+    each deposit strategy): the run advances by three steps per candidate, exactly as
+    the oracle does, and the steps after it follow the oracle as before (the step
+    graph is re-captured)."""
+    wl = gi.drifting_plasma(16, 16, 32, 130.0, galilean=True, shape_order=order, precision=precision,
+                            ppc=(1, 1, 2), jitter=0.05)
+    sim = gp.sim_from_workload(wl)
+    sim.step(2)
+    sim.sort()
+    cfg, st = oracle_state_from_sim(sim, wl)
+    chosen = sim.tune()
+    assert chosen["tile_margin"] in (0, 1) and chosen["deposit"] in (0, 1)
+    ncand = 4 if (precision == 32 and order >= 2) else 2
+    assert chosen["deposit"] == 0 or ncand == 4
+    for _ in range(3 * ncand):
+        pic.step(cfg, st)
+    torch.cuda.synchronize()
+    tol1 = 1e-10 if precision == 64 else 1e-4
+    err = field_rel_l2(sim, st)
+    assert err < tol1, err
+    sim.sort()
+    cfg, st = oracle_state_from_sim(sim, wl)
+    sim.step(3)
+    for _ in range(3):
+        pic.step(cfg, st)
+    torch.cuda.synchronize()
+    err = field_rel_l2(sim, st)
+    assert err < tol1, err
     sim.close()
