@@ -144,10 +144,12 @@ def fp32_peak_tflops():
     return 152 * 128 * 2 * mhz * 1e6 / 1e12
 
 
-# DRAM bytes per particle and per cell of one particle-pass launch, from the ncu
-# capture summarised in profiles/particle_pass_cubic_fp32_64x64x128.md (current
-# kernel); scaled to a launch by the particles and cells it processes.
-PASS_TRAFFIC = {}
+# DRAM bytes per particle and per cell of one particle-pass launch, keyed by (shape
+# order, precision, tile margin, deposit strategy), from the ncu capture summarised in
+# profiles/particle_pass_cubic_fp32_64x64x128.md (dram__bytes_read.sum +
+# dram__bytes_write.sum = 440.5 MB for 8,388,608 particles at 16 per cell); scaled to a
+# launch by the particles it processes (the same 16 particles per cell).
+PASS_TRAFFIC = {(3, 32, 0, 0): (52.5, 0.0)}
 
 
 def kspace_bytes(wl, precision):
@@ -174,6 +176,22 @@ def cpu_baseline(steps=2, grid=(16, 16, 32)):
             "sample": f"{steps} FP64 oracle steps of the same gamma=130 cubic drifting plasma at "
                       f"{grid[0]}x{grid[1]}x{grid[2]} ({P} particles); numpy deposit/gather single-threaded, "
                       f"scipy.fft on all cores"}
+
+
+def slowest_rank(ms, e2e_s, world, device):
+    """Timed-region milliseconds and end-to-end seconds of the slowest rank (max over
+    the process group; the identity for one rank)."""
+    import torch
+    t = torch.tensor([ms, e2e_s], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t[0]), float(t[1])
+
+
+def replica_throughput(particles_per_rank, steps, world, ms_max):
+    """Whole-job particle pushes per second: every rank advances its own replica of the
+    workload by `steps`; the job takes as long as its slowest rank."""
+    return particles_per_rank * steps * world / (ms_max * 1e-3)
 
 
 def run_reference(args, rank):
@@ -217,6 +235,8 @@ def run_ours(args, rank, world, local_rank):
     wl = workload(grid, order=args.order)
     P, N = wl.nparticles, wl.ncells
     sim = gp.sim_from_workload(wl, precision=32, tile_margin=args.margin)
+    # the autotuner picks tile margin and deposit strategy on this run (real steps)
+    tuned = sim.tune() if not args.no_tune else {"tile_margin": args.margin, "deposit": 0}
     torch.cuda.synchronize()
     for _ in range(args.warmup):
         sim.gather_push()
@@ -252,12 +272,10 @@ def run_ours(args, rank, world, local_rank):
 
     # end to end through the C ABI from pinned host buffers: H2D of the initial
     # particles inside pic_init, K steps each followed by a D2H read of the field energy
-    e2e = e2e_run(gp, wl, args.steps) if not args.no_e2e else {"seconds": float("nan"), "h2d": 0, "d2h": 0}
+    e2e = (e2e_run(gp, wl, args.steps, tuned) if not args.no_e2e
+           else {"seconds": float("nan"), "h2d": 0, "d2h": 0})
 
-    t = torch.tensor([ms, e2e["seconds"]], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_max, e2e_max = float(t[0]), float(t[1])
+    ms_max, e2e_max = slowest_rank(ms, e2e["seconds"], world, "cuda")
     if rank != 0:
         return
     hbm, peak_kind = peaks()
@@ -267,9 +285,9 @@ def run_ours(args, rank, world, local_rank):
     ks_ms = ks["ms"] / max(1, ks["count"])
     achieved = particle_bytes(wl, 32) / (part_ms * 1e-3) / 1e9
     ks_achieved = kspace_bytes(wl, 32) / (ks_ms * 1e-3) / 1e9
-    value = P * args.steps * world / (ms_max * 1e-3)
-    kname = f"particle_pass_kernel<float,{args.order},STEP,{args.margin}>"
-    tr = PASS_TRAFFIC.get((args.order, 32, args.margin))
+    value = replica_throughput(P, args.steps, world, ms_max)
+    kname = f"particle_pass_kernel<float,{args.order},STEP,{tuned['tile_margin']},{tuned['deposit']}>"
+    tr = PASS_TRAFFIC.get((args.order, 32, tuned["tile_margin"], tuned["deposit"]))
     traffic = None if tr is None else tr[0] * P + tr[1] * N
     roof_hbm = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
@@ -287,7 +305,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": wl.name + " (gamma=130 e-p plasma, 2x2x2 ppc/species, cubic shapes, "
                                          "v_gal=v_drift, FP32 with FP64-built tables)",
                    "grid": list(grid), "particles": P, "cells": N, "shape_order": args.order, "precision": 32,
-                   "parallelism": f"replicas x{world}", "tile_margin": args.margin,
+                   "parallelism": f"replicas x{world}", "tuned": tuned,
                    "l2": "inputs larger than L2 (15 GB of particles, 0.8 GB of fields); no flush"},
         "cell_updates_per_s": N * args.steps * world / (ms_max * 1e-3),
         "stages_ms_per_step": {k: v["ms"] / max(1, v["count"]) for k, v in stages.items() if v["count"]},
@@ -498,7 +516,10 @@ def lwfa_run(args):
     print(json.dumps(out), flush=True)
 
 
-def e2e_run(gp, wl, steps):
+def e2e_run(gp, wl, steps, tuned):
+    """The same workload end to end through the public API: particles from pinned host
+    memory, the tile margin and deposit strategy the autotuner chose on the first run
+    (a caller keeps them), pic_init and K steps with a D2H read of the field energy each."""
     import torch
     sim = gp.sim_from_workload(wl, precision=32)
     host = []
@@ -520,7 +541,8 @@ def e2e_run(gp, wl, steps):
     cfg = gp.make_config(wl.nx, wl.ny, wl.nz, dx=wl.dx, dy=wl.dy, dz=wl.dz, dt=wl.dt, vgal=wl.vgal,
                          c=wl.c, eps0=wl.eps0, rho_bg=wl.rho_bg, beta_init=wl.beta_init,
                          shape_order=wl.shape_order, precision=32,
-                         current_correction=wl.current_correction, init_fields=wl.init_fields)
+                         current_correction=wl.current_correction, init_fields=wl.init_fields,
+                         tile_margin=tuned["tile_margin"], deposit=tuned["deposit"])
     species = [gp.copied_species(s.q, s.m, wl.weight(s), d["cell"], d["off"], d["u"])
                for s, d in zip(wl.species, pinned)]
     out = torch.empty(1, dtype=torch.float64).pin_memory()
@@ -552,6 +574,8 @@ def main():
                     help="nx,ny,nz of the drifting plasma (default: the 256x256x512 workload)")
     ap.add_argument("--order", type=int, default=3, help="shape order (default 3)")
     ap.add_argument("--margin", type=int, default=1, help="particle tile margin in cells (0 or 1)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the autotuner (pic_tune) and use --margin with the grouped deposit")
     ap.add_argument("--serving-requests", type=int, default=32,
                     help="requests of the serving leg (0 skips it)")
     ap.add_argument("--serving-steps", type=int, default=50, help="steps per serving request")
