@@ -147,9 +147,9 @@ def fp32_peak_tflops():
 # DRAM bytes per particle and per cell of one particle-pass launch, keyed by (shape
 # order, precision, tile margin, deposit strategy), from the ncu capture summarised in
 # profiles/particle_pass_cubic_fp32_64x64x128.md (dram__bytes_read.sum +
-# dram__bytes_write.sum = 440.5 MB for 8,388,608 particles at 16 per cell); scaled to a
+# dram__bytes_write.sum = 457.7 MB for 8,388,608 particles at 16 per cell); scaled to a
 # launch by the particles it processes (the same 16 particles per cell).
-PASS_TRAFFIC = {(3, 32, 0, 0): (52.5, 0.0)}
+PASS_TRAFFIC = {(3, 32, 0, 0): (54.6, 0.0)}
 
 
 def kspace_bytes(wl, precision):
@@ -579,6 +579,8 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=32,
                     help="requests of the serving leg (0 skips it)")
     ap.add_argument("--serving-steps", type=int, default=50, help="steps per serving request")
+    ap.add_argument("--serving-only", action="store_true",
+                    help="only the serving leg (e.g. the full trace: --serving-requests 256 --serving-steps 500)")
     ap.add_argument("--long-run", action="store_true",
                     help="FP32 vs FP64 long-run precision study instead of the throughput line")
     ap.add_argument("--long-run-every", type=int, default=100)
@@ -604,6 +606,12 @@ def main():
         return
     if args.lwfa:
         lwfa_run(args)
+        return
+    if args.serving_only:
+        from paper_1608_00215_gb300 import build
+        build.build()
+        out = serving_bench(args.serving_requests, args.serving_steps)
+        print(json.dumps({"mode": "serving", **out}), flush=True)
         return
     if world > 1:
         import torch
