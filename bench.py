@@ -147,9 +147,9 @@ def fp32_peak_tflops():
 # DRAM bytes per particle and per cell of one particle-pass launch, keyed by (shape
 # order, precision, tile margin, deposit strategy), from the ncu capture summarised in
 # profiles/particle_pass_cubic_fp32_64x64x128.md (dram__bytes_read.sum +
-# dram__bytes_write.sum = 457.7 MB for 8,388,608 particles at 16 per cell); scaled to a
+# dram__bytes_write.sum = 446.1 MB for 8,388,608 particles at 16 per cell); scaled to a
 # launch by the particles it processes (the same 16 particles per cell).
-PASS_TRAFFIC = {(3, 32, 0, 0): (54.6, 0.0)}
+PASS_TRAFFIC = {(3, 32, 0, 0): (53.2, 0.0)}
 
 
 def kspace_bytes(wl, precision):
@@ -348,16 +348,19 @@ def serving_bench(n_req, steps, chunk=25, seed=4):
     serial = serve.serve(burst, max_slots=1, chunk=chunk)
     batched = serve.serve(burst, max_slots=64, chunk=chunk)
     even = serve.serve(burst, max_slots=64, chunk=chunk, priorities=False)
+    uncapped = serve.serve(burst, max_slots=64, chunk=chunk, max_per_level=None)
     out["burst"] = {"serial": serial.summary(), "batched": batched.summary(),
-                    "batched_without_priorities": even.summary()}
+                    "batched_without_priorities": even.summary(),
+                    "batched_without_level_caps": uncapped.summary()}
     out["stream_priority_range"] = list(torch.cuda.Stream.priority_range())
     mean_service = serial.makespan / max(1, n_req)
     arr = gi.poisson_arrivals(n_req, rate=2.0 / mean_service, seed=seed)
     trace = [serve.Request(i, wl, steps, float(a)) for i, (wl, a) in enumerate(zip(wls, arr))]
     serial_p = serve.serve(trace, max_slots=1, chunk=chunk)
     batched_p = serve.serve(trace, max_slots=64, chunk=chunk)
+    uncapped_p = serve.serve(trace, max_slots=64, chunk=chunk, max_per_level=None)
     out["poisson"] = {"rate_per_s": 2.0 / mean_service, "serial": serial_p.summary(),
-                      "batched": batched_p.summary()}
+                      "batched": batched_p.summary(), "batched_without_level_caps": uncapped_p.summary()}
     out["speedup_runs_per_s"] = {"burst": batched.runs_per_s / serial.runs_per_s,
                                  "poisson": batched_p.runs_per_s / serial_p.runs_per_s}
     return out

@@ -189,6 +189,8 @@ int launch_generate(pic_sim* s, int species, const pic_species* spec, cudaStream
 int launch_sort(pic_sim* s, cudaStream_t st);
 int launch_sanitize(pic_sim* s, int species, cudaStream_t st);
 int launch_particle_pass(pic_sim* s, int mode, cudaStream_t st);
+int launch_pass_fp32(pic_sim* s, int mode, cudaStream_t st);   // pass_fp32.cu
+int launch_pass_fp64(pic_sim* s, int mode, cudaStream_t st);   // pass_fp64.cu
 
 enum { PASS_STEP = 0, PASS_DEPOSIT = 1 };
 enum { STAGE_SORT = 0, STAGE_PARTICLES = 1, STAGE_R2C = 2, STAGE_KSPACE = 3, STAGE_C2R = 4,

@@ -1,0 +1,1214 @@
+// The particle pass of the Galilean-PSATD step (templates; instantiated by
+// pass_fp32.cu and pass_fp64.cu, one translation unit per precision so that they
+// compile in parallel). One CTA per bin: the bin's E, B tile (plus stencil halo and
+// a margin) is staged in shared memory as component pairs; each particle gathers E
+// and B with packed FP32x2 FMAs, takes the relativistic Boris push and the Galilean
+// drift in two halves, and deposits J^{n+1/2} and rho^{n+1}. The deposit is reduced
+// inside the warp first (grouped by cell, or by stencil row for few particles per
+// cell), then added to the shared tile, and the tile to the global grids once per
+// CTA. Particles whose stencil leaves the tile use global memory directly.
+#pragma once
+
+#include <math.h>
+
+#include "common.cuh"
+
+namespace galpic {
+
+namespace {
+
+constexpr int PASS_THREADS = 256;
+constexpr int PASS_WARPS = PASS_THREADS / 32;
+
+__device__ __forceinline__ int wrapi(int i, int n) {
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+// Periodic wrap for an index that is at most one period outside [0, n) (the
+// common case); anything further goes through the modulo.
+__device__ __forceinline__ int wrap_near(int i, int n) {
+    if (i < 0)
+        i += n;
+    else if (i >= n)
+        i -= n;
+    return (i >= 0 && i < n) ? i : wrapi(i, n);
+}
+
+// Periodic wrap on the out-of-tile paths: the near form for 4x4x4 stencils; the
+// modulo for 2x2x2 ones, whose kernels then fit their register budget without spills.
+template <int NW>
+__device__ __forceinline__ int wrapf(int i, int n) { return NW == 2 ? wrapi(i, n) : wrap_near(i, n); }
+
+// Division of a non-negative int32 by a fixed divisor d >= 1 with one 64-bit
+// multiply and a shift: q = (x * M) >> s with s = 31 + ceil(log2 d) and
+// M = ceil(2^s / d) < 2^32. For x < 2^31 the rounding error of M adds less than
+// x/2^s < 2^-ceil(log2 d) <= 1/d to x/d, which never carries past the next integer.
+struct FastDiv {
+    uint32_t d, M;
+    int s;
+    __host__ void init(uint32_t dd) {
+        d = dd;
+        int L = 0;
+        while ((1ull << L) < dd) ++L;
+        s = 31 + L;
+        M = (uint32_t)(((1ull << s) + dd - 1) / dd);
+    }
+    __device__ __forceinline__ int div(int x) const {
+        return (int)(((unsigned long long)(unsigned)x * M) >> s);
+    }
+};
+
+// Shape factors of order 1, 2, 3 (B-splines) for a particle at cell i with offset
+// f in [0, 1): node i + J0 + a gets weight w[a], a = 0 .. NW-1.
+template <int ORDER> struct Shape;
+
+template <> struct Shape<1> {
+    static constexpr int NW = 2, J0 = 0;
+    template <typename T> __device__ static void w(T f, T* w) {
+        w[0] = (T)1 - f;
+        w[1] = f;
+    }
+};
+
+template <> struct Shape<2> {
+    static constexpr int NW = 4, J0 = -1;
+    // nearest node n = i + (f >= 1/2), d = f - (f >= 1/2):
+    // W(n-1) = (1/2 - d)^2/2, W(n) = 3/4 - d^2, W(n+1) = (1/2 + d)^2/2
+    template <typename T> __device__ static void w(T f, T* w) {
+        bool up = f >= (T)0.5;
+        T d = up ? f - (T)1 : f;
+        T a = (T)0.5 * ((T)0.5 - d) * ((T)0.5 - d);
+        T b = (T)0.75 - d * d;
+        T c = (T)0.5 * ((T)0.5 + d) * ((T)0.5 + d);
+        w[0] = up ? (T)0 : a;
+        w[1] = up ? a : b;
+        w[2] = up ? b : c;
+        w[3] = up ? c : (T)0;
+    }
+};
+
+template <> struct Shape<3> {
+    static constexpr int NW = 4, J0 = -1;
+    // cubic B-spline at node distances 1+f, f, 1-f, 2-f
+    template <typename T> __device__ static void w(T f, T* w) {
+        T g = (T)1 - f;
+        T f2 = f * f, g2 = g * g;
+        w[0] = g2 * g * (T)(1.0 / 6.0);
+        w[1] = (T)(2.0 / 3.0) - f2 + (T)0.5 * f2 * f;
+        w[2] = (T)(2.0 / 3.0) - g2 + (T)0.5 * g2 * g;
+        w[3] = f2 * f * (T)(1.0 / 6.0);
+    }
+};
+
+// Packed pair FMA: d = a * b + c per component. FP32 uses the paired FP32 FMA of
+// sm_100-class GPUs (one instruction for two IEEE round-to-nearest FMAs).
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
+    unsigned long long ra = *reinterpret_cast<unsigned long long*>(&a);
+    unsigned long long rb = *reinterpret_cast<unsigned long long*>(&b);
+    unsigned long long rc = *reinterpret_cast<unsigned long long*>(&c);
+    unsigned long long rd;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
+    return *reinterpret_cast<float2*>(&rd);
+}
+__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) {
+    unsigned long long ra = *reinterpret_cast<unsigned long long*>(&a);
+    unsigned long long rb = *reinterpret_cast<unsigned long long*>(&b);
+    unsigned long long rd;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    return *reinterpret_cast<float2*>(&rd);
+}
+__device__ __forceinline__ double2 pmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x, a.y * b.y);
+}
+
+template <typename T> struct Pair;
+template <> struct Pair<float> {
+    typedef float2 type;
+    __device__ static float2 make(float a, float b) { return make_float2(a, b); }
+};
+template <> struct Pair<double> {
+    typedef double2 type;
+    __device__ static double2 make(double a, double b) { return make_double2(a, b); }
+};
+
+// E, B tile in shared memory as three component pairs per node:
+// P0 = (Ex, Ey), P1 = (Ez, Bx), P2 = (By, Bz).
+// float: one float4 (P0, P1) and one float2 (P2) per node; double: three double2.
+template <typename T> struct FieldTile;
+template <> struct FieldTile<float> {
+    float4* q;
+    float2* r;
+    __device__ void init(unsigned char* base, int R) {
+        q = reinterpret_cast<float4*>(base);
+        r = reinterpret_cast<float2*>(base + 16 * (size_t)R);
+    }
+    __device__ void store(int idx, const float* v) {
+        q[idx] = make_float4(v[0], v[1], v[2], v[3]);
+        r[idx] = make_float2(v[4], v[5]);
+    }
+    __device__ void load(int idx, float2& p0, float2& p1, float2& p2) const {
+        float4 a = q[idx];
+        p0 = make_float2(a.x, a.y);
+        p1 = make_float2(a.z, a.w);
+        p2 = r[idx];
+    }
+    static constexpr size_t bytes_per_node = 24;
+};
+template <> struct FieldTile<double> {
+    double2 *a, *b, *c;
+    __device__ void init(unsigned char* base, int R) {
+        a = reinterpret_cast<double2*>(base);
+        b = a + R;
+        c = b + R;
+    }
+    __device__ void store(int idx, const double* v) {
+        a[idx] = make_double2(v[0], v[1]);
+        b[idx] = make_double2(v[2], v[3]);
+        c[idx] = make_double2(v[4], v[5]);
+    }
+    __device__ void load(int idx, double2& p0, double2& p1, double2& p2) const {
+        p0 = a[idx];
+        p1 = b[idx];
+        p2 = c[idx];
+    }
+    static constexpr size_t bytes_per_node = 48;
+};
+
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) / 16 * 16; }
+
+// Per-warp staging area of the grouped deposit, transposed: one row per staged
+// quantity, indexed by lane. Rows 0..2 hold the velocity (J phase), then NW rows of
+// x weights wx[a], NW rows of y weights wy[b] and NW rows of z weights wz[c].
+// A group of lanes that share a stencil is summed two members at a time: the values
+// of lanes m and m+1 of one row are one aligned pair, loaded in one instruction and
+// fed to the packed FP32x2 multiply/FMA. The row stride RS = 34 elements keeps pairs
+// aligned and puts consecutive rows two banks apart, so the up-to-16 distinct rows a
+// warp reads at one lane index hit distinct banks; a lane's stores to its own column
+// are contiguous across the warp.
+// Linear stencils (NW = 2) add a flag row and rows of the x^{n+1} (rho) weights for
+// the combined J and rho deposit.
+template <typename T, int NW> struct Stage {
+    static constexpr int RS = 34;
+    static constexpr int ROWS = NW == 2 ? 4 + 6 * NW : 3 + 3 * NW;
+    static constexpr size_t BYTES = align16((size_t)ROWS * RS * sizeof(T));   // per warp
+    T* base;
+    __device__ T* row(int r) const { return base + r * RS; }
+    __device__ T* vrow(int q) const { return row(q); }
+    __device__ T* xrow(int a) const { return row(3 + a); }
+    __device__ T* yrow(int b) const { return row(3 + NW + b); }
+    __device__ T* zrow(int c) const { return row(3 + 2 * NW + c); }
+    __device__ T* frow() const { return row(3 + 3 * NW); }
+    __device__ T* xRrow(int a) const { return row(4 + 3 * NW + a); }
+    __device__ T* yRrow(int b) const { return row(4 + 4 * NW + b); }
+    __device__ T* zRrow(int c) const { return row(4 + 5 * NW + c); }
+};
+
+// Per-warp staging area of the row deposit (FP32, quadratic/cubic): one block of 52
+// floats per lane (member) m at m * 52, in two halves h = 0 (the lanes that own Jx,
+// Jy) and h = 1 (Jz, rho), each of pairs ready for the packed multiply/FMA:
+//   XV[h][a]: h = 0 (wxJ[a] qw vx, wxJ[a] qw vy), h = 1 (wxJ[a] qw vz, wxR[a] qw);
+//   Y[h][b]:  h = 0 (wyJ[b], wyJ[b]),             h = 1 (wyJ[b], wyR[b]);
+//   Z[h][c]:  h = 0 (wzJ[c], wzJ[c]),             h = 1 (wzJ[c], wzR[c]);
+// J is the stencil at x^{n+1/2}, R the one at x^{n+1}. The 208-byte stride puts
+// the eight lanes of a quarter-warp 16-byte store on distinct banks.
+struct RowStage {
+    static constexpr int MEMBER = 52;
+    static constexpr int XV = 0, Y = 16, Z = 32;
+    static constexpr size_t BYTES = 32 * MEMBER * sizeof(float);
+};
+
+// Deposit strategies: grouped by cell (all passes) or by stencil row (FP32, NW = 4).
+enum { DEP_GROUP = 0, DEP_ROW = 1 };
+
+__host__ __device__ constexpr size_t stage_bytes(int NW, size_t T, int dep) {
+    return (T == 4 && NW == 4 && dep == DEP_ROW)
+               ? RowStage::BYTES
+               : T == 4 ? (NW == 4 ? Stage<float, 4>::BYTES : Stage<float, 2>::BYTES)
+                        : (NW == 4 ? Stage<double, 4>::BYTES : Stage<double, 2>::BYTES);
+}
+
+// Shared-memory layout of one particle-pass CTA (bytes), shared with the host.
+struct PassSmem {
+    size_t tile, dep, stage, total;
+    __host__ __device__ PassSmem(int R, int NW, size_t T, bool step, int strategy) {
+        size_t tb = step ? (T == 4 ? FieldTile<float>::bytes_per_node : FieldTile<double>::bytes_per_node) : 0;
+        tile = 0;
+        dep = align16(tb * (size_t)R);
+        stage = align16(dep + 4 * (size_t)R * T);
+        total = align16(stage + (size_t)PASS_WARPS * stage_bytes(NW, T, strategy));
+    }
+};
+
+// Bins are BIN^3 cells; the shared tile of a bin covers its cells' stencils plus
+// MARGIN cells on every side, so particles that moved up to MARGIN cells out of
+// their bin since the last sort still use the tile.
+constexpr int BIN = 8;
+template <int NW, int MARGIN> struct TileGeom {
+    static constexpr int E = BIN + NW - 1 + 2 * MARGIN;   // tile extent per axis (nodes)
+    static constexpr int R = E * E * E;
+};
+
+template <typename T>
+struct SpeciesK {
+    int32_t* cell;
+    T* off[3];
+    T* u[3];
+    const int32_t* bin_start;
+    T qw_dv;   // q w / dV
+    T qdt2m;   // q dt / (2 m)
+};
+
+template <typename T>
+struct PassK {
+    const T* F;     // real E (3N) then B (3N)
+    T* S;           // real Jx, Jy, Jz, rho (4N)
+    int64_t N;
+    int nx, ny, nz;
+    FastDiv div_nynz, div_nz;
+    int nbx, nby, nbz;
+    T inv_c2;
+    T hd[3];             // dt / (2 d) per axis
+    T vgal[3];
+    int nspecies;
+    SpeciesK<T> sp[PIC_MAX_SPECIES];
+    unsigned long long* cnt;
+};
+
+// Move (i, f) by d cells along an axis of n cells: offset back to [0, 1), periodic.
+// Returns the cell shift (before the periodic wrap).
+template <typename T>
+__device__ __forceinline__ int drift_axis(int& i, T& f, T d, int n) {
+    f += d;
+    T s = floor(f);
+    f -= s;
+    int si = (int)s;
+    if (f >= (T)1) {
+        f -= (T)1;
+        si += 1;
+    }
+    i = wrap_near(i + si, n);
+    return si;
+}
+
+// Tile coordinates: tile node t holds global node (o + t) mod n with
+// o = bin origin + J0 - margin, so the stencil of a particle in cell i starts at tile
+// index r = i - bin origin + margin; the pass tracks r through the drifts without
+// wrapping it (r + shift stays congruent to the new cell's index modulo n). The
+// stencil lies in the tile iff 0 <= r <= extent - NW; otherwise the particle takes
+// the global-memory path.
+template <int NW, int TE>
+__device__ __forceinline__ bool in_tile(int r) {
+    return (unsigned)r <= (unsigned)(TE - NW);
+}
+
+// Element i of a small register array without dynamic indexing (the array stays in
+// registers).
+template <typename T, int NW>
+__device__ __forceinline__ T pick(const T* w, int i) {
+    T r = w[0];
+#pragma unroll
+    for (int k = 1; k < NW; ++k) r = (i == k) ? w[k] : r;
+    return r;
+}
+
+// Direct deposit of Q values at one particle's stencil into the global grids
+// (particles outside the tile, a rare path). For 4x4x4 stencils a rolled loop over
+// the nodes keeps it from holding registers the in-tile path needs; 2x2x2 stencils
+// are unrolled.
+template <typename T, int NW, int J0>
+__device__ void deposit_global(const PassK<T>& p, int ix, int iy, int iz, const T* wx, const T* wy,
+                               const T* wz, int q0, int Q, const T* val) {
+    if constexpr (NW == 2) {
+#pragma unroll
+        for (int a = 0; a < NW; ++a)
+#pragma unroll
+            for (int b = 0; b < NW; ++b) {
+                const T wxy = wx[a] * wy[b];
+                const int64_t base =
+                    ((int64_t)wrapi(ix + J0 + a, p.nx) * p.ny + wrapi(iy + J0 + b, p.ny)) * p.nz;
+#pragma unroll
+                for (int c = 0; c < NW; ++c) {
+                    const T w = wxy * wz[c];
+                    const int64_t g = base + wrapi(iz + J0 + c, p.nz);
+                    for (int q = 0; q < Q; ++q) atomicAdd(&p.S[(q0 + q) * p.N + g], w * val[q]);
+                }
+            }
+        return;
+    }
+    const T v0 = val[0], v1 = Q > 1 ? val[1] : (T)0, v2 = Q > 2 ? val[2] : (T)0;
+#pragma unroll 1
+    for (int n = 0; n < NW * NW * NW; ++n) {
+        const int a = n / (NW * NW), b = (n / NW) % NW, c = n % NW;
+        const T w = pick<T, NW>(wx, a) * pick<T, NW>(wy, b) * pick<T, NW>(wz, c);
+        const int64_t g = ((int64_t)wrap_near(ix + J0 + a, p.nx) * p.ny + wrap_near(iy + J0 + b, p.ny)) * p.nz +
+                          wrap_near(iz + J0 + c, p.nz);
+        T* dst = p.S + q0 * p.N + g;
+        atomicAdd(dst, w * v0);
+        if (Q > 1) {
+            atomicAdd(dst + p.N, w * v1);
+            atomicAdd(dst + 2 * p.N, w * v2);
+        }
+    }
+}
+
+// Adds K values to K distinct shared-memory words. Shared-memory floating-point
+// atomics are compare-and-swap loops on this GPU; issuing all K reads, then all K
+// compare-and-swaps, and retrying only the ones that lost a race keeps K round trips
+// in flight at once instead of K dependent ones.
+__device__ __forceinline__ unsigned as_bits(float x) { return __float_as_uint(x); }
+__device__ __forceinline__ unsigned long long as_bits(double x) { return (unsigned long long)__double_as_longlong(x); }
+__device__ __forceinline__ float from_bits(unsigned x) { return __uint_as_float(x); }
+__device__ __forceinline__ double from_bits(unsigned long long x) { return __longlong_as_double((long long)x); }
+
+template <typename T, int K>
+__device__ __forceinline__ void smem_add_batch(T* const (&addr)[K], const T (&val)[K]) {
+    typedef decltype(as_bits((T)0)) U;
+    U old[K];
+    bool done[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) old[k] = as_bits(*reinterpret_cast<volatile T*>(addr[k]));
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const U prev = atomicCAS(reinterpret_cast<U*>(addr[k]), old[k], as_bits(from_bits(old[k]) + val[k]));
+        done[k] = prev == old[k];
+        old[k] = prev;
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        while (!done[k]) {   // lost a race with another warp: retry (lock-free, always progresses)
+            const U prev = atomicCAS(reinterpret_cast<U*>(addr[k]), old[k], as_bits(from_bits(old[k]) + val[k]));
+            done[k] = prev == old[k];
+            old[k] = prev;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ typename Pair<T>::type ld2(const T* p) {
+    return *reinterpret_cast<const typename Pair<T>::type*>(p);
+}
+
+// Grouped deposit of one warp. `member`: this lane staged its weights (and, for J,
+// its velocity) and its stencil starts at tile node `key` (tile linear index).
+// Q = 3 (J, components q0 = 0..2) or 1 (rho, q0 = 3); every deposited value is
+// qw * (weight product) * (velocity component or 1). For each group of lanes with
+// one key, the lanes take (node, component) roles, sum over the group's members
+// (two at a time when the group is a contiguous run of lanes, the normal case for
+// cell-sorted particles) and add each role's sum to the shared tile once.
+// Every lane of the warp must call this (warp-collective).
+template <typename T, int NW, int Q, int TE>
+__device__ void group_deposit(T* sD, const Stage<T, NW>& stg, bool member, int key, int lane, T qw) {
+    typedef typename Pair<T>::type P2;
+    constexpr int q0 = (Q == 3) ? 0 : 3;
+    constexpr int R = TE * TE * TE;
+    const P2 one = Pair<T>::make((T)1, (T)1);
+    const P2 zero = Pair<T>::make((T)0, (T)0);
+    unsigned pending = __ballot_sync(0xffffffffu, member);
+    while (pending) {
+        const int leader = __ffs(pending) - 1;
+        const int gkey = __shfl_sync(0xffffffffu, key, leader);
+        const unsigned grp = __ballot_sync(0xffffffffu, member && key == gkey);
+        pending &= ~grp;
+        const int lo = __ffs(grp) - 1;
+        const int len = __popc(grp);
+        const bool run = (grp >> lo) == (len == 32 ? 0xffffffffu : ((1u << len) - 1u));   // warp-uniform
+        if (NW == 4) {
+            // lane -> y-z node (b, c) = (bc >> 2, bc & 3), bc = lane & 15, and x nodes h, h + 2
+            const int bc = lane & 15, h = lane >> 4, b = bc >> 2, c = bc & 3;
+            const T* xh = stg.xrow(h);
+            const T* xh2 = stg.xrow(h + 2);
+            const T* yb = stg.yrow(b);
+            const T* zc = stg.zrow(c);
+            P2 A[Q], A2[Q];   // (even, odd member) partial sums for x nodes h and h + 2
+#pragma unroll
+            for (int q = 0; q < Q; ++q) A[q] = A2[q] = zero;
+            auto single = [&](int m) {
+                const T wyz = yb[m] * zc[m];
+                const T w0 = xh[m] * wyz, w1 = xh2[m] * wyz;
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const T v = (Q == 3) ? stg.vrow(q)[m] : (T)1;
+                    A[q].x = fma(w0, v, A[q].x);
+                    A2[q].x = fma(w1, v, A2[q].x);
+                }
+            };
+            auto pair = [&](int m) {
+                const P2 wyz = pmul(ld2(yb + m), ld2(zc + m));
+                const P2 w0 = pmul(ld2(xh + m), wyz);
+                const P2 w1 = pmul(ld2(xh2 + m), wyz);
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const P2 v = (Q == 3) ? ld2(stg.vrow(q) + m) : one;
+                    A[q] = pfma(w0, v, A[q]);
+                    A2[q] = pfma(w1, v, A2[q]);
+                }
+            };
+            if (run) {
+                int m = lo;
+                const int me = lo + len;
+                if (m & 1) single(m++);
+                for (; m + 1 < me; m += 2) pair(m);
+                if (m < me) single(m);
+            } else {
+                unsigned g = grp;
+                while (g) {
+                    const int m = __ffs(g) - 1;
+                    g &= g - 1;
+                    single(m);
+                }
+            }
+            const int n0 = gkey + (h * TE + b) * TE + c;
+            const int n1 = n0 + 2 * TE * TE;
+            T* addr[2 * Q];
+            T val[2 * Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                addr[2 * q] = &sD[(q0 + q) * R + n0];
+                addr[2 * q + 1] = &sD[(q0 + q) * R + n1];
+                val[2 * q] = (A[q].x + A[q].y) * qw;
+                val[2 * q + 1] = (A2[q].x + A2[q].y) * qw;
+            }
+            smem_add_batch<T, 2 * Q>(addr, val);
+        } else {
+            // NW == 2: lane -> (component q = lane / 8, node j = lane % 8)
+            if (lane < 8 * Q) {
+                const int q = lane >> 3, j = lane & 7;
+                const int ax = j >> 2, by = (j >> 1) & 1, cz = j & 1;
+                const T* xa = stg.xrow(ax);
+                const T* yb = stg.yrow(by);
+                const T* zc = stg.zrow(cz);
+                const T* vq = stg.vrow(Q == 3 ? q : 0);
+                P2 A = zero;
+                if (run) {
+                    int m = lo;
+                    const int me = lo + len;
+                    if (m & 1) {
+                        A.x = fma(xa[m] * yb[m] * zc[m], (Q == 3) ? vq[m] : (T)1, A.x);
+                        ++m;
+                    }
+                    for (; m + 1 < me; m += 2) {
+                        const P2 w = pmul(pmul(ld2(xa + m), ld2(yb + m)), ld2(zc + m));
+                        A = pfma(w, (Q == 3) ? ld2(vq + m) : one, A);
+                    }
+                    if (m < me) A.x = fma(xa[m] * yb[m] * zc[m], (Q == 3) ? vq[m] : (T)1, A.x);
+                } else {
+                    unsigned g = grp;
+                    while (g) {
+                        const int m = __ffs(g) - 1;
+                        g &= g - 1;
+                        A.x = fma(xa[m] * yb[m] * zc[m], (Q == 3) ? vq[m] : (T)1, A.x);
+                    }
+                }
+                T* addr[1] = {&sD[(q0 + q) * R + gkey + (ax * TE + by) * TE + cz]};
+                const T val[1] = {(A.x + A.y) * qw};
+                smem_add_batch<T, 1>(addr, val);
+            }
+        }
+    }
+}
+
+// Combined J and rho deposit of one warp for linear stencils (NW = 2). Members are
+// grouped by the start `key` of their J stencil; lane q * 8 + j takes component q
+// (Jx, Jy, Jz, rho) at node j = (a, b, c) of the 2x2x2 stencil, so every lane works
+// on every group. The rho lanes read the x^{n+1} weights and, as the value, the
+// member's flag: 1 when its rho stencil starts at its J stencil's node (the normal
+// case), 0 otherwise (that member's rho goes through a separate rho-only pass).
+// Every lane of the warp must call this (warp-collective).
+template <typename T, int TE>
+__device__ void group_deposit_jr(T* sD, const Stage<T, 2>& stg, bool member, int key, int lane, T qw) {
+    typedef typename Pair<T>::type P2;
+    constexpr int R = TE * TE * TE;
+    const int q = lane >> 3, j = lane & 7;
+    const int ax = j >> 2, by = (j >> 1) & 1, cz = j & 1;
+    const bool rho = q == 3;
+    const T* xa = rho ? stg.xRrow(ax) : stg.xrow(ax);
+    const T* yb = rho ? stg.yRrow(by) : stg.yrow(by);
+    const T* zc = rho ? stg.zRrow(cz) : stg.zrow(cz);
+    const T* vq = rho ? stg.frow() : stg.vrow(q);
+    T* const dst = sD + q * R + (ax * TE + by) * TE + cz;
+    unsigned pending = __ballot_sync(0xffffffffu, member);
+    while (pending) {
+        const int leader = __ffs(pending) - 1;
+        const int gkey = __shfl_sync(0xffffffffu, key, leader);
+        const unsigned grp = __ballot_sync(0xffffffffu, member && key == gkey);
+        pending &= ~grp;
+        const int lo = __ffs(grp) - 1;
+        const int len = __popc(grp);
+        const bool run = (grp >> lo) == (len == 32 ? 0xffffffffu : ((1u << len) - 1u));   // warp-uniform
+        P2 A = Pair<T>::make((T)0, (T)0);
+        if (run) {
+            int m = lo;
+            const int me = lo + len;
+            if (m & 1) {
+                A.x = fma(xa[m] * yb[m] * zc[m], vq[m], A.x);
+                ++m;
+            }
+            for (; m + 1 < me; m += 2) {
+                const P2 w = pmul(pmul(ld2(xa + m), ld2(yb + m)), ld2(zc + m));
+                A = pfma(w, ld2(vq + m), A);
+            }
+            if (m < me) A.x = fma(xa[m] * yb[m] * zc[m], vq[m], A.x);
+        } else {
+            unsigned g = grp;
+            while (g) {
+                const int m = __ffs(g) - 1;
+                g &= g - 1;
+                A.x = fma(xa[m] * yb[m] * zc[m], vq[m], A.x);
+            }
+        }
+        T* addr[1] = {dst + gkey};
+        const T val[1] = {(A.x + A.y) * qw};
+        smem_add_batch<T, 1>(addr, val);
+    }
+}
+
+// Stage this lane's weights (and, for J, its velocity) in its column of the rows.
+template <typename T, int NW>
+__device__ __forceinline__ void stage_record(const Stage<T, NW>& stg, int lane, const T* wx, const T* wy,
+                                             const T* wz, const T* vel) {
+    if (vel) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) stg.vrow(q)[lane] = vel[q];
+    }
+#pragma unroll
+    for (int a = 0; a < NW; ++a) {
+        stg.xrow(a)[lane] = wx[a];
+        stg.yrow(a)[lane] = wy[a];
+        stg.zrow(a)[lane] = wz[a];
+    }
+}
+
+// Stage this lane's block of the row deposit (see RowStage).
+__device__ __forceinline__ void row_record(float* blk, const float* wxJ, const float* wyJ, const float* wzJ,
+                                           const float* wxR, const float* wyR, const float* wzR,
+                                           float qvx, float qvy, float qvz, float qw) {
+    float4* q = reinterpret_cast<float4*>(blk);
+#pragma unroll
+    for (int a = 0; a < 4; a += 2) {
+        q[a / 2] = make_float4(wxJ[a] * qvx, wxJ[a] * qvy, wxJ[a + 1] * qvx, wxJ[a + 1] * qvy);
+        q[2 + a / 2] = make_float4(wxJ[a] * qvz, wxR[a] * qw, wxJ[a + 1] * qvz, wxR[a + 1] * qw);
+        q[4 + a / 2] = make_float4(wyJ[a], wyJ[a], wyJ[a + 1], wyJ[a + 1]);
+        q[6 + a / 2] = make_float4(wyJ[a], wyR[a], wyJ[a + 1], wyR[a + 1]);
+        q[8 + a / 2] = make_float4(wzJ[a], wzJ[a], wzJ[a + 1], wzJ[a + 1]);
+        q[10 + a / 2] = make_float4(wzJ[a], wzR[a], wzJ[a + 1], wzR[a + 1]);
+    }
+}
+
+// Adds acc[z].x / acc[z].y to two shared-memory rows p0[z], p1[z] for z in
+// [zlo, zhi], in chunks of four nodes: all reads, then all compare-and-swaps, then
+// the retries of those that lost a race (shared-memory float atomics are
+// compare-and-swap loops on this GPU).
+template <int TE>
+__device__ __forceinline__ void row_flush(unsigned* p0, unsigned* p1, const float2 (&acc)[TE], int zlo, int zhi) {
+#pragma unroll
+    for (int z0 = 0; z0 < TE; z0 += 4) {
+        unsigned o0[4], o1[4];
+        bool d0[4], d1[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int z = z0 + k;
+            d0[k] = d1[k] = true;
+            if (z < TE && z >= zlo && z <= zhi) {
+                o0[k] = *reinterpret_cast<volatile unsigned*>(p0 + z);
+                o1[k] = *reinterpret_cast<volatile unsigned*>(p1 + z);
+                d0[k] = d1[k] = false;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int z = z0 + k;
+            if (z < TE && !d0[k]) {
+                unsigned prev = atomicCAS(p0 + z, o0[k], __float_as_uint(__uint_as_float(o0[k]) + acc[z].x));
+                d0[k] = prev == o0[k];
+                o0[k] = prev;
+                prev = atomicCAS(p1 + z, o1[k], __float_as_uint(__uint_as_float(o1[k]) + acc[z].y));
+                d1[k] = prev == o1[k];
+                o1[k] = prev;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int z = z0 + k;
+            if (z >= TE) continue;
+            while (!d0[k]) {   // lost a race with another warp: retry (lock-free, always progresses)
+                const unsigned prev = atomicCAS(p0 + z, o0[k], __float_as_uint(__uint_as_float(o0[k]) + acc[z].x));
+                d0[k] = prev == o0[k];
+                o0[k] = prev;
+            }
+            while (!d1[k]) {
+                const unsigned prev = atomicCAS(p1 + z, o1[k], __float_as_uint(__uint_as_float(o1[k]) + acc[z].y));
+                d1[k] = prev == o1[k];
+                o1[k] = prev;
+            }
+        }
+    }
+}
+
+// Row deposit of one warp (FP32, NW = 4, tile extent TE): the strategy for few
+// particles per cell. Members are grouped by the (x, y) start of their stencil in
+// the tile (`row` = rx * TE + ry), so the particles of a whole row of cells form
+// one group. For a row, lane (h, a, b) = (lane >> 4, (lane >> 2) & 3, lane & 3)
+// owns the tile nodes (rx + a, ry + b, z) for every z and two components, (Jx, Jy)
+// for h = 0 and (Jz, rho) for h = 1, summed in registers as packed pairs: a member
+// whose stencil starts at z node j adds its staged x-weight-times-value pair times
+// its y-weight pair times z-weight pair c to node j + c (one packed multiply, four
+// packed FMAs). J (stencil at x^{n+1/2}) and rho (at x^{n+1}) of a particle normally
+// start at the same node; where they do not, the particle joins two (row, j) groups
+// with the other part zeroed. Each row's sums go to the shared tile once, over the
+// z range it touched. mJ / mR: this lane's J / rho stencil lies in the tile; zJ /
+// zR: its z start. Every lane of the warp must call this (warp-collective).
+template <int TE>
+__device__ void row_deposit(float* sD, const float* stg, bool mJ, int rowJ, int zJ, bool mR, int rowR, int zR,
+                            int lane) {
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int R = TE * TE * TE;
+    constexpr int NS = TE - 3;   // stencil starts along z
+    constexpr int M = RowStage::MEMBER;
+    const int h = lane >> 4, a = (lane >> 2) & 3, b = lane & 3;
+    const bool hi = h != 0;
+    const float* sx = stg + RowStage::XV + 8 * h + 2 * a;
+    const float* sy = stg + RowStage::Y + 8 * h + 2 * b;
+    const float* sz = stg + RowStage::Z + 8 * h;
+    unsigned pendJ = __ballot_sync(FULL, mJ), pendR = __ballot_sync(FULL, mR);
+    while (pendJ | pendR) {
+        const int leader = __ffs(pendJ ? pendJ : pendR) - 1;
+        const int cur = __shfl_sync(FULL, pendJ ? rowJ : rowR, leader);
+        const bool inJ = mJ && rowJ == cur, inR = mR && rowR == cur;
+        const unsigned gJ = __ballot_sync(FULL, inJ), gR = __ballot_sync(FULL, inR);
+        pendJ &= ~gJ;
+        pendR &= ~gR;
+        const unsigned zs = __reduce_or_sync(FULL, (inJ ? 1u << zJ : 0u) | (inR ? 1u << zR : 0u));
+        float2 acc[TE];
+#pragma unroll
+        for (int z = 0; z < TE; ++z) acc[z] = make_float2(0.f, 0.f);
+        auto coef = [&](int m) { return pmul(ld2(sx + m * M), ld2(sy + m * M)); };
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+            if (!((zs >> j) & 1u)) continue;
+            const unsigned sJ = __ballot_sync(FULL, inJ && zJ == j);
+            const unsigned sR = __ballot_sync(FULL, inR && zR == j);
+            auto add = [&](int m, float2 c) {
+                const float4 z01 = *reinterpret_cast<const float4*>(sz + m * M);
+                const float4 z23 = *reinterpret_cast<const float4*>(sz + m * M + 4);
+                acc[j + 0] = pfma(c, make_float2(z01.x, z01.y), acc[j + 0]);
+                acc[j + 1] = pfma(c, make_float2(z01.z, z01.w), acc[j + 1]);
+                acc[j + 2] = pfma(c, make_float2(z23.x, z23.y), acc[j + 2]);
+                acc[j + 3] = pfma(c, make_float2(z23.z, z23.w), acc[j + 3]);
+            };
+            // members whose J and rho both start here, two at a time; cell-sorted
+            // particles make them one run of consecutive lanes
+            unsigned mm = sJ & sR;
+            if (mm) {
+                const int lo = __ffs(mm) - 1, len = __popc(mm);
+                if ((mm >> lo) == (len == 32 ? FULL : ((1u << len) - 1u))) {
+                    int m = lo;
+                    const int me = lo + len;
+                    for (; m + 1 < me; m += 2) {
+                        const float2 c1 = coef(m), c2 = coef(m + 1);
+                        add(m, c1);
+                        add(m + 1, c2);
+                    }
+                    if (m < me) add(m, coef(m));
+                } else {
+                    while (mm) {
+                        const int m = __ffs(mm) - 1;
+                        mm &= mm - 1;
+                        add(m, coef(m));
+                    }
+                }
+            }
+            // members with only one of J, rho starting here: zero the other part
+            unsigned rr = (sJ | sR) & ~(sJ & sR);
+            while (rr) {
+                const int k = __ffs(rr) - 1;
+                rr &= rr - 1;
+                const float fJ = ((sJ >> k) & 1u) ? 1.f : 0.f, fR = ((sR >> k) & 1u) ? 1.f : 0.f;
+                add(k, pmul(coef(k), make_float2(fJ, hi ? fR : fJ)));
+            }
+        }
+        // add the row to the tile: nodes (rx + a, ry + b, z) over the touched z range
+        const int zlo = __ffs(zs) - 1, zhi = 31 - __clz(zs) + 3;
+        const int node0 = (cur + a * TE + b) * TE;
+        row_flush<TE>(reinterpret_cast<unsigned*>(sD + (2 * h) * R + node0),
+                      reinterpret_cast<unsigned*>(sD + (2 * h + 1) * R + node0), acc, zlo, zhi);
+    }
+}
+
+template <typename T, int ORDER, int MODE, int MARGIN, int DEP>
+__device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
+    typedef Shape<ORDER> SH;
+    typedef typename Pair<T>::type P2;
+    constexpr int NW = SH::NW;
+    constexpr int TE = TileGeom<NW, MARGIN>::E;
+    constexpr int R = TileGeom<NW, MARGIN>::R;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const PassSmem L(R, NW, sizeof(T), MODE == PASS_STEP, DEP);
+    static_assert(DEP == DEP_GROUP || (sizeof(T) == 4 && NW == 4), "row deposit: FP32, NW = 4 only");
+    FieldTile<T> tile;
+    tile.init(smem_raw + L.tile, R);
+    T* sD = reinterpret_cast<T*>(smem_raw + L.dep);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    Stage<T, NW> stg;
+    stg.base = reinterpret_cast<T*>(smem_raw + L.stage + warp * stage_bytes(NW, sizeof(T), DEP));
+    float* const rstg = reinterpret_cast<float*>(stg.base);
+
+    const int b = blockIdx.x;
+    const int bz = b % p.nbz, by = (b / p.nbz) % p.nby, bx = b / (p.nbz * p.nby);
+    const int x0 = bx * BIN, y0 = by * BIN, z0 = bz * BIN;
+    // global node of tile index 0 along each axis
+    const int ox = x0 + SH::J0 - MARGIN, oy = y0 + SH::J0 - MARGIN, oz = z0 + SH::J0 - MARGIN;
+    const int64_t N = p.N;
+
+    for (int idx = threadIdx.x; idx < R; idx += blockDim.x) {
+        const int rx = idx / (TE * TE);
+        const int rem = idx - rx * (TE * TE);
+        const int ry = rem / TE;
+        const int rz = rem - ry * TE;
+        if (MODE == PASS_STEP) {
+            int64_t g = ((int64_t)wrap_near(ox + rx, p.nx) * p.ny + wrap_near(oy + ry, p.ny)) * p.nz +
+                        wrap_near(oz + rz, p.nz);
+            T v[6];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) v[q] = p.F[q * N + g];
+            tile.store(idx, v);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sD[q * R + idx] = (T)0;
+    }
+    __syncthreads();
+
+    unsigned long long miss = 0, far = 0;
+    for (int s = 0; s < p.nspecies; ++s) {
+        const SpeciesK<T> sp = p.sp[s];
+        const int beg = sp.bin_start[b], end = sp.bin_start[b + 1];
+        // the next chunk's particle is loaded while the current one is processed
+        int c_n = 0;
+        T f_n[3] = {0, 0, 0}, u_n[3] = {0, 0, 0};
+        if (beg + (int)threadIdx.x < end) {
+            const int j = beg + threadIdx.x;
+            c_n = sp.cell[j];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                f_n[d] = sp.off[d][j];
+                u_n[d] = sp.u[d][j];
+            }
+        }
+        for (int base = beg; base < end; base += PASS_THREADS) {
+            const int i = base + threadIdx.x;
+            const bool valid = i < end;
+            int ix = 0, iy = 0, iz = 0, rx = -1, ry = -1, rz = -1;
+            T fx = f_n[0], fy = f_n[1], fz = f_n[2], ux = u_n[0], uy = u_n[1], uz = u_n[2];
+            const int c = c_n;
+            if (i + PASS_THREADS < end) {
+                const int j = i + PASS_THREADS;
+                c_n = sp.cell[j];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    f_n[d] = sp.off[d][j];
+                    u_n[d] = sp.u[d][j];
+                }
+            }
+            T wx[4], wy[4], wz[4];
+            T vx = 0, vy = 0, vz = 0;
+            if (valid) {
+                ix = p.div_nynz.div(c);
+                const int rem = c - ix * (p.ny * p.nz);
+                iy = p.div_nz.div(rem);
+                iz = rem - iy * p.nz;
+                rx = ix - x0 + MARGIN;
+                ry = iy - y0 + MARGIN;
+                rz = iz - z0 + MARGIN;
+                if (MODE == PASS_STEP) {
+                    // ---- gather E^n, B^n at x^n
+                    SH::w(fx, wx);
+                    SH::w(fy, wy);
+                    SH::w(fz, wz);
+                    T E[3], B[3];
+                    if (in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz)) {
+                        // two interleaved accumulator sets (even / odd z node) for ILP
+                        P2 a0 = Pair<T>::make(0, 0), a1 = a0, a2 = a0, c0 = a0, c1 = a0, c2 = a0;
+                        P2 wzp[NW];
+#pragma unroll
+                        for (int cc = 0; cc < NW; ++cc) wzp[cc] = Pair<T>::make(wz[cc], wz[cc]);
+#pragma unroll
+                        for (int a = 0; a < NW; ++a)
+#pragma unroll
+                            for (int bb = 0; bb < NW; ++bb) {
+                                const T wxy = wx[a] * wy[bb];
+                                const P2 wxyp = Pair<T>::make(wxy, wxy);
+                                const int base_t = ((rx + a) * TE + (ry + bb)) * TE + rz;
+#pragma unroll
+                                for (int cc = 0; cc < NW; ++cc) {
+                                    const P2 w2 = pmul(wxyp, wzp[cc]);
+                                    P2 f0, f1, f2;
+                                    tile.load(base_t + cc, f0, f1, f2);
+                                    if (cc & 1) {
+                                        c0 = pfma(w2, f0, c0);
+                                        c1 = pfma(w2, f1, c1);
+                                        c2 = pfma(w2, f2, c2);
+                                    } else {
+                                        a0 = pfma(w2, f0, a0);
+                                        a1 = pfma(w2, f1, a1);
+                                        a2 = pfma(w2, f2, a2);
+                                    }
+                                }
+                            }
+                        E[0] = a0.x + c0.x; E[1] = a0.y + c0.y; E[2] = a1.x + c1.x;
+                        B[0] = a1.y + c1.y; B[1] = a2.x + c2.x; B[2] = a2.y + c2.y;
+                    } else {
+                        far++;
+                        for (int q = 0; q < 3; ++q) E[q] = B[q] = (T)0;
+#pragma unroll
+                        for (int a = 0; a < NW; ++a)
+#pragma unroll
+                            for (int bb = 0; bb < NW; ++bb) {
+                                const T wxy = wx[a] * wy[bb];
+                                const int64_t gb = ((int64_t)wrapf<NW>(ix + SH::J0 + a, p.nx) * p.ny +
+                                                    wrapf<NW>(iy + SH::J0 + bb, p.ny)) * p.nz;
+#pragma unroll
+                                for (int cc = 0; cc < NW; ++cc) {
+                                    const T w = wxy * wz[cc];
+                                    const int64_t g = gb + wrapf<NW>(iz + SH::J0 + cc, p.nz);
+                                    E[0] += w * p.F[0 * N + g];
+                                    E[1] += w * p.F[1 * N + g];
+                                    E[2] += w * p.F[2 * N + g];
+                                    B[0] += w * p.F[3 * N + g];
+                                    B[1] += w * p.F[4 * N + g];
+                                    B[2] += w * p.F[5 * N + g];
+                                }
+                            }
+                    }
+                    // ---- relativistic Boris push u^{n-1/2} -> u^{n+1/2}
+                    const T a = sp.qdt2m;
+                    const T umx = ux + a * E[0], umy = uy + a * E[1], umz = uz + a * E[2];
+                    const T igm = (T)1 / sqrt((T)1 + (umx * umx + umy * umy + umz * umz) * p.inv_c2);
+                    const T tx = a * B[0] * igm, ty = a * B[1] * igm, tz = a * B[2] * igm;
+                    const T s2 = (T)2 / ((T)1 + tx * tx + ty * ty + tz * tz);
+                    const T sx = s2 * tx, sy = s2 * ty, sz = s2 * tz;
+                    const T upx = umx + (umy * tz - umz * ty);
+                    const T upy = umy + (umz * tx - umx * tz);
+                    const T upz = umz + (umx * ty - umy * tx);
+                    ux = umx + (upy * sz - upz * sy) + a * E[0];
+                    uy = umy + (upz * sx - upx * sz) + a * E[1];
+                    uz = umz + (upx * sy - upy * sx) + a * E[2];
+                }
+                const T igam = (T)1 / sqrt((T)1 + (ux * ux + uy * uy + uz * uz) * p.inv_c2);
+                vx = ux * igam;
+                vy = uy * igam;
+                vz = uz * igam;
+            }
+            // ---- deposit J (phase 0: at x^{n+1/2} with v^{n+1/2}) and rho (phase 1:
+            // at x^{n+1}); DEPOSIT mode: both at the current x
+            if constexpr (NW == 2) {
+                // linear: both stencils first, then one combined pass (see group_deposit_jr)
+                bool mJ = false, mR = false, same = false;
+                int keyJ = 0, keyR = 0;
+                T wxR[2], wyR[2], wzR[2];
+                if (valid) {
+                    if (MODE == PASS_STEP) {
+                        rx += drift_axis(ix, fx, (vx - p.vgal[0]) * p.hd[0], p.nx);
+                        ry += drift_axis(iy, fy, (vy - p.vgal[1]) * p.hd[1], p.ny);
+                        rz += drift_axis(iz, fz, (vz - p.vgal[2]) * p.hd[2], p.nz);
+                    }
+                    SH::w(fx, wx);
+                    SH::w(fy, wy);
+                    SH::w(fz, wz);
+                    mJ = in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz);
+                    if (mJ) {
+                        keyJ = (rx * TE + ry) * TE + rz;
+                    } else {
+                        const T val[3] = {sp.qw_dv * vx, sp.qw_dv * vy, sp.qw_dv * vz};
+                        deposit_global<T, NW, SH::J0>(p, ix, iy, iz, wx, wy, wz, 0, 3, val);
+                    }
+                    if (MODE == PASS_STEP) {
+                        rx += drift_axis(ix, fx, (vx - p.vgal[0]) * p.hd[0], p.nx);
+                        ry += drift_axis(iy, fy, (vy - p.vgal[1]) * p.hd[1], p.ny);
+                        rz += drift_axis(iz, fz, (vz - p.vgal[2]) * p.hd[2], p.nz);
+                        SH::w(fx, wxR);
+                        SH::w(fy, wyR);
+                        SH::w(fz, wzR);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < NW; ++q) {
+                            wxR[q] = wx[q];
+                            wyR[q] = wy[q];
+                            wzR[q] = wz[q];
+                        }
+                    }
+                    mR = in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz);
+                    if (mR) {
+                        keyR = (rx * TE + ry) * TE + rz;
+                    } else {
+                        far++;
+                        const T val[1] = {sp.qw_dv};
+                        deposit_global<T, NW, SH::J0>(p, ix, iy, iz, wxR, wyR, wzR, 3, 1, val);
+                    }
+                    same = mJ && mR && keyR == keyJ;
+                    if (mJ) {
+                        const T vel[3] = {vx, vy, vz};
+                        stage_record<T, NW>(stg, lane, wx, wy, wz, vel);
+                        stg.frow()[lane] = same ? (T)1 : (T)0;
+#pragma unroll
+                        for (int a = 0; a < NW; ++a) {
+                            stg.xRrow(a)[lane] = wxR[a];
+                            stg.yRrow(a)[lane] = wyR[a];
+                            stg.zRrow(a)[lane] = wzR[a];
+                        }
+                    }
+                }
+                __syncwarp();
+                group_deposit_jr<T, TE>(sD, stg, mJ, keyJ, lane, sp.qw_dv);
+                __syncwarp();
+                // rho of members whose rho stencil starts elsewhere
+                const bool restR = mR && !same;
+                if (__any_sync(0xffffffffu, restR)) {
+                    if (restR) stage_record<T, NW>(stg, lane, wxR, wyR, wzR, nullptr);
+                    __syncwarp();
+                    group_deposit<T, NW, 1, TE>(sD, stg, restR, keyR, lane, sp.qw_dv);
+                    __syncwarp();
+                }
+            } else if constexpr (DEP == DEP_ROW) {
+                // few particles per cell: both stencils first, then one pass by stencil row
+                bool mJ = false, mR = false;
+                int rowJ = 0, zJ = 0, rowR = 0, zR = 0;
+                if (valid) {
+                    if (MODE == PASS_STEP) {
+                        rx += drift_axis(ix, fx, (vx - p.vgal[0]) * p.hd[0], p.nx);
+                        ry += drift_axis(iy, fy, (vy - p.vgal[1]) * p.hd[1], p.ny);
+                        rz += drift_axis(iz, fz, (vz - p.vgal[2]) * p.hd[2], p.nz);
+                    }
+                    SH::w(fx, wx);
+                    SH::w(fy, wy);
+                    SH::w(fz, wz);
+                    const T qvx = sp.qw_dv * vx, qvy = sp.qw_dv * vy, qvz = sp.qw_dv * vz;
+                    mJ = in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz);
+                    if (mJ) {
+                        rowJ = rx * TE + ry;
+                        zJ = rz;
+                    } else {
+                        const T val[3] = {qvx, qvy, qvz};
+                        deposit_global<T, NW, SH::J0>(p, ix, iy, iz, wx, wy, wz, 0, 3, val);
+                    }
+                    T wxR[NW], wyR[NW], wzR[NW];
+                    if (MODE == PASS_STEP) {
+                        rx += drift_axis(ix, fx, (vx - p.vgal[0]) * p.hd[0], p.nx);
+                        ry += drift_axis(iy, fy, (vy - p.vgal[1]) * p.hd[1], p.ny);
+                        rz += drift_axis(iz, fz, (vz - p.vgal[2]) * p.hd[2], p.nz);
+                        SH::w(fx, wxR);
+                        SH::w(fy, wyR);
+                        SH::w(fz, wzR);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < NW; ++q) {
+                            wxR[q] = wx[q];
+                            wyR[q] = wy[q];
+                            wzR[q] = wz[q];
+                        }
+                    }
+                    mR = in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz);
+                    if (mR) {
+                        rowR = rx * TE + ry;
+                        zR = rz;
+                    } else {
+                        far++;
+                        const T val[1] = {sp.qw_dv};
+                        deposit_global<T, NW, SH::J0>(p, ix, iy, iz, wxR, wyR, wzR, 3, 1, val);
+                    }
+                    if (mJ || mR)
+                        row_record(rstg + lane * RowStage::MEMBER, (const float*)wx, (const float*)wy,
+                                   (const float*)wz, (const float*)wxR, (const float*)wyR, (const float*)wzR,
+                                   (float)qvx, (float)qvy, (float)qvz, (float)sp.qw_dv);
+                }
+                __syncwarp();
+                row_deposit<TE>(reinterpret_cast<float*>(sD), rstg, mJ, rowJ, zJ, mR, rowR, zR, lane);
+                __syncwarp();
+            } else
+#pragma unroll
+            for (int phase = 0; phase < 2; ++phase) {
+                bool member = false;
+                int key = 0;
+                if (valid) {
+                    if (MODE == PASS_STEP) {
+                        rx += drift_axis(ix, fx, (vx - p.vgal[0]) * p.hd[0], p.nx);
+                        ry += drift_axis(iy, fy, (vy - p.vgal[1]) * p.hd[1], p.ny);
+                        rz += drift_axis(iz, fz, (vz - p.vgal[2]) * p.hd[2], p.nz);
+                    }
+                    if (MODE == PASS_STEP || phase == 0) {
+                        SH::w(fx, wx);
+                        SH::w(fy, wy);
+                        SH::w(fz, wz);
+                    }
+                    T val[3];
+                    if (phase == 0) {
+                        val[0] = sp.qw_dv * vx;
+                        val[1] = sp.qw_dv * vy;
+                        val[2] = sp.qw_dv * vz;
+                    } else {
+                        val[0] = sp.qw_dv;
+                        val[1] = val[2] = (T)0;
+                    }
+                    if (in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz)) {
+                        member = true;
+                        key = (rx * TE + ry) * TE + rz;
+                        const T vel[3] = {vx, vy, vz};
+                        stage_record<T, NW>(stg, lane, wx, wy, wz, phase == 0 ? vel : nullptr);
+                    } else {
+                        if (phase == 1) far++;
+                        if (phase == 0)
+                            deposit_global<T, NW, SH::J0>(p, ix, iy, iz, wx, wy, wz, 0, 3, val);
+                        else
+                            deposit_global<T, NW, SH::J0>(p, ix, iy, iz, wx, wy, wz, 3, 1, val);
+                    }
+                }
+                __syncwarp();
+                if (phase == 0)
+                    group_deposit<T, NW, 3, TE>(sD, stg, member, key, lane, sp.qw_dv);
+                else
+                    group_deposit<T, NW, 1, TE>(sD, stg, member, key, lane, sp.qw_dv);
+                __syncwarp();
+            }
+            if (valid && MODE == PASS_STEP) {
+                sp.cell[i] = (ix * p.ny + iy) * p.nz + iz;
+                sp.off[0][i] = fx;
+                sp.off[1][i] = fy;
+                sp.off[2][i] = fz;
+                sp.u[0][i] = ux;
+                sp.u[1][i] = uy;
+                sp.u[2][i] = uz;
+                if (ix < x0 || ix >= x0 + BIN || iy < y0 || iy >= y0 + BIN || iz < z0 || iz >= z0 + BIN)
+                    miss++;
+            }
+        }
+    }
+    __syncthreads();
+
+    // add the tile to the global source grids
+    for (int idx = threadIdx.x; idx < R; idx += blockDim.x) {
+        const int rx = idx / (TE * TE);
+        const int rem = idx - rx * (TE * TE);
+        const int ry = rem / TE;
+        const int rz = rem - ry * TE;
+        int64_t g = ((int64_t)wrap_near(ox + rx, p.nx) * p.ny + wrap_near(oy + ry, p.ny)) * p.nz +
+                    wrap_near(oz + rz, p.nz);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            T v = sD[q * R + idx];
+            if (v != (T)0) atomicAdd(&p.S[q * N + g], v);
+        }
+    }
+
+    if (MODE == PASS_STEP) {
+        for (int o = 16; o > 0; o >>= 1) {
+            miss += __shfl_down_sync(0xffffffffu, miss, o);
+            far += __shfl_down_sync(0xffffffffu, far, o);
+        }
+        if (lane == 0) {
+            if (miss) atomicAdd(&p.cnt[CNT_HOME_MISS], miss);
+            if (far) atomicAdd(&p.cnt[CNT_FAR], far);
+        }
+    }
+}
+
+// One CTA per bin. FP32 linear passes and FP32 grouped quadratic/cubic steps at tile
+// margin 0 fit three CTAs per SM by shared memory and have their registers held to
+// that; row-deposit passes are held to two; the others are left to the compiler.
+template <typename T, int ORDER, int MODE, int MARGIN, int DEP>
+__global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p) {
+    particle_pass_body<T, ORDER, MODE, MARGIN, DEP>(p);
+}
+
+template <typename T, int ORDER, int MODE, int MARGIN, int DEP>
+__global__ void __launch_bounds__(PASS_THREADS, 3) particle_pass_kernel_3(PassK<T> p) {
+    particle_pass_body<T, ORDER, MODE, MARGIN, DEP>(p);
+}
+
+template <typename T, int ORDER, int MODE, int MARGIN, int DEP>
+__global__ void __launch_bounds__(PASS_THREADS, 2) particle_pass_kernel_2(PassK<T> p) {
+    particle_pass_body<T, ORDER, MODE, MARGIN, DEP>(p);
+}
+
+template <typename T, int ORDER, int MODE, int MARGIN, int DEP>
+int pass_launch(pic_sim* s, cudaStream_t st) {
+    const pic_config& c = s->cfg;
+    PassK<T> p;
+    p.F = (const T*)s->F;
+    p.S = (T*)s->S;
+    p.N = s->d.N;
+    p.nx = s->d.nx;
+    p.ny = s->d.ny;
+    p.nz = s->d.nz;
+    p.nbx = s->d.nbx;
+    p.nby = s->d.nby;
+    p.nbz = s->d.nbz;
+    p.div_nynz.init((uint32_t)(s->d.ny * s->d.nz));
+    p.div_nz.init((uint32_t)s->d.nz);
+    p.inv_c2 = (T)(1.0 / (c.c * c.c));
+    p.hd[0] = (T)(0.5 * c.dt / c.dx);
+    p.hd[1] = (T)(0.5 * c.dt / c.dy);
+    p.hd[2] = (T)(0.5 * c.dt / c.dz);
+    for (int d = 0; d < 3; ++d) p.vgal[d] = (T)c.vgal[d];
+    p.nspecies = s->nspecies;
+    const double dV = c.dx * c.dy * c.dz;
+    for (int k = 0; k < s->nspecies; ++k) {
+        const SpeciesDev& sp = s->sp[k];
+        p.sp[k].cell = sp.cell;
+        for (int d = 0; d < 3; ++d) {
+            p.sp[k].off[d] = (T*)sp.off[d];
+            p.sp[k].u[d] = (T*)sp.u[d];
+        }
+        p.sp[k].bin_start = sp.bin_start;
+        p.sp[k].qw_dv = (T)(sp.q * sp.w / dV);
+        p.sp[k].qdt2m = (T)(sp.q * c.dt / (2.0 * sp.m));
+    }
+    p.cnt = s->cnt;
+    const PassSmem L(TileGeom<Shape<ORDER>::NW, MARGIN>::R, Shape<ORDER>::NW, sizeof(T), MODE == PASS_STEP, DEP);
+    // FP32 grouped quadratic/cubic steps at tile margin 0 (70 KB of shared memory) run
+    // three CTAs per SM: registers held to 80 (a few spill) and the largest shared
+    // memory carve-out; measured 48.1 against 51.2 ms at two CTAs on the 256x256x512
+    // cubic plasma.
+    constexpr bool three = sizeof(T) == 4 && ORDER >= 2 && MARGIN == 0 && DEP == DEP_GROUP &&
+                           MODE == PASS_STEP;
+    void (*kern)(PassK<T>);
+    if constexpr (sizeof(T) == 4 && (ORDER == 1 || three))
+        kern = particle_pass_kernel_3<T, ORDER, MODE, MARGIN, DEP>;
+    else if constexpr (DEP == DEP_ROW)
+        kern = particle_pass_kernel_2<T, ORDER, MODE, MARGIN, DEP>;
+    else
+        kern = particle_pass_kernel<T, ORDER, MODE, MARGIN, DEP>;
+    GP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+    if constexpr (three)
+        GP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    kern<<<s->d.nbins, PASS_THREADS, L.total, st>>>(p);
+    GP_CUDA(cudaGetLastError());
+    return PIC_OK;
+}
+
+template <typename T, int ORDER, int MODE, int MARGIN>
+int pass_strategy(pic_sim* s, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        if (s->cfg.deposit == DEP_ROW) return pass_launch<T, ORDER, MODE, MARGIN, DEP_ROW>(s, st);
+    }
+    return pass_launch<T, ORDER, MODE, MARGIN, DEP_GROUP>(s, st);
+}
+
+template <typename T, int MODE, int MARGIN>
+int pass_order(pic_sim* s, cudaStream_t st) {
+    switch (s->cfg.shape_order) {
+        case 1: return pass_launch<T, 1, MODE, MARGIN, DEP_GROUP>(s, st);
+        case 2: return pass_strategy<T, 2, MODE, MARGIN>(s, st);
+        default: return pass_strategy<T, 3, MODE, MARGIN>(s, st);
+    }
+}
+
+template <typename T, int MODE>
+int pass_margin(pic_sim* s, cudaStream_t st) {
+    return s->d.margin == 0 ? pass_order<T, MODE, 0>(s, st) : pass_order<T, MODE, 1>(s, st);
+}
+
+}  // namespace
+
+}  // namespace galpic

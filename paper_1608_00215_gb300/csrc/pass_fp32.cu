@@ -1,0 +1,10 @@
+// float instantiations of the particle pass (pass.cuh).
+#include "pass.cuh"
+
+namespace galpic {
+
+int launch_pass_fp32(pic_sim* s, int mode, cudaStream_t st) {
+    return mode == PASS_STEP ? pass_margin<float, PASS_STEP>(s, st) : pass_margin<float, PASS_DEPOSIT>(s, st);
+}
+
+}  // namespace galpic

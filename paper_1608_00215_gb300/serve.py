@@ -62,6 +62,7 @@ class _Active:
     event: Optional[torch.cuda.Event] = None
     rec: RunRecord = None
     status: Optional[torch.Tensor] = None     # pinned int32 copy of the device status word
+    level: int = 0                            # priority level (0 = largest runs)
 
 
 def footprint(wl, precision: Optional[int] = None) -> int:
@@ -138,7 +139,8 @@ class ServeResult:
 def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_slots: int = 64,
           chunk: int = 25, precision: Optional[int] = None, device: str = "cuda",
           sleep: float = 2e-4, keep_final_state: bool = False, on_retire=None,
-          priorities: bool = True, admit_per_poll: int = 1) -> ServeResult:
+          priorities: bool = True, admit_per_poll: int = 1,
+          max_per_level: Optional[Sequence[int]] = (2, 4, 64, 64)) -> ServeResult:
     """Run all requests with continuous batching; returns per-run records.
 
     ``max_slots = 1`` gives the serial baseline on the same arrival trace.
@@ -148,6 +150,9 @@ def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_
     builds tables and may create FFT plans, so finished runs are retired in between).
     A run's finish time is taken on the device: the event after its last chunk,
     measured against an event recorded at the start.
+    ``max_per_level``: most runs of each priority level (0 = largest) active at once
+    (with ``priorities``): a large run fills the GPU alone, so more of them at once add
+    no throughput, only latency to every run sharing the device with them.
     """
     prange = torch.cuda.Stream.priority_range() if priorities else (0, 0)
     if hbm_budget is None:
@@ -216,6 +221,11 @@ def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_
         admitted = 0
         while wi < len(waiting) and len(active) < max_slots and admitted < admit_per_poll:
             r = waiting[wi]
+            lvl = priority_level(work[r.rid])
+            if priorities and max_per_level is not None and \
+                    sum(1 for a in active if a.level == lvl) >= max_per_level[lvl]:
+                wi += 1
+                continue
             if used + fps[r.rid] > hbm_budget:
                 if not priorities:
                     break
@@ -233,7 +243,8 @@ def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_
                 continue
             rec.start = time.perf_counter() - t0
             used += fps[r.rid]
-            a = _Active(r, sim, stream, 0, None, rec, torch.zeros(1, dtype=torch.int32).pin_memory())
+            a = _Active(r, sim, stream, 0, None, rec, torch.zeros(1, dtype=torch.int32).pin_memory(),
+                        priority_level(work[r.rid]))
             active.append(a)
             admitted += 1
             max_conc = max(max_conc, len(active))
