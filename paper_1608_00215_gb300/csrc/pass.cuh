@@ -400,7 +400,10 @@ __device__ __forceinline__ typename Pair<T>::type ld2(const T* p) {
 // (two at a time when the group is a contiguous run of lanes, the normal case for
 // cell-sorted particles) and add each role's sum to the shared tile once.
 // Every lane of the warp must call this (warp-collective).
-template <typename T, int NW, int Q, int TE>
+// PREMUL: the members' staged values already carry their charge factor (the J rows
+// hold q w v / dV, and for rho, row 0 holds q w / dV), so members of different
+// species can share a group; qw is then 1.
+template <typename T, int NW, int Q, int TE, bool PREMUL = false>
 __device__ void group_deposit(T* sD, const Stage<T, NW>& stg, bool member, int key, int lane, T qw) {
     typedef typename Pair<T>::type P2;
     constexpr int q0 = (Q == 3) ? 0 : 3;
@@ -431,7 +434,7 @@ __device__ void group_deposit(T* sD, const Stage<T, NW>& stg, bool member, int k
                 const T w0 = xh[m] * wyz, w1 = xh2[m] * wyz;
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
-                    const T v = (Q == 3) ? stg.vrow(q)[m] : (T)1;
+                    const T v = (Q == 3) ? stg.vrow(q)[m] : (PREMUL ? stg.vrow(0)[m] : (T)1);
                     A[q].x = fma(w0, v, A[q].x);
                     A2[q].x = fma(w1, v, A2[q].x);
                 }
@@ -442,7 +445,7 @@ __device__ void group_deposit(T* sD, const Stage<T, NW>& stg, bool member, int k
                 const P2 w1 = pmul(ld2(xh2 + m), wyz);
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
-                    const P2 v = (Q == 3) ? ld2(stg.vrow(q) + m) : one;
+                    const P2 v = (Q == 3) ? ld2(stg.vrow(q) + m) : (PREMUL ? ld2(stg.vrow(0) + m) : one);
                     A[q] = pfma(w0, v, A[q]);
                     A2[q] = pfma(w1, v, A2[q]);
                 }
@@ -454,11 +457,19 @@ __device__ void group_deposit(T* sD, const Stage<T, NW>& stg, bool member, int k
                 for (; m + 1 < me; m += 2) pair(m);
                 if (m < me) single(m);
             } else {
+                // several runs of consecutive lanes (e.g. one cell's particles of two
+                // species in the two half-warps): pairs within each run
                 unsigned g = grp;
                 while (g) {
-                    const int m = __ffs(g) - 1;
-                    g &= g - 1;
-                    single(m);
+                    const int r0 = __ffs(g) - 1;
+                    const unsigned inv = ~(g >> r0);
+                    const int rl = inv ? __ffs(inv) - 1 : 32 - r0;
+                    int m = r0;
+                    const int me = r0 + rl;
+                    if (m & 1) single(m++);
+                    for (; m + 1 < me; m += 2) pair(m);
+                    if (m < me) single(m);
+                    g &= rl == 32 ? 0u : ~(((1u << rl) - 1u) << r0);
                 }
             }
             const int n0 = gkey + (h * TE + b) * TE + c;
@@ -738,7 +749,7 @@ __device__ void row_deposit(float* sD, const float* stg, bool mJ, int rowJ, int 
     }
 }
 
-template <typename T, int ORDER, int MODE, int MARGIN, int DEP>
+template <typename T, int ORDER, int MODE, int MARGIN, int DEP, bool MIX>
 __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
     typedef Shape<ORDER> SH;
     typedef typename Pair<T>::type P2;
@@ -748,6 +759,7 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const PassSmem L(R, NW, sizeof(T), MODE == PASS_STEP, DEP);
     static_assert(DEP == DEP_GROUP || (sizeof(T) == 4 && NW == 4), "row deposit: FP32, NW = 4 only");
+    static_assert(!MIX || (NW == 4 && DEP == DEP_GROUP), "mixed-species groups: NW = 4, grouped deposit");
     FieldTile<T> tile;
     tile.init(smem_raw + L.tile, R);
     T* sD = reinterpret_cast<T*>(smem_raw + L.dep);
@@ -782,14 +794,24 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
     __syncthreads();
 
     unsigned long long miss = 0, far = 0;
-    for (int s = 0; s < p.nspecies; ++s) {
-        const SpeciesK<T> sp = p.sp[s];
+    // MIX (two species, cell-sorted alike): half-warps take 16 particles of each
+    // species from the same place in their bin ranges, so the particles of one cell of
+    // both species form one deposit group. Otherwise one species at a time.
+    constexpr int STRIDE = MIX ? PASS_THREADS / 2 : PASS_THREADS;
+    const int local = MIX ? (int)((threadIdx.x >> 5) * 16 + (threadIdx.x & 15)) : (int)threadIdx.x;
+    for (int s = 0; s < (MIX ? 1 : p.nspecies); ++s) {
+        const int hs = MIX ? (int)((threadIdx.x >> 4) & 1) : s;
+        const SpeciesK<T> sp = p.sp[hs];
         const int beg = sp.bin_start[b], end = sp.bin_start[b + 1];
+        int span = end - beg;
+        if constexpr (MIX)
+            span = max(p.sp[0].bin_start[b + 1] - p.sp[0].bin_start[b],
+                       p.sp[1].bin_start[b + 1] - p.sp[1].bin_start[b]);
         // the next chunk's particle is loaded while the current one is processed
         int c_n = 0;
         T f_n[3] = {0, 0, 0}, u_n[3] = {0, 0, 0};
-        if (beg + (int)threadIdx.x < end) {
-            const int j = beg + threadIdx.x;
+        if (beg + local < end) {
+            const int j = beg + local;
             c_n = sp.cell[j];
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
@@ -797,14 +819,14 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
                 u_n[d] = sp.u[d][j];
             }
         }
-        for (int base = beg; base < end; base += PASS_THREADS) {
-            const int i = base + threadIdx.x;
+        for (int off0 = 0; off0 < span; off0 += STRIDE) {
+            const int i = beg + off0 + local;
             const bool valid = i < end;
             int ix = 0, iy = 0, iz = 0, rx = -1, ry = -1, rz = -1;
             T fx = f_n[0], fy = f_n[1], fz = f_n[2], ux = u_n[0], uy = u_n[1], uz = u_n[2];
             const int c = c_n;
-            if (i + PASS_THREADS < end) {
-                const int j = i + PASS_THREADS;
+            if (i + STRIDE < end) {
+                const int j = i + STRIDE;
                 c_n = sp.cell[j];
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
@@ -1054,8 +1076,14 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
                     if (in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz)) {
                         member = true;
                         key = (rx * TE + ry) * TE + rz;
-                        const T vel[3] = {vx, vy, vz};
-                        stage_record<T, NW>(stg, lane, wx, wy, wz, phase == 0 ? vel : nullptr);
+                        if constexpr (MIX) {   // values carry q w / dV (members of both species)
+                            const T qvel[3] = {sp.qw_dv * vx, sp.qw_dv * vy, sp.qw_dv * vz};
+                            stage_record<T, NW>(stg, lane, wx, wy, wz, phase == 0 ? qvel : nullptr);
+                            if (phase == 1) stg.vrow(0)[lane] = sp.qw_dv;
+                        } else {
+                            const T vel[3] = {vx, vy, vz};
+                            stage_record<T, NW>(stg, lane, wx, wy, wz, phase == 0 ? vel : nullptr);
+                        }
                     } else {
                         if (phase == 1) far++;
                         if (phase == 0)
@@ -1066,9 +1094,9 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
                 }
                 __syncwarp();
                 if (phase == 0)
-                    group_deposit<T, NW, 3, TE>(sD, stg, member, key, lane, sp.qw_dv);
+                    group_deposit<T, NW, 3, TE, MIX>(sD, stg, member, key, lane, MIX ? (T)1 : sp.qw_dv);
                 else
-                    group_deposit<T, NW, 1, TE>(sD, stg, member, key, lane, sp.qw_dv);
+                    group_deposit<T, NW, 1, TE, MIX>(sD, stg, member, key, lane, MIX ? (T)1 : sp.qw_dv);
                 __syncwarp();
             }
             if (valid && MODE == PASS_STEP) {
@@ -1116,22 +1144,22 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
 // One CTA per bin. FP32 linear passes and FP32 grouped quadratic/cubic steps at tile
 // margin 0 fit three CTAs per SM by shared memory and have their registers held to
 // that; row-deposit passes are held to two; the others are left to the compiler.
-template <typename T, int ORDER, int MODE, int MARGIN, int DEP>
+template <typename T, int ORDER, int MODE, int MARGIN, int DEP, bool MIX>
 __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p) {
-    particle_pass_body<T, ORDER, MODE, MARGIN, DEP>(p);
+    particle_pass_body<T, ORDER, MODE, MARGIN, DEP, MIX>(p);
 }
 
-template <typename T, int ORDER, int MODE, int MARGIN, int DEP>
+template <typename T, int ORDER, int MODE, int MARGIN, int DEP, bool MIX>
 __global__ void __launch_bounds__(PASS_THREADS, 3) particle_pass_kernel_3(PassK<T> p) {
-    particle_pass_body<T, ORDER, MODE, MARGIN, DEP>(p);
+    particle_pass_body<T, ORDER, MODE, MARGIN, DEP, MIX>(p);
 }
 
-template <typename T, int ORDER, int MODE, int MARGIN, int DEP>
+template <typename T, int ORDER, int MODE, int MARGIN, int DEP, bool MIX>
 __global__ void __launch_bounds__(PASS_THREADS, 2) particle_pass_kernel_2(PassK<T> p) {
-    particle_pass_body<T, ORDER, MODE, MARGIN, DEP>(p);
+    particle_pass_body<T, ORDER, MODE, MARGIN, DEP, MIX>(p);
 }
 
-template <typename T, int ORDER, int MODE, int MARGIN, int DEP>
+template <typename T, int ORDER, int MODE, int MARGIN, int DEP, bool MIX = false>
 int pass_launch(pic_sim* s, cudaStream_t st) {
     const pic_config& c = s->cfg;
     PassK<T> p;
@@ -1174,11 +1202,11 @@ int pass_launch(pic_sim* s, cudaStream_t st) {
                            MODE == PASS_STEP;
     void (*kern)(PassK<T>);
     if constexpr (sizeof(T) == 4 && (ORDER == 1 || three))
-        kern = particle_pass_kernel_3<T, ORDER, MODE, MARGIN, DEP>;
+        kern = particle_pass_kernel_3<T, ORDER, MODE, MARGIN, DEP, MIX>;
     else if constexpr (DEP == DEP_ROW)
-        kern = particle_pass_kernel_2<T, ORDER, MODE, MARGIN, DEP>;
+        kern = particle_pass_kernel_2<T, ORDER, MODE, MARGIN, DEP, MIX>;
     else
-        kern = particle_pass_kernel<T, ORDER, MODE, MARGIN, DEP>;
+        kern = particle_pass_kernel<T, ORDER, MODE, MARGIN, DEP, MIX>;
     GP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
     if constexpr (three)
         GP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
@@ -1191,6 +1219,11 @@ template <typename T, int ORDER, int MODE, int MARGIN>
 int pass_strategy(pic_sim* s, cudaStream_t st) {
     if constexpr (sizeof(T) == 4) {
         if (s->cfg.deposit == DEP_ROW) return pass_launch<T, ORDER, MODE, MARGIN, DEP_ROW>(s, st);
+        // two species of equal size (the neutral plasmas): one group per cell for both
+        if constexpr (MODE == PASS_STEP) {
+            if (s->nspecies == 2 && s->sp[0].n == s->sp[1].n)
+                return pass_launch<T, ORDER, MODE, MARGIN, DEP_GROUP, true>(s, st);
+        }
     }
     return pass_launch<T, ORDER, MODE, MARGIN, DEP_GROUP>(s, st);
 }

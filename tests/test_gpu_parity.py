@@ -419,3 +419,27 @@ def test_tune_takes_real_steps_and_keeps_results(gp, precision, order):
     err = field_rel_l2(sim, st)
     assert err < tol1, err
     sim.close()
+
+
+@pytest.mark.parametrize("margin", [0, 1])
+def test_fp32_step_two_species_random_positions(gp, margin):
+    """Two species of equal size share deposit groups (half-warps of each species in
+    one group per cell); with random positions the groups are scattered lane sets.
+    One FP32 cubic step from random particles (sorted first) within 1e-5 of the oracle."""
+    wl = gi.drifting_plasma(16, 16, 32, 130.0, galilean=True, shape_order=3, precision=32, jitter=0.0)
+    sim = gp.sim_from_workload(wl, tile_margin=margin)
+    rng = np.random.default_rng(11 + margin)
+    for k, spec in enumerate(wl.species):
+        n = sim.n[k]
+        cell = torch.from_numpy(rng.integers(0, wl.ncells, n).astype(np.int32))
+        off = [torch.from_numpy(rng.uniform(0, 1, n)).to(torch.float32) for _ in range(3)]
+        u = [torch.from_numpy(spec.u0[d] + rng.normal(size=n) * 0.5).to(torch.float32) for d in range(3)]
+        sim.set_particles(k, cell, off, u)
+    sim.sort()
+    cfg, st = oracle_state_from_sim(sim, wl)
+    sim.step(1)
+    pic.step(cfg, st)
+    torch.cuda.synchronize()
+    err = field_rel_l2(sim, st)
+    assert err < 1e-5, err
+    sim.close()
