@@ -421,12 +421,13 @@ def test_tune_takes_real_steps_and_keeps_results(gp, precision, order):
     sim.close()
 
 
+@pytest.mark.parametrize("order", [1, 3])
 @pytest.mark.parametrize("margin", [0, 1])
-def test_fp32_step_two_species_random_positions(gp, margin):
+def test_fp32_step_two_species_random_positions(gp, margin, order):
     """Two species of equal size share deposit groups (half-warps of each species in
     one group per cell); with random positions the groups are scattered lane sets.
-    One FP32 cubic step from random particles (sorted first) within 1e-5 of the oracle."""
-    wl = gi.drifting_plasma(16, 16, 32, 130.0, galilean=True, shape_order=3, precision=32, jitter=0.0)
+    One FP32 step from random particles (sorted first) within 1e-5 of the oracle."""
+    wl = gi.drifting_plasma(16, 16, 32, 130.0, galilean=True, shape_order=order, precision=32, jitter=0.0)
     sim = gp.sim_from_workload(wl, tile_margin=margin)
     rng = np.random.default_rng(11 + margin)
     for k, spec in enumerate(wl.species):
