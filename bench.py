@@ -147,9 +147,10 @@ def fp32_peak_tflops():
 # DRAM bytes per particle and per cell of one particle-pass launch, keyed by (shape
 # order, precision, tile margin, deposit strategy), from the ncu capture summarised in
 # profiles/particle_pass_cubic_fp32_64x64x128.md (dram__bytes_read.sum +
-# dram__bytes_write.sum = 446.1 MB for 8,388,608 particles at 16 per cell); scaled to a
-# launch by the particles it processes (the same 16 particles per cell).
-PASS_TRAFFIC = {(3, 32, 0, 0): (53.2, 0.0)}
+# dram__bytes_write.sum = 449.5 MB for 8,388,608 particles at 16 per cell, two species
+# sharing deposit groups); scaled to a launch by the particles it processes (the same
+# 16 particles per cell).
+PASS_TRAFFIC = {(3, 32, 0, 0): (53.6, 0.0)}
 
 
 def kspace_bytes(wl, precision):
@@ -286,7 +287,9 @@ def run_ours(args, rank, world, local_rank):
     achieved = particle_bytes(wl, 32) / (part_ms * 1e-3) / 1e9
     ks_achieved = kspace_bytes(wl, 32) / (ks_ms * 1e-3) / 1e9
     value = replica_throughput(P, args.steps, world, ms_max)
-    kname = f"particle_pass_kernel<float,{args.order},STEP,{tuned['tile_margin']},{tuned['deposit']}>"
+    mixed = len(wl.species) == 2 and args.order > 1 and tuned["deposit"] == 0
+    kname = (f"particle_pass_kernel<float,{args.order},STEP,{tuned['tile_margin']},{tuned['deposit']}"
+             f"{',mixed' if mixed else ''}>")
     tr = PASS_TRAFFIC.get((args.order, 32, tuned["tile_margin"], tuned["deposit"]))
     traffic = None if tr is None else tr[0] * P + tr[1] * N
     roof_hbm = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
