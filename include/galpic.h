@@ -92,9 +92,11 @@ typedef struct {
                                    re-sort threshold; 1: particles up to one cell out
                                    still use the tile)                                 */
     int32_t deposit;            /* deposit strategy of FP32 quadratic/cubic passes:
-                                   0: grouped by cell (fastest with many particles per
-                                   cell), 1: by stencil row (fastest with few); other
-                                   passes always group by cell. pic_tune picks one.   */
+                                   0: grouped by cell, J and rho in separate group
+                                   passes (many particles per cell), 1: by stencil row
+                                   (few particles per cell), 2: grouped by cell, J and
+                                   rho in one group pass; other passes always group by
+                                   cell (linear: J and rho together). pic_tune picks. */
 } pic_config;
 
 /* One particle species. Particles are either generated on the device on a
@@ -202,7 +204,7 @@ int pic_set(pic_sim* sim, int which, const void* src, size_t bytes, void* stream
  * run's own particles and fields, keeps the fastest for all later steps (the step
  * graph is re-captured) and writes it to chosen[0] (margin) and chosen[1]
  * (strategy); chosen may be NULL. Each candidate takes three real, complete steps
- * (one to settle, two timed), so the run advances by 6 or 12 steps, exactly as
+ * (one to settle, two timed), so the run advances by 6 or 18 steps, exactly as
  * pic_step would advance it. Synchronises `stream`. Errors: PIC_EINVAL, PIC_ECUDA,
  * PIC_ECUFFT (the run keeps its previous choice). */
 int pic_tune(pic_sim* sim, int32_t chosen[2], void* stream);

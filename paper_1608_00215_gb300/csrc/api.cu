@@ -56,7 +56,7 @@ int validate(const pic_config* c, const pic_species* sp, int ns) {
     if (c->init_fields == 1 && !(b2 < 1.0)) return fail(PIC_EINVAL, "|beta_init| must be below 1");
     if (c->init_fields != 0 && c->init_fields != 1) return fail(PIC_EINVAL, "init_fields must be 0 or 1");
     if (c->tile_margin != 0 && c->tile_margin != 1) return fail(PIC_EINVAL, "tile_margin must be 0 or 1");
-    if (c->deposit != 0 && c->deposit != 1) return fail(PIC_EINVAL, "deposit must be 0 or 1");
+    if (c->deposit < 0 || c->deposit > 2) return fail(PIC_EINVAL, "deposit must be 0, 1 or 2");
     if (ns < 0 || ns > PIC_MAX_SPECIES) return fail(PIC_EINVAL, "nspecies out of range");
     if (ns > 0 && !sp) return fail(PIC_EINVAL, "species array is NULL");
     int64_t ncell = (int64_t)c->nx * c->ny * c->nz;
@@ -635,7 +635,7 @@ int pic_tune(pic_sim* s, int32_t chosen[2], void* stream) {
     } a, b;
     GP_CUDA(cudaEventCreate(&a.e));
     GP_CUDA(cudaEventCreate(&b.e));
-    const int nstrat = (s->cfg.precision == 32 && s->cfg.shape_order >= 2) ? 2 : 1;
+    const int nstrat = (s->cfg.precision == 32 && s->cfg.shape_order >= 2) ? 3 : 1;
     const int keep_m = s->d.margin, keep_d = s->cfg.deposit;
     int best_m = keep_m, best_d = keep_d;
     float tbest = 0.f;

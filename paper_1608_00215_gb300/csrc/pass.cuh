@@ -193,8 +193,6 @@ __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) / 16 * 
 // the combined J and rho deposit.
 template <typename T, int NW> struct Stage {
     static constexpr int RS = 34;
-    static constexpr int ROWS = NW == 2 ? 4 + 6 * NW : 3 + 3 * NW;
-    static constexpr size_t BYTES = align16((size_t)ROWS * RS * sizeof(T));   // per warp
     T* base;
     __device__ T* row(int r) const { return base + r * RS; }
     __device__ T* vrow(int q) const { return row(q); }
@@ -221,14 +219,19 @@ struct RowStage {
     static constexpr size_t BYTES = 32 * MEMBER * sizeof(float);
 };
 
-// Deposit strategies: grouped by cell (all passes) or by stencil row (FP32, NW = 4).
-enum { DEP_GROUP = 0, DEP_ROW = 1 };
+// Deposit strategies: grouped by cell, J and rho in separate group passes (all
+// passes; linear passes always combine them), by stencil row (FP32, NW = 4), or grouped
+// by cell with J and rho in one group pass (FP32, NW = 4).
+enum { DEP_GROUP = 0, DEP_ROW = 1, DEP_JR = 2 };
+
+// Rows of the grouped staging area: velocity, x, y, z weights; the combined J and rho
+// pass adds a flag row and the x^{n+1} weights.
+__host__ __device__ constexpr int stage_rows(int NW, bool jr) { return jr ? 4 + 6 * NW : 3 + 3 * NW; }
 
 __host__ __device__ constexpr size_t stage_bytes(int NW, size_t T, int dep) {
     return (T == 4 && NW == 4 && dep == DEP_ROW)
                ? RowStage::BYTES
-               : T == 4 ? (NW == 4 ? Stage<float, 4>::BYTES : Stage<float, 2>::BYTES)
-                        : (NW == 4 ? Stage<double, 4>::BYTES : Stage<double, 2>::BYTES);
+               : align16((size_t)stage_rows(NW, NW == 2 || dep == DEP_JR) * 34 * T);
 }
 
 // Shared-memory layout of one particle-pass CTA (bytes), shared with the host.
@@ -577,6 +580,97 @@ __device__ void group_deposit_jr(T* sD, const Stage<T, 2>& stg, bool member, int
     }
 }
 
+// Combined J and rho deposit of one warp for 4x4x4 stencils (strategy DEP_JR). Members
+// are grouped by the start `key` of their J stencil; lane (b, c, h) = ((lane & 15) >> 2,
+// lane & 3, lane >> 4) sums the y-z node (b, c) at x nodes h and h + 2 for Jx, Jy, Jz
+// (x^{n+1/2} weights, velocity rows) and rho (x^{n+1} weights, flag row: the member's
+// value when its rho stencil starts at its J stencil's node, 0 otherwise; those members'
+// rho goes through a rho-only pass). One group loop and one batch of eight
+// compare-and-swaps serve both. PREMUL as for group_deposit.
+// Every lane of the warp must call this (warp-collective).
+template <typename T, int TE>
+__device__ void group_deposit_jr4(T* sD, const Stage<T, 4>& stg, bool member, int key, int lane, T qw) {
+    typedef typename Pair<T>::type P2;
+    constexpr int R = TE * TE * TE;
+    const P2 zero = Pair<T>::make((T)0, (T)0);
+    const int bc = lane & 15, h = lane >> 4, b = bc >> 2, c = bc & 3;
+    const T* xh = stg.xrow(h);
+    const T* xh2 = stg.xrow(h + 2);
+    const T* yb = stg.yrow(b);
+    const T* zc = stg.zrow(c);
+    const T* xRh = stg.xRrow(h);
+    const T* xRh2 = stg.xRrow(h + 2);
+    const T* yRb = stg.yRrow(b);
+    const T* zRc = stg.zRrow(c);
+    const T* fr = stg.frow();
+    unsigned pending = __ballot_sync(0xffffffffu, member);
+    while (pending) {
+        const int leader = __ffs(pending) - 1;
+        const int gkey = __shfl_sync(0xffffffffu, key, leader);
+        const unsigned grp = __ballot_sync(0xffffffffu, member && key == gkey);
+        pending &= ~grp;
+        P2 A[3], A2[3], Rr = zero, Rr2 = zero;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) A[q] = A2[q] = zero;
+        auto single = [&](int m) {
+            const T wyz = yb[m] * zc[m];
+            const T w0 = xh[m] * wyz, w1 = xh2[m] * wyz;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const T v = stg.vrow(q)[m];
+                A[q].x = fma(w0, v, A[q].x);
+                A2[q].x = fma(w1, v, A2[q].x);
+            }
+            const T rz = yRb[m] * zRc[m] * fr[m];
+            Rr.x = fma(xRh[m], rz, Rr.x);
+            Rr2.x = fma(xRh2[m], rz, Rr2.x);
+        };
+        auto pair = [&](int m) {
+            const P2 wyz = pmul(ld2(yb + m), ld2(zc + m));
+            const P2 w0 = pmul(ld2(xh + m), wyz);
+            const P2 w1 = pmul(ld2(xh2 + m), wyz);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const P2 v = ld2(stg.vrow(q) + m);
+                A[q] = pfma(w0, v, A[q]);
+                A2[q] = pfma(w1, v, A2[q]);
+            }
+            const P2 rz = pmul(pmul(ld2(yRb + m), ld2(zRc + m)), ld2(fr + m));
+            Rr = pfma(ld2(xRh + m), rz, Rr);
+            Rr2 = pfma(ld2(xRh2 + m), rz, Rr2);
+        };
+        // runs of consecutive lanes (one per cell and species), pairs within each
+        unsigned g = grp;
+        while (g) {
+            const int r0 = __ffs(g) - 1;
+            const unsigned inv = ~(g >> r0);
+            const int rl = inv ? __ffs(inv) - 1 : 32 - r0;
+            int m = r0;
+            const int me = r0 + rl;
+            if (m & 1) single(m++);
+            for (; m + 1 < me; m += 2) pair(m);
+            if (m < me) single(m);
+            g &= rl == 32 ? 0u : ~(((1u << rl) - 1u) << r0);
+        }
+        const int n0 = gkey + (h * TE + b) * TE + c;
+        const int n1 = n0 + 2 * TE * TE;
+        T* addr[8];
+        T val[8];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            addr[2 * q] = &sD[q * R + n0];
+            addr[2 * q + 1] = &sD[q * R + n1];
+            val[2 * q] = (A[q].x + A[q].y) * qw;
+            val[2 * q + 1] = (A2[q].x + A2[q].y) * qw;
+        }
+        addr[6] = &sD[3 * R + n0];
+        addr[7] = &sD[3 * R + n1];
+        val[6] = (Rr.x + Rr.y) * qw;
+        val[7] = (Rr2.x + Rr2.y) * qw;
+        smem_add_batch<T, 8>(addr, val);
+    }
+}
+
 // Stage this lane's weights (and, for J, its velocity) in its column of the rows.
 template <typename T, int NW>
 __device__ __forceinline__ void stage_record(const Stage<T, NW>& stg, int lane, const T* wx, const T* wy,
@@ -759,7 +853,9 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const PassSmem L(R, NW, sizeof(T), MODE == PASS_STEP, DEP);
     static_assert(DEP == DEP_GROUP || (sizeof(T) == 4 && NW == 4), "row deposit: FP32, NW = 4 only");
-    static_assert(!MIX || (NW == 4 && DEP == DEP_GROUP), "mixed-species groups: NW = 4, grouped deposit");
+    static_assert(!MIX || (NW == 4 && (DEP == DEP_GROUP || DEP == DEP_JR)),
+                  "mixed-species groups: NW = 4, grouped deposits");
+    static_assert(DEP != DEP_JR || (sizeof(T) == 4 && NW == 4), "combined J and rho groups: FP32, NW = 4 only");
     FieldTile<T> tile;
     tile.init(smem_raw + L.tile, R);
     T* sD = reinterpret_cast<T*>(smem_raw + L.dep);
@@ -925,11 +1021,12 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
             }
             // ---- deposit J (phase 0: at x^{n+1/2} with v^{n+1/2}) and rho (phase 1:
             // at x^{n+1}); DEPOSIT mode: both at the current x
-            if constexpr (NW == 2) {
-                // linear: both stencils first, then one combined pass (see group_deposit_jr)
+            if constexpr (NW == 2 || DEP == DEP_JR) {
+                // both stencils first, then one combined J and rho group pass
+                // (group_deposit_jr / group_deposit_jr4)
                 bool mJ = false, mR = false, same = false;
                 int keyJ = 0, keyR = 0;
-                T wxR[2], wyR[2], wzR[2];
+                T wxR[NW], wyR[NW], wzR[NW];
                 if (valid) {
                     if (MODE == PASS_STEP) {
                         rx += drift_axis(ix, fx, (vx - p.vgal[0]) * p.hd[0], p.nx);
@@ -971,9 +1068,11 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
                     }
                     same = mJ && mR && keyR == keyJ;
                     if (mJ) {
-                        const T vel[3] = {vx, vy, vz};
+                        // MIX: values carry q w / dV (members of both species)
+                        const T qs = MIX ? sp.qw_dv : (T)1;
+                        const T vel[3] = {qs * vx, qs * vy, qs * vz};
                         stage_record<T, NW>(stg, lane, wx, wy, wz, vel);
-                        stg.frow()[lane] = same ? (T)1 : (T)0;
+                        stg.frow()[lane] = same ? qs : (T)0;
 #pragma unroll
                         for (int a = 0; a < NW; ++a) {
                             stg.xRrow(a)[lane] = wxR[a];
@@ -983,14 +1082,20 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
                     }
                 }
                 __syncwarp();
-                group_deposit_jr<T, TE>(sD, stg, mJ, keyJ, lane, sp.qw_dv);
+                if constexpr (NW == 2)
+                    group_deposit_jr<T, TE>(sD, stg, mJ, keyJ, lane, MIX ? (T)1 : sp.qw_dv);
+                else
+                    group_deposit_jr4<T, TE>(sD, stg, mJ, keyJ, lane, MIX ? (T)1 : sp.qw_dv);
                 __syncwarp();
                 // rho of members whose rho stencil starts elsewhere
                 const bool restR = mR && !same;
                 if (__any_sync(0xffffffffu, restR)) {
-                    if (restR) stage_record<T, NW>(stg, lane, wxR, wyR, wzR, nullptr);
+                    if (restR) {
+                        stage_record<T, NW>(stg, lane, wxR, wyR, wzR, nullptr);
+                        if constexpr (MIX) stg.vrow(0)[lane] = sp.qw_dv;
+                    }
                     __syncwarp();
-                    group_deposit<T, NW, 1, TE>(sD, stg, restR, keyR, lane, sp.qw_dv);
+                    group_deposit<T, NW, 1, TE, MIX>(sD, stg, restR, keyR, lane, MIX ? (T)1 : sp.qw_dv);
                     __syncwarp();
                 }
             } else if constexpr (DEP == DEP_ROW) {
@@ -1203,7 +1308,7 @@ int pass_launch(pic_sim* s, cudaStream_t st) {
     void (*kern)(PassK<T>);
     if constexpr (sizeof(T) == 4 && (ORDER == 1 || three))
         kern = particle_pass_kernel_3<T, ORDER, MODE, MARGIN, DEP, MIX>;
-    else if constexpr (DEP == DEP_ROW)
+    else if constexpr (DEP == DEP_ROW || DEP == DEP_JR)
         kern = particle_pass_kernel_2<T, ORDER, MODE, MARGIN, DEP, MIX>;
     else
         kern = particle_pass_kernel<T, ORDER, MODE, MARGIN, DEP, MIX>;
@@ -1220,9 +1325,15 @@ int pass_strategy(pic_sim* s, cudaStream_t st) {
     if constexpr (sizeof(T) == 4) {
         if (s->cfg.deposit == DEP_ROW) return pass_launch<T, ORDER, MODE, MARGIN, DEP_ROW>(s, st);
         // two species of equal size (the neutral plasmas): one group per cell for both
+        const bool mix = MODE == PASS_STEP && s->nspecies == 2 && s->sp[0].n == s->sp[1].n;
+        if (s->cfg.deposit == DEP_JR) {
+            if constexpr (MODE == PASS_STEP) {
+                if (mix) return pass_launch<T, ORDER, MODE, MARGIN, DEP_JR, true>(s, st);
+                return pass_launch<T, ORDER, MODE, MARGIN, DEP_JR>(s, st);
+            }
+        }
         if constexpr (MODE == PASS_STEP) {
-            if (s->nspecies == 2 && s->sp[0].n == s->sp[1].n)
-                return pass_launch<T, ORDER, MODE, MARGIN, DEP_GROUP, true>(s, st);
+            if (mix) return pass_launch<T, ORDER, MODE, MARGIN, DEP_GROUP, true>(s, st);
         }
     }
     return pass_launch<T, ORDER, MODE, MARGIN, DEP_GROUP>(s, st);

@@ -224,8 +224,9 @@ class Sim:
 
     def tune(self) -> Dict[str, int]:
         """Time the particle pass for each tile margin and deposit strategy (0: grouped
-        by cell, 1: by stencil row) on this run and keep the fastest. Takes real steps:
-        the run advances by 6 or 12 steps. Returns {"tile_margin": m, "deposit": d}."""
+        by cell, 1: by stencil row, 2: grouped with J and rho together) on this run and
+        keep the fastest. Takes real steps:
+        the run advances by 6 or 18 steps. Returns {"tile_margin": m, "deposit": d}."""
         out = (c_int32 * 2)()
         check(lib.pic_tune(self.handle, out, _stream_ptr(self.stream)))
         return {"tile_margin": int(out[0]), "deposit": int(out[1])}

@@ -339,7 +339,7 @@ def test_fp32_parity(gp, fixture, galilean):
     sim.close()
 
 
-@pytest.mark.parametrize("strategy", [0, 1])
+@pytest.mark.parametrize("strategy", [0, 1, 2])
 @pytest.mark.parametrize("margin", [0, 1])
 @pytest.mark.parametrize("galilean", [True, False])
 @pytest.mark.parametrize("order", [2, 3])
@@ -401,9 +401,9 @@ def test_tune_takes_real_steps_and_keeps_results(gp, precision, order):
     sim.sort()
     cfg, st = oracle_state_from_sim(sim, wl)
     chosen = sim.tune()
-    assert chosen["tile_margin"] in (0, 1) and chosen["deposit"] in (0, 1)
-    ncand = 4 if (precision == 32 and order >= 2) else 2
-    assert chosen["deposit"] == 0 or ncand == 4
+    assert chosen["tile_margin"] in (0, 1) and chosen["deposit"] in (0, 1, 2)
+    ncand = 6 if (precision == 32 and order >= 2) else 2
+    assert chosen["deposit"] == 0 or ncand == 6
     for _ in range(3 * ncand):
         pic.step(cfg, st)
     torch.cuda.synchronize()
@@ -421,14 +421,14 @@ def test_tune_takes_real_steps_and_keeps_results(gp, precision, order):
     sim.close()
 
 
-@pytest.mark.parametrize("order", [1, 3])
+@pytest.mark.parametrize("order,strategy", [(1, 0), (3, 0), (3, 2)])
 @pytest.mark.parametrize("margin", [0, 1])
-def test_fp32_step_two_species_random_positions(gp, margin, order):
+def test_fp32_step_two_species_random_positions(gp, margin, order, strategy):
     """Two species of equal size share deposit groups (half-warps of each species in
     one group per cell); with random positions the groups are scattered lane sets.
     One FP32 step from random particles (sorted first) within 1e-5 of the oracle."""
     wl = gi.drifting_plasma(16, 16, 32, 130.0, galilean=True, shape_order=order, precision=32, jitter=0.0)
-    sim = gp.sim_from_workload(wl, tile_margin=margin)
+    sim = gp.sim_from_workload(wl, tile_margin=margin, deposit=strategy)
     rng = np.random.default_rng(11 + margin)
     for k, spec in enumerate(wl.species):
         n = sim.n[k]
