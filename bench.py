@@ -432,18 +432,36 @@ def long_run(args):
         o64.close()
         del o32, o64
         torch.cuda.empty_cache()
-    wl = gi.drifting_plasma(*grid, GAMMA, galilean=True, shape_order=1, precision=64, seed=1)
+    wl = gi.drifting_plasma(*grid, GAMMA, galilean=True, shape_order=args.long_run_order, precision=64,
+                            seed=1)
     s32 = gp.sim_from_workload(wl, precision=32)
     s64 = gp.sim_from_workload(wl, precision=64)
+    t1 = time.perf_counter()
+    s32.step(1)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    s64.step(1)
+    torch.cuda.synchronize()
+    out["first_step_s"] = {"fp32": t2 - t1, "fp64": time.perf_counter() - t2}
     out["particles"] = wl.nparticles
+    out["shape_order"] = args.long_run_order
     out["curve"] = []
     W0_32, W0_64 = s32.energy(), s64.energy()
+    done = 1
     t0 = time.perf_counter()
-    done = 0
+    seg_s = {"fp32": 0.0, "fp64": 0.0, "steps": 0}
     while done < args.steps:
         n = min(args.long_run_every, args.steps - done)
+        torch.cuda.synchronize()
+        ta = time.perf_counter()
         s32.step(n - 1)
+        torch.cuda.synchronize()
+        tb = time.perf_counter()
         s64.step(n - 1)
+        torch.cuda.synchronize()
+        seg_s["fp32"] += tb - ta
+        seg_s["fp64"] += time.perf_counter() - tb
+        seg_s["steps"] += n - 1
         rho32 = s32.get(gp.BUF_RHO_HAT, device="cpu").to(torch.complex128).numpy()
         s32.step(1)
         s64.step(1)
@@ -455,6 +473,9 @@ def long_run(args):
                              "relL2_E_B_fp32_vs_fp64": rel(E32, B32, E64, B64),
                              "continuity_residual_fp32": continuity_residual(gp, s32, rho32, wl)})
     out["seconds"] = time.perf_counter() - t0
+    if seg_s["steps"]:
+        out["ms_per_step"] = {"fp32": 1e3 * seg_s["fp32"] / seg_s["steps"],
+                              "fp64": 1e3 * seg_s["fp64"] / seg_s["steps"]}
     out["status"] = [s32.status(), s64.status()]
     print(json.dumps(out), flush=True)
 
@@ -593,6 +614,8 @@ def main():
     ap.add_argument("--long-run-oracle", type=int, default=0,
                     help="also compare both precisions with the FP64 oracle for this many steps")
     ap.add_argument("--long-run-oracle-grid", default="32,32,64", help="grid of the oracle comparison")
+    ap.add_argument("--long-run-order", type=int, default=1,
+                    help="shape order of the long run (1: the config-1 plasma; 3: the bench plasma)")
     ap.add_argument("--lwfa", action="store_true",
                     help="boosted-frame laser-wakefield run (on-axis Ez, field energy) instead")
     ap.add_argument("--lwfa-grid", default="384,384,1536")
