@@ -1248,7 +1248,8 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
 
 // One CTA per bin. FP32 linear passes and FP32 grouped quadratic/cubic steps at tile
 // margin 0 fit three CTAs per SM by shared memory and have their registers held to
-// that; row-deposit passes are held to two; the others are left to the compiler.
+// that; row-deposit and combined J and rho passes are held to two; the others are left
+// to the compiler.
 template <typename T, int ORDER, int MODE, int MARGIN, int DEP, bool MIX>
 __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p) {
     particle_pass_body<T, ORDER, MODE, MARGIN, DEP, MIX>(p);
