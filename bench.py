@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -480,6 +481,38 @@ def long_run(args):
     print(json.dumps(out), flush=True)
 
 
+def lab_snapshots(wl, lines, step0):
+    """Back-transform the recorded on-axis Ez lines (boosted steps step0 + 1, ...) to
+    lab-frame snapshots at three lab times whose slices cross the laser pulse."""
+    import numpy as np
+    from paper_1608_00215_gb300.lab_frame import LabFrameAxis
+    L = wl.laser
+    # the grid moves with the plasma, which streams at -beta c in the boosted frame
+    beta = abs(wl.vgal[2]) / wl.c
+    gamma = 1.0 / math.sqrt(1.0 - beta * beta)
+    steps = lines.shape[0]
+    t_mid = [(step0 + f * steps) * wl.dt for f in (0.25, 0.5, 0.75)]
+    # the slice of lab time T passes, at boosted time tp, through the laser's image in the
+    # periodic box: Galilean coordinate (z0 + (c - v_gal) tp) mod box, i.e. z' = that + v_gal tp
+    box = wl.nz * wl.dz
+    zc = [math.fmod(L.z0 * wl.dz + (wl.c - wl.vgal[2]) * tp, box) + wl.vgal[2] * tp for tp in t_mid]
+    t_lab = [gamma * (tp + beta * z / wl.c) for tp, z in zip(t_mid, zc)]
+    ax = LabFrameAxis(gamma, wl.dz, wl.dt, wl.nz, t_lab, c=wl.c, v_gal=wl.vgal[2])
+    for n in range(steps):
+        ax.add(step0 + n + 1, lines[n])
+    out = {"gamma_boost": gamma, "lab_sample_spacing": ax.sample_spacing(), "snapshots": []}
+    for k, T in enumerate(t_lab):
+        Z, E = ax.snapshot(k)
+        if Z.size == 0:
+            out["snapshots"].append({"t_lab": T, "points": 0})
+            continue
+        i = int(np.abs(E).argmax())
+        out["snapshots"].append({"t_lab": T, "points": int(Z.size), "z_lab_range": [float(Z[0]), float(Z[-1])],
+                                 "Ez_max": float(np.abs(E).max()), "z_lab_at_max": float(Z[i]),
+                                 "Ez_rms": float(np.sqrt(np.mean(E * E)))})
+    return out
+
+
 def lwfa_run(args):
     """Boosted-frame laser-wakefield run (384x384x1536, gamma_boost = 10, a0 = 2 laser,
     FP32, cubic): on-axis Ez and the field energy every `--lwfa-every` steps and the
@@ -507,17 +540,25 @@ def lwfa_run(args):
         done = 0
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
+        # lab-frame snapshots (Galilean run, --lwfa-lab): the on-axis Ez of every step is
+        # copied on the device into a buffer and back-transformed on the host at the end
+        lab_lines = None
+        if args.lwfa_lab and gal:
+            lab_lines = torch.empty((args.steps, wl.nz), dtype=torch.float32, device="cuda")
         while done < args.steps:
             n = min(args.lwfa_every, args.steps - done)
             a.record(sim.stream)
-            sim.step(n)
+            if lab_lines is None:
+                sim.step(n)
+            else:
+                for k in range(n):
+                    sim.step(1)
+                    sim.get_line(2, xc, yc, out=lab_lines[done + k])
             b.record(sim.stream)
             b.synchronize()
             ms += a.elapsed_time(b)
             done += n
-            E = sim.get(gp.BUF_E)
-            ez = E[2, xc, yc].double().cpu().numpy()
-            del E
+            ez = sim.get_line(2, xc, yc).double().cpu().numpy()
             W = sim.energy()
             c = sim.counters()
             curve.append({"step": done, "W_over_W0": W / W0, "Ez_axis_max": float(np.abs(ez).max()),
@@ -531,11 +572,15 @@ def lwfa_run(args):
             sim.field_update()
         stages = {k: v["ms"] / v["count"] for k, v in sim.profile_read().items() if v["count"]}
         sim.profile(False)
+        lab = None
+        if lab_lines is not None:
+            lab = lab_snapshots(wl, lab_lines.double().cpu().numpy(), tuned_steps)
         cnt = sim.counters()
         out["runs"]["galilean" if gal else "standard"] = {
             "particles": wl.nparticles, "init_s": init_s, "ms_per_step": ms / args.steps,
             "pushes_per_s": wl.nparticles * args.steps / (ms * 1e-3), "W0": W0, "curve": curve,
             "stages_ms": stages, "tuned": strategy, "steps_taken_by_tuning": tuned_steps,
+            "lab_frame": lab,
             "sorts": cnt.get("sorts") if isinstance(cnt, dict) else None, "status": sim.status()}
         sim.close()
         del sim
@@ -621,6 +666,8 @@ def main():
     ap.add_argument("--lwfa-grid", default="384,384,1536")
     ap.add_argument("--lwfa-every", type=int, default=100)
     ap.add_argument("--lwfa-std", action="store_true", help="also run the v_gal = 0 twin")
+    ap.add_argument("--lwfa-lab", action="store_true",
+                    help="record on-axis Ez every step and back-transform it to lab-frame snapshots")
     ap.add_argument("--tune", action="store_true",
                     help="let the autotuner pick the deposit strategy (pic_tune) before timing")
     args = ap.parse_args()

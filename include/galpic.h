@@ -195,6 +195,13 @@ int pic_diag_energy(pic_sim* sim, double* out_dev, void* stream);
 /* Copy a buffer out to dst (host or device, `bytes` must equal its size). */
 int pic_get(pic_sim* sim, int which, void* dst, size_t bytes, void* stream);
 
+/* Copy the line of real field component `component` (0..5 = Ex, Ey, Ez, Bx, By, Bz) at
+ * grid column (ix, iy), all nz nodes along z, to dst (host or device, nz reals of the
+ * run's precision), e.g. the on-axis Ez that the boosted-frame wakefield runs record
+ * every step. Asynchronous on `stream`. Errors: PIC_EINVAL (NULL pointers, component
+ * or column out of range), PIC_ECUDA. */
+int pic_get_line(pic_sim* sim, int component, int ix, int iy, void* dst, void* stream);
+
 /* Overwrite the spectral E^n, B^n or rho^n (PIC_BUF_E_HAT, _B_HAT, _RHO_HAT)
  * from src (host or device). Setting E_HAT or B_HAT recomputes the real E, B. */
 int pic_set(pic_sim* sim, int which, const void* src, size_t bytes, void* stream);

@@ -607,6 +607,16 @@ int pic_get(pic_sim* s, int which, void* dst, size_t bytes, void* stream) {
     return PIC_OK;
 }
 
+int pic_get_line(pic_sim* s, int component, int ix, int iy, void* dst, void* stream) {
+    if (!s || !dst) return fail(PIC_EINVAL, "sim or dst is NULL");
+    if (component < 0 || component > 5) return fail(PIC_EINVAL, "component must be 0..5 (Ex..Bz)");
+    if (ix < 0 || ix >= s->d.nx || iy < 0 || iy >= s->d.ny) return fail(PIC_EINVAL, "line outside the grid");
+    const size_t T = real_bytes(s);
+    const char* src = (const char*)s->F + ((size_t)component * s->d.N + ((size_t)ix * s->d.ny + iy) * s->d.nz) * T;
+    GP_CUDA(cudaMemcpyAsync(dst, src, (size_t)s->d.nz * T, cudaMemcpyDefault, (cudaStream_t)stream));
+    return PIC_OK;
+}
+
 int pic_set(pic_sim* s, int which, const void* src, size_t bytes, void* stream) {
     if (!s || !src) return fail(PIC_EINVAL, "sim or src is NULL");
     if (which != PIC_BUF_E_HAT && which != PIC_BUF_B_HAT && which != PIC_BUF_RHO_HAT)

@@ -71,6 +71,7 @@ def _load():
         "pic_add_fields": (c_int, [P, P, P]),
         "pic_sort_policy": (c_int, [P, c_int64, c_int64, P]),
         "pic_tune": (c_int, [P, P, P]),
+        "pic_get_line": (c_int, [P, c_int, c_int, c_int, P, P]),
         "pic_get_particles": (c_int, [P, c_int, P, POINTER(P), POINTER(P), P]),
         "pic_set_particles": (c_int, [P, c_int, P, POINTER(P), POINTER(P), P]),
         "pic_sort": (c_int, [P, P]),
@@ -95,7 +96,7 @@ EXPORTS = ("pic_version", "pic_last_error", "pic_footprint", "pic_init", "pic_de
            "pic_gather_push", "pic_field_update", "pic_step", "pic_step_many", "pic_diag_energy",
            "pic_get", "pic_set", "pic_get_particles", "pic_set_particles", "pic_status",
            "pic_counters", "pic_sizes", "pic_profile", "pic_profile_read", "pic_sort",
-           "pic_field_energy_noalloc", "pic_add_fields", "pic_sort_policy", "pic_tune")
+           "pic_field_energy_noalloc", "pic_add_fields", "pic_sort_policy", "pic_tune", "pic_get_line")
 
 STAGES = ("sort", "particles", "fft_r2c", "kspace", "fft_c2r", "energy")
 
@@ -214,6 +215,13 @@ class Sim:
         out = torch.empty(shape, dtype=dt, device=device or self.device)
         check(lib.pic_get(self.handle, which, c_void_p(out.data_ptr()),
                           out.numel() * out.element_size(), _stream_ptr(self.stream)))
+        return out
+
+    def get_line(self, component: int, ix: int, iy: int, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """The z-line of real field component (0..5 = Ex..Bz) at column (ix, iy)."""
+        if out is None:
+            out = torch.empty(self.cfg.nz, dtype=self.real, device=self.device)
+        check(lib.pic_get_line(self.handle, component, ix, iy, c_void_p(out.data_ptr()), _stream_ptr(self.stream)))
         return out
 
     def set(self, which: int, src: torch.Tensor):

@@ -105,3 +105,26 @@ def test_lwfa_fp32_step_parity(gp, margin):
     e5 = field_rel_l2(sim, st)
     assert e5 < 1e-4, e5
     sim.close()
+
+
+def test_get_line_matches_full_copy(gp):
+    """pic_get_line copies exactly the z-line of a field component (host and device
+    destinations), and rejects columns outside the grid."""
+    wl = _small_lwfa(32)
+    sim = gp.sim_from_workload(wl)
+    sim.step(2)
+    E = sim.get(gp.BUF_E, device="cpu")
+    B = sim.get(gp.BUF_B, device="cpu")
+    torch.cuda.synchronize()
+    for comp, ix, iy in ((2, 16, 16), (0, 3, 30), (4, 31, 0)):
+        dev = sim.get_line(comp, ix, iy)
+        host = torch.empty(wl.nz, dtype=torch.float32).pin_memory()
+        sim.get_line(comp, ix, iy, out=host)
+        torch.cuda.synchronize()
+        want = (E if comp < 3 else B)[comp % 3, ix, iy]
+        assert torch.equal(dev.cpu(), want) and torch.equal(host, want)
+    with pytest.raises(gp.GalpicError):
+        sim.get_line(2, wl.nx, 0)
+    with pytest.raises(gp.GalpicError):
+        sim.get_line(6, 0, 0)
+    sim.close()
