@@ -481,6 +481,19 @@ def long_run(args):
     print(json.dumps(out), flush=True)
 
 
+def bunch_energy(sim, wl):
+    """Lab-frame kinetic energy (MeV) of the witness bunch: mean and rms spread, from the
+    boosted-frame momenta by the inverse boost gamma_lab = gamma_b (gamma' + beta_b u'_z / c)."""
+    import numpy as np
+    p = sim.get_particles(sim.nspecies - 1, device="cpu")
+    u = np.stack([t.double().numpy() for t in p["u"]]) / wl.c
+    gp_ = np.sqrt(1.0 + (u * u).sum(0))
+    gamma_b = wl.bunch.gamma_boost
+    beta_b = math.sqrt(1.0 - 1.0 / (gamma_b * gamma_b))
+    e = (gamma_b * (gp_ + beta_b * u[2]) - 1.0) * 0.51099895
+    return {"bunch_E_lab_MeV": float(e.mean()), "bunch_E_lab_rms_MeV": float(e.std())}
+
+
 def lab_snapshots(wl, lines, step0):
     """Back-transform the recorded on-axis Ez lines (boosted steps step0 + 1, ...) to
     lab-frame snapshots at three lab times whose slices cross the laser pulse."""
@@ -528,6 +541,8 @@ def lwfa_run(args):
            "runs": {}}
     for gal in ([True, False] if args.lwfa_std else [True]):
         wl = gi.boosted_lwfa(*grid, galilean=gal, steps=args.steps)
+        if args.lwfa_bunch:
+            gi.add_witness_bunch(wl)
         t0 = time.perf_counter()
         sim = gp.sim_from_workload(wl, precision=32, tile_margin=args.margin)
         torch.cuda.synchronize()
@@ -561,7 +576,8 @@ def lwfa_run(args):
             ez = sim.get_line(2, xc, yc).double().cpu().numpy()
             W = sim.energy()
             c = sim.counters()
-            curve.append({"step": done, "W_over_W0": W / W0, "Ez_axis_max": float(np.abs(ez).max()),
+            extra = bunch_energy(sim, wl) if wl.bunch is not None else {}
+            curve.append({**extra, "step": done, "W_over_W0": W / W0, "Ez_axis_max": float(np.abs(ez).max()),
                           "Ez_axis_argmax_z": int(np.abs(ez).argmax()),
                           "Ez_axis_rms": float(np.sqrt(np.mean(ez * ez))),
                           "sorts": c["sorts"], "outside_bin": c["home_miss"], "outside_tile": c["far"]})
@@ -666,6 +682,8 @@ def main():
     ap.add_argument("--lwfa-grid", default="384,384,1536")
     ap.add_argument("--lwfa-every", type=int, default=100)
     ap.add_argument("--lwfa-std", action="store_true", help="also run the v_gal = 0 twin")
+    ap.add_argument("--lwfa-bunch", action="store_true",
+                    help="add the witness electron bunch (1 pC, 100 MeV) and report its lab-frame energy")
     ap.add_argument("--lwfa-lab", action="store_true",
                     help="record on-axis Ez every step and back-transform it to lab-frame snapshots")
     ap.add_argument("--tune", action="store_true",

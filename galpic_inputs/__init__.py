@@ -98,6 +98,7 @@ class Workload:
     steps: int = 1
     seed: int = 1
     laser: Optional["LaserSpec"] = None   # external field added to the initial state
+    bunch: Optional["BunchSpec"] = None   # explicit particles added as one more species
 
     @property
     def ncells(self) -> int:
@@ -357,3 +358,88 @@ def laser_box(wl: Workload, extent: float = 4.0, dtype=np.float64):
     B[1] = dAdz
     B[2] = -dAdy
     return (x0 % wl.nx, y0 % wl.ny, z0 % wl.nz), E, B
+
+
+@dataclass
+class BunchSpec:
+    """A Gaussian electron bunch given in the lab frame, placed in a boosted frame.
+
+    Lengths in cells of the boosted grid; the bunch is centred at (xc, yc, zc), its
+    lab-frame energy and length are transformed with the frame's gamma_boost.
+    """
+
+    n_macro: int
+    charge: float         # total charge in units of the plasma's normalised charge scale
+    gamma_lab: float      # lab-frame Lorentz factor of the bunch electrons
+    sigma_r: float        # transverse rms size (cells; invariant under the boost)
+    sigma_z_lab: float    # lab-frame rms length (cells of the boosted grid's length unit)
+    xc: float
+    yc: float
+    zc: float
+    gamma_boost: float
+    seed: int = 7
+
+
+ELECTRON_MC2_MEV = 0.51099895
+ELEMENTARY_CHARGE_PC = 1.602176634e-7   # picocoulomb per elementary charge
+
+
+def add_witness_bunch(wl: Workload, *, charge_pc: float = 1.0, energy_mev: float = 100.0,
+                      sigma_z_um: float = 1.0, sigma_r_um: float = 2.0, n_macro: int = 100_000,
+                      behind: float = 0.9, seed: int = 7) -> Workload:
+    """Add the paper's witness bunch (1 pC at 100 MeV, sigma_z = 1 um, sigma_r = 2 um,
+    lab frame) to a boosted_lwfa workload, `behind` plasma wavelengths behind the laser
+    centre (the back of the first bucket).
+
+    Units: the boosted cell is lambda_lab * gamma (1 + beta) / cells_per_lambda long, with
+    lambda_lab = 0.8 um; the plasma's normalised density n0 stands for the lab density
+    1e18 cm^-3 times gamma_boost, which fixes how many physical electrons one unit of
+    macro weight carries. The bunch keeps its lab-frame velocity: u' = gamma_b gamma
+    (beta - beta_b) c along z; its length in the boosted frame is its rest length
+    gamma sigma_z over gamma'. The initial fields are then the boosted-Coulomb field of
+    all charges moving at the bunch velocity (the neutral plasma contributes only noise).
+    """
+    L = wl.laser
+    if L is None:
+        raise ValueError("needs a boosted_lwfa workload")
+    # the plasma streams at -beta_b c: its momentum per mass gives the boost
+    uz = -wl.species[0].u0[2] / wl.c
+    gamma_b = math.sqrt(1.0 + uz * uz)
+    beta_b = uz / gamma_b
+    cell_um = 0.8 * gamma_b * (1.0 + beta_b) / L.wavelength
+    gamma = 1.0 + energy_mev / ELECTRON_MC2_MEV
+    beta = math.sqrt(1.0 - 1.0 / (gamma * gamma))
+    gamma_p = gamma_b * gamma * (1.0 - beta_b * beta)
+    sigma_z = sigma_z_um / cell_um * gamma / gamma_p
+    # plasma wavelength in the boosted frame: lab lambda_p = lambda / sqrt(n/n_c), stretched
+    lambda_p = L.wavelength / math.sqrt(LAB_DENSITY_RATIO)
+    n_phys = charge_pc / ELEMENTARY_CHARGE_PC                  # electrons in the bunch
+    per_weight = (1e18 * 1e-12 * gamma_b / wl.species[0].density) * cell_um ** 3   # electrons per unit weight
+    wl.bunch = BunchSpec(n_macro=n_macro, charge=n_phys / per_weight, gamma_lab=gamma,
+                         sigma_r=sigma_r_um / cell_um, sigma_z_lab=sigma_z, xc=L.xc, yc=L.yc,
+                         zc=L.z0 - behind * lambda_p, gamma_boost=gamma_b, seed=seed)
+    wl.init_fields = 1
+    wl.beta_init = (0.0, 0.0, (beta - beta_b) / (1.0 - beta * beta_b))
+    return wl
+
+
+def bunch_particles(wl: Workload):
+    """The bunch of ``wl`` as macro particles: dict with q, m, w, cell (int64), off (3 arrays
+    in [0, 1)), u (3 arrays, momentum per mass in the boosted frame)."""
+    b = wl.bunch
+    rng = np.random.default_rng(b.seed)
+    x = b.xc + b.sigma_r * rng.standard_normal(b.n_macro)
+    y = b.yc + b.sigma_r * rng.standard_normal(b.n_macro)
+    z = b.zc + b.sigma_z_lab * rng.standard_normal(b.n_macro)
+    beta_b = math.sqrt(1.0 - 1.0 / (b.gamma_boost ** 2))
+    beta = math.sqrt(1.0 - 1.0 / (b.gamma_lab ** 2))
+    uz = b.gamma_boost * b.gamma_lab * (beta - beta_b) * wl.c
+    out = []
+    for v, n, d in ((x, wl.nx, wl.dx), (y, wl.ny, wl.dy), (z, wl.nz, wl.dz)):
+        i, f = _renormalise(np.zeros(v.shape, dtype=np.int64), v / d, n)
+        out.append((i, f))
+    (ix, fx), (iy, fy), (iz, fz) = out
+    cell = (ix * wl.ny + iy) * wl.nz + iz
+    zeros = np.zeros(b.n_macro)
+    return {"q": -1.0, "m": 1.0, "w": b.charge / b.n_macro, "cell": cell, "off": [fx, fy, fz],
+            "u": [zeros, zeros.copy(), np.full(b.n_macro, uz)]}

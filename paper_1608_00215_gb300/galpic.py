@@ -342,7 +342,17 @@ def sim_from_workload(wl, precision: Optional[int] = None, stream=None, device="
     for k, s in enumerate(wl.species):
         w = s.density * wl.dx * wl.dy * wl.dz / (s.ppc[0] * s.ppc[1] * s.ppc[2])
         sp.append(generated_species(s.q, s.m, w, ncells, s.ppc, s.u0, s.jitter, wl.seed, k))
-    sim = Sim(cfg, sp, stream=stream, device=device)
+    keep = ()
+    if getattr(wl, "bunch", None) is not None:   # explicit particles (galpic_inputs.bunch_particles)
+        import galpic_inputs as gi
+        b = gi.bunch_particles(wl)
+        real = torch.float64 if prec == 64 else torch.float32
+        cell = torch.from_numpy(b["cell"].astype(np.int32))
+        off = [torch.from_numpy(a).to(real) for a in b["off"]]
+        u = [torch.from_numpy(a).to(real) for a in b["u"]]
+        sp.append(copied_species(b["q"], b["m"], b["w"], cell, off, u))
+        keep = (cell, off, u)
+    sim = Sim(cfg, sp, stream=stream, device=device, keepalive=keep)
     if getattr(wl, "laser", None) is not None:
         add_laser(sim, wl)
     return sim

@@ -12,12 +12,15 @@ def oracle_state_from_sim(sim, wl):
     """Oracle config and state equal to the GPU run's current state (cast to FP64)."""
     cfg = problems.config_of(wl)
     torch.cuda.synchronize()
+    params = [(spec.q, spec.m, wl.weight(spec)) for spec in wl.species]
+    if getattr(wl, "bunch", None) is not None:    # explicit particles after the lattice species
+        params.append((-1.0, 1.0, wl.bunch.charge / wl.bunch.n_macro))
     species = []
-    for k, spec in enumerate(wl.species):
+    for k, (q, m, w) in enumerate(params):
         p = sim.get_particles(k, device="cpu")
         torch.cuda.synchronize()
         species.append(problems.species_from_arrays(
-            spec.q, spec.m, wl.weight(spec), p["cell"].numpy(), [t.double().numpy() for t in p["off"]],
+            q, m, w, p["cell"].numpy(), [t.double().numpy() for t in p["off"]],
             [t.double().numpy() for t in p["u"]], wl.ny, wl.nz))
     E_hat = sim.get(4, device="cpu").to(torch.complex128).numpy()
     B_hat = sim.get(5, device="cpu").to(torch.complex128).numpy()

@@ -128,3 +128,28 @@ def test_get_line_matches_full_copy(gp):
     with pytest.raises(gp.GalpicError):
         sim.get_line(6, 0, 0)
     sim.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_lwfa_with_witness_bunch_step_parity(gp, precision):
+    """The wakefield run with the witness bunch as a third set of particles (copied
+    from the host, moving at its own velocity, its boosted-Coulomb field in the
+    initial state): one step against the oracle (FP64 1e-11 and particles 1e-12;
+    FP32 1e-5)."""
+    wl = gi.add_witness_bunch(_small_lwfa(precision), n_macro=4000, behind=0.1)
+    sim = gp.sim_from_workload(wl)
+    assert sim.nspecies == 2
+    sim.step(2)
+    sim.sort()
+    cfg, st = oracle_state_from_sim(sim, wl)
+    sim.step(1)
+    pic.step(cfg, st)
+    torch.cuda.synchronize()
+    err = field_rel_l2(sim, st)
+    if precision == 64:
+        assert err < 1e-11, err
+        pos, uerr = particle_errors(sim, st, wl)
+        assert pos < 1e-12 and uerr < 1e-12
+    else:
+        assert err < 1e-5, err
+    sim.close()

@@ -1,9 +1,11 @@
 """CPU checks of the boosted-frame wakefield workload's inputs: the laser pulse is
 divergence-free in E and B, travels forward (c B_y = E_x on its axis), has the
-stated peak amplitude, and the plasma parameters follow the stated lab plasma."""
+stated peak amplitude, the plasma parameters follow the stated lab plasma, and the
+witness bunch is the stated lab-frame bunch seen from the boosted frame."""
 import math
 
 import numpy as np
+import pytest
 
 import galpic_inputs as gi
 
@@ -70,3 +72,33 @@ def test_laser_box_wraps_and_clips():
     # wider than the grid: clipped to one period starting at node 0
     assert (x0, y0, z0) == (0, 0, 0)
     assert E.shape == (3, 16, 16, 64)
+
+
+def test_witness_bunch_in_the_boosted_frame():
+    """The paper's witness bunch (1 pC, 100 MeV, sigma_z = 1 um, sigma_r = 2 um) placed in
+    the boosted frame: its charge, the lab energy recovered by the inverse boost, its
+    sizes and its place behind the laser."""
+    wl = gi.add_witness_bunch(gi.boosted_lwfa(steps=1), n_macro=200_000)
+    b = wl.bunch
+    p = gi.bunch_particles(wl)
+    g = 10.0
+    beta_b = math.sqrt(1 - 1 / g ** 2)
+    cell_um = 0.8 * g * (1 + beta_b) / 16.0
+    # charge: macro weight times count in electrons, through the plasma's density scale
+    per_weight = 1e18 * 1e-12 * g / wl.species[0].density * cell_um ** 3
+    assert abs(p["w"] * b.n_macro * per_weight * 1.602176634e-7 - 1.0) < 1e-12
+    # inverse boost of the momentum: gamma_lab = gamma_b (gamma' + beta_b u'_z / c)
+    uz = p["u"][2][0]
+    gp_ = math.sqrt(1 + uz * uz)
+    assert abs(g * (gp_ + beta_b * uz) - (1 + 100.0 / 0.51099895)) < 1e-9
+    assert np.all(p["u"][0] == 0) and np.all(p["u"][1] == 0)
+    # sizes: transverse invariant, longitudinal = rest length / gamma'
+    z = (p["cell"] % wl.nz) + p["off"][2]
+    x = (p["cell"] // (wl.ny * wl.nz)) + p["off"][0]
+    assert abs(np.std(x) - 2.0 / cell_um) < 0.02 * 2.0 / cell_um
+    assert abs(np.std(z) - 1.0 / cell_um * (1 + 100.0 / 0.51099895) / gp_) < 0.02 * np.std(z)
+    # behind the laser by 0.9 boosted plasma wavelengths
+    lam_p = 16.0 / math.sqrt(1e18 / 1.742e21)
+    assert abs(np.mean(z) - (wl.laser.z0 - 0.9 * lam_p)) < 0.2
+    assert p["cell"].min() >= 0 and p["cell"].max() < wl.ncells
+    assert wl.init_fields == 1 and wl.beta_init[2] == pytest.approx(uz / gp_)
