@@ -212,7 +212,8 @@ int pic_set(pic_sim* sim, int which, const void* src, size_t bytes, void* stream
  * graph is re-captured) and writes it to chosen[0] (margin) and chosen[1]
  * (strategy); chosen may be NULL. Each candidate takes three real, complete steps
  * (one to settle, two timed), so the run advances by 6 or 18 steps, exactly as
- * pic_step would advance it. Synchronises `stream`. Errors: PIC_EINVAL, PIC_ECUDA,
+ * pic_step would advance it. Candidates are tried margin 0 then 1, strategy 0, 1, 2;
+ * a later one replaces the best so far only when it is at least 2 % faster. Synchronises `stream`. Errors: PIC_EINVAL, PIC_ECUDA,
  * PIC_ECUFFT (the run keeps its previous choice). */
 int pic_tune(pic_sim* sim, int32_t chosen[2], void* stream);
 

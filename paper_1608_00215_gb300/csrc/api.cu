@@ -676,7 +676,9 @@ int pic_tune(pic_sim* s, int32_t chosen[2], void* stream) {
                 return rc;
             }
             s->steps += 3;
-            if (first || ms < tbest) {
+            // a later candidate must be clearly faster (2 %): timing noise does not flip
+            // the choice between near-equal candidates, and the earlier (simpler) one stays
+            if (first || ms < 0.98f * tbest) {
                 tbest = ms;
                 best_m = m;
                 best_d = k;
