@@ -236,9 +236,9 @@ def run_ours(args, rank, world, local_rank):
     grid = tuple(int(x) for x in args.grid.split(","))
     wl = workload(grid, order=args.order)
     P, N = wl.nparticles, wl.ncells
-    sim = gp.sim_from_workload(wl, precision=32, tile_margin=args.margin)
+    sim = gp.sim_from_workload(wl, precision=32, tile_margin=args.margin, deposit=args.deposit)
     # the autotuner picks tile margin and deposit strategy on this run (real steps)
-    tuned = sim.tune() if not args.no_tune else {"tile_margin": args.margin, "deposit": 0}
+    tuned = sim.tune() if not args.no_tune else {"tile_margin": args.margin, "deposit": args.deposit}
     torch.cuda.synchronize()
     for _ in range(args.warmup):
         sim.gather_push()
@@ -544,10 +544,10 @@ def lwfa_run(args):
         if args.lwfa_bunch:
             gi.add_witness_bunch(wl)
         t0 = time.perf_counter()
-        sim = gp.sim_from_workload(wl, precision=32, tile_margin=args.margin)
+        sim = gp.sim_from_workload(wl, precision=32, tile_margin=args.margin, deposit=args.deposit)
         torch.cuda.synchronize()
         init_s = time.perf_counter() - t0
-        strategy = sim.tune() if args.tune else {"tile_margin": args.margin, "deposit": 0}
+        strategy = sim.tune() if args.tune else {"tile_margin": args.margin, "deposit": args.deposit}
         tuned_steps = 0 if not args.tune else sim.counters()["steps"]
         xc, yc = wl.nx // 2, wl.ny // 2
         W0 = sim.energy()
@@ -663,7 +663,9 @@ def main():
     ap.add_argument("--order", type=int, default=3, help="shape order (default 3)")
     ap.add_argument("--margin", type=int, default=1, help="particle tile margin in cells (0 or 1)")
     ap.add_argument("--no-tune", action="store_true",
-                    help="skip the autotuner (pic_tune) and use --margin with the grouped deposit")
+                    help="skip the autotuner (pic_tune) and use --margin and --deposit")
+    ap.add_argument("--deposit", type=int, default=0,
+                    help="deposit strategy without the autotuner (0 grouped, 1 row, 2 grouped J+rho)")
     ap.add_argument("--serving-requests", type=int, default=32,
                     help="requests of the serving leg (0 skips it)")
     ap.add_argument("--serving-steps", type=int, default=50, help="steps per serving request")
