@@ -146,12 +146,29 @@ def fp32_peak_tflops():
 
 
 # DRAM bytes per particle and per cell of one particle-pass launch, keyed by (shape
-# order, precision, tile margin, deposit strategy), from the ncu capture summarised in
-# profiles/particle_pass_cubic_fp32_64x64x128.md (dram__bytes_read.sum +
-# dram__bytes_write.sum = 449.5 MB for 8,388,608 particles at 16 per cell, two species
-# sharing deposit groups); scaled to a launch by the particles it processes (the same
-# 16 particles per cell).
-PASS_TRAFFIC = {(3, 32, 0, 0): (53.6, 0.0)}
+# order, precision, tile margin, deposit strategy), from the ncu captures summarised in
+# profiles/particle_pass_cubic_fp32_row_64x64x128.md (row deposit: dram__bytes_read.sum +
+# dram__bytes_write.sum = 444.4 MB for 8,388,608 particles at 16 per cell) and
+# profiles/particle_pass_cubic_fp32_64x64x128.md (grouped deposit, two species sharing
+# groups: 449.5 MB); scaled to a launch by the particles it processes (the same 16
+# particles per cell).
+PASS_TRAFFIC = {(3, 32, 0, 0): (53.6, 0.0), (3, 32, 0, 1): (53.0, 0.0)}
+
+
+def pass_kernel_name(order, margin, deposit, equal_pair):
+    """Name of the FP32 particle-pass kernel one step launches, following the library's
+    choice: three CTAs per SM for linear shapes and for the grouped quadratic/cubic
+    deposit at tile margin 0, two for the row and combined-J-and-rho deposits; two
+    species of equal size share groups in the grouped and combined deposits."""
+    dep = ("GROUP", "ROW", "JR")[deposit] if order > 1 else "GROUP"
+    if order == 1 or (margin == 0 and dep == "GROUP"):
+        suffix = "_3"
+    elif dep in ("ROW", "JR"):
+        suffix = "_2"
+    else:
+        suffix = ""
+    mixed = equal_pair and order > 1 and dep in ("GROUP", "JR")
+    return f"particle_pass_kernel{suffix}<float,{order},STEP,{margin},{dep}{',mixed' if mixed else ''}>"
 
 
 def kspace_bytes(wl, precision):
@@ -288,9 +305,8 @@ def run_ours(args, rank, world, local_rank):
     achieved = particle_bytes(wl, 32) / (part_ms * 1e-3) / 1e9
     ks_achieved = kspace_bytes(wl, 32) / (ks_ms * 1e-3) / 1e9
     value = replica_throughput(P, args.steps, world, ms_max)
-    mixed = len(wl.species) == 2 and args.order > 1 and tuned["deposit"] == 0
-    kname = (f"particle_pass_kernel<float,{args.order},STEP,{tuned['tile_margin']},{tuned['deposit']}"
-             f"{',mixed' if mixed else ''}>")
+    kname = pass_kernel_name(args.order, tuned["tile_margin"], tuned["deposit"],
+                             len(wl.species) == 2 and wl.species[0].ppc_total == wl.species[1].ppc_total)
     tr = PASS_TRAFFIC.get((args.order, 32, tuned["tile_margin"], tuned["deposit"]))
     traffic = None if tr is None else tr[0] * P + tr[1] * N
     roof_hbm = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",

@@ -703,53 +703,13 @@ __device__ __forceinline__ void row_record(float* blk, const float* wxJ, const f
     }
 }
 
-// Adds acc[z].x / acc[z].y to two shared-memory rows p0[z], p1[z] for z in
-// [zlo, zhi], in chunks of four nodes: all reads, then all compare-and-swaps, then
-// the retries of those that lost a race (shared-memory float atomics are
-// compare-and-swap loops on this GPU).
-template <int TE>
-__device__ __forceinline__ void row_flush(unsigned* p0, unsigned* p1, const float2 (&acc)[TE], int zlo, int zhi) {
-#pragma unroll
-    for (int z0 = 0; z0 < TE; z0 += 4) {
-        unsigned o0[4], o1[4];
-        bool d0[4], d1[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int z = z0 + k;
-            d0[k] = d1[k] = true;
-            if (z < TE && z >= zlo && z <= zhi) {
-                o0[k] = *reinterpret_cast<volatile unsigned*>(p0 + z);
-                o1[k] = *reinterpret_cast<volatile unsigned*>(p1 + z);
-                d0[k] = d1[k] = false;
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int z = z0 + k;
-            if (z < TE && !d0[k]) {
-                unsigned prev = atomicCAS(p0 + z, o0[k], __float_as_uint(__uint_as_float(o0[k]) + acc[z].x));
-                d0[k] = prev == o0[k];
-                o0[k] = prev;
-                prev = atomicCAS(p1 + z, o1[k], __float_as_uint(__uint_as_float(o1[k]) + acc[z].y));
-                d1[k] = prev == o1[k];
-                o1[k] = prev;
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int z = z0 + k;
-            if (z >= TE) continue;
-            while (!d0[k]) {   // lost a race with another warp: retry (lock-free, always progresses)
-                const unsigned prev = atomicCAS(p0 + z, o0[k], __float_as_uint(__uint_as_float(o0[k]) + acc[z].x));
-                d0[k] = prev == o0[k];
-                o0[k] = prev;
-            }
-            while (!d1[k]) {
-                const unsigned prev = atomicCAS(p1 + z, o1[k], __float_as_uint(__uint_as_float(o1[k]) + acc[z].y));
-                d1[k] = prev == o1[k];
-                o1[k] = prev;
-            }
-        }
+// Adds v to the float at p, whose value was `old` when read: compare-and-swap,
+// retried while another warp changed it in between (shared-memory float atomics are
+// compare-and-swap loops on this GPU; lock-free, always progresses).
+__device__ __forceinline__ void cas_add_retry(unsigned* p, unsigned old, unsigned prev, float v) {
+    while (prev != old) {
+        old = prev;
+        prev = atomicCAS(p, old, __float_as_uint(__uint_as_float(old) + v));
     }
 }
 
@@ -758,20 +718,21 @@ __device__ __forceinline__ void row_flush(unsigned* p0, unsigned* p1, const floa
 // the tile (`row` = rx * TE + ry), so the particles of a whole row of cells form
 // one group. For a row, lane (h, a, b) = (lane >> 4, (lane >> 2) & 3, lane & 3)
 // owns the tile nodes (rx + a, ry + b, z) for every z and two components, (Jx, Jy)
-// for h = 0 and (Jz, rho) for h = 1, summed in registers as packed pairs: a member
-// whose stencil starts at z node j adds its staged x-weight-times-value pair times
-// its y-weight pair times z-weight pair c to node j + c (one packed multiply, four
-// packed FMAs). J (stencil at x^{n+1/2}) and rho (at x^{n+1}) of a particle normally
-// start at the same node; where they do not, the particle joins two (row, j) groups
-// with the other part zeroed. Each row's sums go to the shared tile once, over the
-// z range it touched. mJ / mR: this lane's J / rho stencil lies in the tile; zJ /
-// zR: its z start. Every lane of the warp must call this (warp-collective).
+// for h = 0 and (Jz, rho) for h = 1. The row is walked along z: at stencil start j
+// the members starting there add their staged x-weight-times-value pair times
+// y-weight pair times z-weight pair c to a window of four packed register pairs
+// (nodes j .. j + 3; one packed multiply, four packed FMAs each); node j is then
+// complete and goes to the shared tile, and the window shifts by one node. The walk
+// is one rolled loop, so its code is small. J (stencil at x^{n+1/2}) and rho (at
+// x^{n+1}) of a particle normally start at the same node; where they do not, the
+// particle joins two (row, j) groups with the other part zeroed. mJ / mR: this
+// lane's J / rho stencil lies in the tile; zJ / zR: its z start. Every lane of the
+// warp must call this (warp-collective).
 template <int TE>
 __device__ void row_deposit(float* sD, const float* stg, bool mJ, int rowJ, int zJ, bool mR, int rowR, int zR,
                             int lane) {
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int R = TE * TE * TE;
-    constexpr int NS = TE - 3;   // stencil starts along z
     constexpr int M = RowStage::MEMBER;
     const int h = lane >> 4, a = (lane >> 2) & 3, b = lane & 3;
     const bool hi = h != 0;
@@ -786,60 +747,76 @@ __device__ void row_deposit(float* sD, const float* stg, bool mJ, int rowJ, int 
         const unsigned gJ = __ballot_sync(FULL, inJ), gR = __ballot_sync(FULL, inR);
         pendJ &= ~gJ;
         pendR &= ~gR;
+        // stencil starts present in this row, and the nodes they touch
         const unsigned zs = __reduce_or_sync(FULL, (inJ ? 1u << zJ : 0u) | (inR ? 1u << zR : 0u));
-        float2 acc[TE];
-#pragma unroll
-        for (int z = 0; z < TE; ++z) acc[z] = make_float2(0.f, 0.f);
+        const unsigned touched = zs | (zs << 1) | (zs << 2) | (zs << 3);
+        const int jlo = __ffs(zs) - 1, jend = 31 - __clz(zs) + 3;
+        const int node0 = (cur + a * TE + b) * TE;
+        unsigned* const p0 = reinterpret_cast<unsigned*>(sD + (2 * h) * R + node0);
+        unsigned* const p1 = reinterpret_cast<unsigned*>(sD + (2 * h + 1) * R + node0);
+        float2 w0 = make_float2(0.f, 0.f), w1 = w0, w2 = w0, w3 = w0;
         auto coef = [&](int m) { return pmul(ld2(sx + m * M), ld2(sy + m * M)); };
-#pragma unroll
-        for (int j = 0; j < NS; ++j) {
-            if (!((zs >> j) & 1u)) continue;
-            const unsigned sJ = __ballot_sync(FULL, inJ && zJ == j);
-            const unsigned sR = __ballot_sync(FULL, inR && zR == j);
-            auto add = [&](int m, float2 c) {
-                const float4 z01 = *reinterpret_cast<const float4*>(sz + m * M);
-                const float4 z23 = *reinterpret_cast<const float4*>(sz + m * M + 4);
-                acc[j + 0] = pfma(c, make_float2(z01.x, z01.y), acc[j + 0]);
-                acc[j + 1] = pfma(c, make_float2(z01.z, z01.w), acc[j + 1]);
-                acc[j + 2] = pfma(c, make_float2(z23.x, z23.y), acc[j + 2]);
-                acc[j + 3] = pfma(c, make_float2(z23.z, z23.w), acc[j + 3]);
-            };
-            // members whose J and rho both start here, two at a time; cell-sorted
-            // particles make them one run of consecutive lanes
-            unsigned mm = sJ & sR;
-            if (mm) {
-                const int lo = __ffs(mm) - 1, len = __popc(mm);
-                if ((mm >> lo) == (len == 32 ? FULL : ((1u << len) - 1u))) {
-                    int m = lo;
-                    const int me = lo + len;
-                    for (; m + 1 < me; m += 2) {
-                        const float2 c1 = coef(m), c2 = coef(m + 1);
-                        add(m, c1);
-                        add(m + 1, c2);
-                    }
-                    if (m < me) add(m, coef(m));
-                } else {
-                    while (mm) {
-                        const int m = __ffs(mm) - 1;
-                        mm &= mm - 1;
-                        add(m, coef(m));
+        auto add = [&](int m, float2 c) {
+            const float4 z01 = *reinterpret_cast<const float4*>(sz + m * M);
+            const float4 z23 = *reinterpret_cast<const float4*>(sz + m * M + 4);
+            w0 = pfma(c, make_float2(z01.x, z01.y), w0);
+            w1 = pfma(c, make_float2(z01.z, z01.w), w1);
+            w2 = pfma(c, make_float2(z23.x, z23.y), w2);
+            w3 = pfma(c, make_float2(z23.z, z23.w), w3);
+        };
+#pragma unroll 1
+        for (int j = jlo; j <= jend; ++j) {   // warp-uniform bounds
+            const bool flush = (touched >> j) & 1u;
+            unsigned o0 = 0u, o1 = 0u;
+            if (flush) {   // read node j's old values before the adds, to overlap the latency
+                o0 = *reinterpret_cast<volatile unsigned*>(p0 + j);
+                o1 = *reinterpret_cast<volatile unsigned*>(p1 + j);
+            }
+            if ((zs >> j) & 1u) {
+                const unsigned sJ = __ballot_sync(FULL, inJ && zJ == j);
+                const unsigned sR = __ballot_sync(FULL, inR && zR == j);
+                // members whose J and rho both start here, two at a time; cell-sorted
+                // particles make them one run of consecutive lanes
+                unsigned mm = sJ & sR;
+                if (mm) {
+                    const int lo = __ffs(mm) - 1, len = __popc(mm);
+                    if ((mm >> lo) == (len == 32 ? FULL : ((1u << len) - 1u))) {
+                        int m = lo;
+                        const int me = lo + len;
+                        for (; m + 1 < me; m += 2) {
+                            const float2 c1 = coef(m), c2 = coef(m + 1);
+                            add(m, c1);
+                            add(m + 1, c2);
+                        }
+                        if (m < me) add(m, coef(m));
+                    } else {
+                        while (mm) {
+                            const int m = __ffs(mm) - 1;
+                            mm &= mm - 1;
+                            add(m, coef(m));
+                        }
                     }
                 }
+                // members with only one of J, rho starting here: zero the other part
+                unsigned rr = (sJ | sR) & ~(sJ & sR);
+                while (rr) {
+                    const int k = __ffs(rr) - 1;
+                    rr &= rr - 1;
+                    const float fJ = ((sJ >> k) & 1u) ? 1.f : 0.f, fR = ((sR >> k) & 1u) ? 1.f : 0.f;
+                    add(k, pmul(coef(k), make_float2(fJ, hi ? fR : fJ)));
+                }
             }
-            // members with only one of J, rho starting here: zero the other part
-            unsigned rr = (sJ | sR) & ~(sJ & sR);
-            while (rr) {
-                const int k = __ffs(rr) - 1;
-                rr &= rr - 1;
-                const float fJ = ((sJ >> k) & 1u) ? 1.f : 0.f, fR = ((sR >> k) & 1u) ? 1.f : 0.f;
-                add(k, pmul(coef(k), make_float2(fJ, hi ? fR : fJ)));
+            if (flush) {   // node j is complete: add it to the tile
+                const unsigned q0 = atomicCAS(p0 + j, o0, __float_as_uint(__uint_as_float(o0) + w0.x));
+                const unsigned q1 = atomicCAS(p1 + j, o1, __float_as_uint(__uint_as_float(o1) + w0.y));
+                cas_add_retry(p0 + j, o0, q0, w0.x);
+                cas_add_retry(p1 + j, o1, q1, w0.y);
             }
+            w0 = w1;
+            w1 = w2;
+            w2 = w3;
+            w3 = make_float2(0.f, 0.f);
         }
-        // add the row to the tile: nodes (rx + a, ry + b, z) over the touched z range
-        const int zlo = __ffs(zs) - 1, zhi = 31 - __clz(zs) + 3;
-        const int node0 = (cur + a * TE + b) * TE;
-        row_flush<TE>(reinterpret_cast<unsigned*>(sD + (2 * h) * R + node0),
-                      reinterpret_cast<unsigned*>(sD + (2 * h + 1) * R + node0), acc, zlo, zhi);
     }
 }
 
