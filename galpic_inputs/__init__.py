@@ -95,6 +95,7 @@ class Workload:
     beta_init: Tuple[float, float, float] = (0.0, 0.0, 0.0)  # drift of the initial Coulomb field
     init_fields: int = 1      # 1 = boosted-Coulomb field of rho^0, 0 = zero fields
     current_correction: int = 1
+    stencil_order: int = 0    # 0: spectral derivatives; even p: order-p centred differences
     steps: int = 1
     seed: int = 1
     laser: Optional["LaserSpec"] = None   # external field added to the initial state

@@ -17,12 +17,14 @@ Modules:
 * ``coefficients`` - the per-mode coefficients C, S, nu, theta, chi1..chi3 of
   the update, evaluated from their literal closed forms in 40-digit mpmath;
 * ``shapes``       - B-spline particle shapes evaluated from their definition;
+* ``stencils``     - modified wavenumbers of centred differences of even order p
+  (finite-order spectral stencils; order 0 is the paper's spectral k);
 * ``pic``          - grid, deposit, gather, Boris push, Galilean drift,
   spectral current correction, the update, energy and residual diagnostics
   and the full step.
 
-Parity status: the coefficients, the vacuum update, the deposit/gather, the
-FFT and the push are pinned against closed forms, quadrature, library
+Parity status: the coefficients, the vacuum update, the finite-order stencils,
+the deposit/gather, the FFT and the push are pinned against closed forms, quadrature, library
 routines and invariants in ``tests/test_oracle_*.py``. The full plasma step
 has no printed values in the paper to pin against: "parity unpinned" for the
 plasma step beyond those invariants and the qualitative NCI claim.

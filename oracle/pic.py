@@ -35,6 +35,7 @@ import numpy as np
 import scipy.fft as sfft
 
 from . import coefficients as coef
+from . import stencils
 from .shapes import weights_1d
 
 WORKERS = os.cpu_count() or 1
@@ -55,6 +56,7 @@ class Config:
     shape_order: int = 1
     current_correction: bool = True
     rho_bg: float = 0.0
+    stencil_order: int = 0   # 0: spectral k; even p: modified k of the order-p centred difference
 
     @property
     def shape(self):
@@ -114,10 +116,14 @@ class State:
 # ----------------------------------------------------------------------------
 
 def kvectors(cfg: Config):
-    """k_d = 2 pi m_d / (N_d d_d), broadcastable to (nx, ny, nz//2+1)."""
-    kx = 2 * np.pi * np.fft.fftfreq(cfg.nx, cfg.dx)
-    ky = 2 * np.pi * np.fft.fftfreq(cfg.ny, cfg.dy)
-    kz = 2 * np.pi * np.fft.rfftfreq(cfg.nz, cfg.dz)
+    """k_d = 2 pi m_d / (N_d d_d), broadcastable to (nx, ny, nz//2+1); with a finite
+    stencil order, the modified wavenumbers [k_d] (``oracle.stencils``), used by every
+    stage that takes k: the curl, |k| and k.v_gal of the coefficients, the current
+    correction, the initial field and the residual diagnostics."""
+    p = cfg.stencil_order
+    kx = stencils.axis_wavenumbers(cfg.nx, cfg.dx, p)
+    ky = stencils.axis_wavenumbers(cfg.ny, cfg.dy, p)
+    kz = stencils.axis_wavenumbers(cfg.nz, cfg.dz, p, half=True)
     return kx[:, None, None], ky[None, :, None], kz[None, None, :]
 
 

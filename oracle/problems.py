@@ -16,7 +16,8 @@ from .pic import Config, Species, State, init_state
 
 def config_of(wl: gi.Workload) -> Config:
     return Config(wl.nx, wl.ny, wl.nz, wl.dx, wl.dy, wl.dz, wl.dt, tuple(wl.vgal), wl.c,
-                  wl.eps0, wl.shape_order, bool(wl.current_correction), wl.rho_bg)
+                  wl.eps0, wl.shape_order, bool(wl.current_correction), wl.rho_bg,
+                  wl.stencil_order)
 
 
 def species_of(wl: gi.Workload) -> List[Species]:
