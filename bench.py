@@ -37,11 +37,13 @@ GRID = (256, 256, 512)
 GAMMA = 130.0
 
 
-def workload(grid=GRID, order=3, precision=32):
+def workload(grid=GRID, order=3, precision=32, stencil_order=0):
+    import dataclasses
     import galpic_inputs as gi
-    return gi.drifting_plasma(*grid, GAMMA, galilean=True, shape_order=order, precision=precision,
-                              ppc=(2, 2, 2), jitter=1e-3, seed=2,
-                              name=f"drifting_plasma_{grid[0]}x{grid[1]}x{grid[2]}")
+    wl = gi.drifting_plasma(*grid, GAMMA, galilean=True, shape_order=order, precision=precision,
+                            ppc=(2, 2, 2), jitter=1e-3, seed=2,
+                            name=f"drifting_plasma_{grid[0]}x{grid[1]}x{grid[2]}")
+    return dataclasses.replace(wl, stencil_order=stencil_order) if stencil_order else wl
 
 
 def peaks():
@@ -179,11 +181,11 @@ def kspace_bytes(wl, precision):
     return M * C * (6 + 4 + 1 + 6 + 6 + 6 + 1)
 
 
-def cpu_baseline(steps=2, grid=(16, 16, 32)):
+def cpu_baseline(steps=2, grid=(16, 16, 32), stencil_order=0):
     """The FP64 oracle, as it stands, on a bounded sample of the same plasma."""
     import numpy as np  # noqa: F401
     from oracle import pic, problems
-    wl = workload(grid, order=3, precision=64)
+    wl = workload(grid, order=3, precision=64, stencil_order=stencil_order)
     cfg, st = problems.initial_state(wl)
     pic.step(cfg, st)          # warm caches (coefficient tables are built in initial_state)
     t0 = time.perf_counter()
@@ -218,7 +220,7 @@ def run_reference(args, rank):
         return
     grid = (16, 16, 32)
     from oracle import pic, problems
-    wl = workload(grid, order=3, precision=64)
+    wl = workload(grid, order=3, precision=64, stencil_order=args.stencil_order)
     cfg, st = problems.initial_state(wl)
     for _ in range(args.warmup):
         pic.step(cfg, st)
@@ -232,7 +234,8 @@ def run_reference(args, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": wl.name + " (bounded sample of the GPU arm's plasma)",
-                                            "grid": list(grid), "particles": P, "shape_order": 3},
+                                            "grid": list(grid), "particles": P, "shape_order": 3,
+                                            "stencil_order": args.stencil_order},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"{args.steps} FP64 oracle steps at {grid[0]}x{grid[1]}x{grid[2]} "
                                        f"({P} particles) of the same plasma"},
@@ -251,7 +254,7 @@ def run_ours(args, rank, world, local_rank):
     from paper_1608_00215_gb300 import galpic as gp
 
     grid = tuple(int(x) for x in args.grid.split(","))
-    wl = workload(grid, order=args.order)
+    wl = workload(grid, order=args.order, stencil_order=args.stencil_order)
     P, N = wl.nparticles, wl.ncells
     sim = gp.sim_from_workload(wl, precision=32, tile_margin=args.margin, deposit=args.deposit)
     # the autotuner picks tile margin and deposit strategy on this run (real steps)
@@ -326,6 +329,7 @@ def run_ours(args, rank, world, local_rank):
                                          "v_gal=v_drift, FP32 with FP64-built tables)",
                    "grid": list(grid), "particles": P, "cells": N, "shape_order": args.order, "precision": 32,
                    "parallelism": f"replicas x{world}", "tuned": tuned,
+                   "stencil_order": args.stencil_order,
                    "l2": "inputs larger than L2 (15 GB of particles, 0.8 GB of fields); no flush"},
         "cell_updates_per_s": N * args.steps * world / (ms_max * 1e-3),
         "stages_ms_per_step": {k: v["ms"] / max(1, v["count"]) for k, v in stages.items() if v["count"]},
@@ -345,7 +349,7 @@ def run_ours(args, rank, world, local_rank):
     if args.serving_requests > 0 and world == 1:
         line["serving"] = serving_bench(args.serving_requests, args.serving_steps)
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(stencil_order=args.stencil_order)
     print(json.dumps(line), flush=True)
 
 
@@ -680,6 +684,8 @@ def main():
     ap.add_argument("--margin", type=int, default=1, help="particle tile margin in cells (0 or 1)")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner (pic_tune) and use --margin and --deposit")
+    ap.add_argument("--stencil-order", type=int, default=0,
+                    help="0: spectral derivatives (the paper's solver); even p: finite-order stencil")
     ap.add_argument("--deposit", type=int, default=0,
                     help="deposit strategy without the autotuner (0 grouped, 1 row, 2 grouped J+rho)")
     ap.add_argument("--serving-requests", type=int, default=32,

@@ -97,6 +97,14 @@ typedef struct {
                                    (few particles per cell), 2: grouped by cell, J and
                                    rho in one group pass; other passes always group by
                                    cell (linear: J and rho together). pic_tune picks. */
+    int32_t stencil_order;      /* 0: spectral derivatives i k (the paper's solver);
+                                   even p in [2, 128]: finite-order spectral stencil,
+                                   every k_d of the update (curl, |k|, k.v_gal, current
+                                   correction, initial field) replaced by the symbol of
+                                   the centred difference of order p on the collocated
+                                   grid, [k_d] = (2/d) sum_{l<=p/2} a_l sin(l k_d d)
+                                   (the arbitrary-order solvers the paper's conclusion
+                                   names for domain decomposition); 0 on Nyquist planes */
 } pic_config;
 
 /* One particle species. Particles are either generated on the device on a

@@ -57,6 +57,8 @@ int validate(const pic_config* c, const pic_species* sp, int ns) {
     if (c->init_fields != 0 && c->init_fields != 1) return fail(PIC_EINVAL, "init_fields must be 0 or 1");
     if (c->tile_margin != 0 && c->tile_margin != 1) return fail(PIC_EINVAL, "tile_margin must be 0 or 1");
     if (c->deposit < 0 || c->deposit > 2) return fail(PIC_EINVAL, "deposit must be 0, 1 or 2");
+    if (c->stencil_order < 0 || c->stencil_order > 128 || (c->stencil_order & 1))
+        return fail(PIC_EINVAL, "stencil_order must be 0 or an even number in [2, 128]");
     if (ns < 0 || ns > PIC_MAX_SPECIES) return fail(PIC_EINVAL, "nspecies out of range");
     if (ns > 0 && !sp) return fail(PIC_EINVAL, "species array is NULL");
     int64_t ncell = (int64_t)c->nx * c->ny * c->nz;
@@ -170,6 +172,8 @@ void make_layout(const pic_config& c, const Dims& d, const int64_t* n, int ns, s
     L.off_Sh = take(4 * d.M * 2 * T);
     L.off_Rn = take(d.M * 2 * T);
     L.off_Tab = take(6 * d.M * 2 * T);
+    L.off_K = take((size_t)(d.nx + d.ny + d.nzh) * 8);
+    L.off_Kt = take((size_t)(d.nx + d.ny + d.nzh) * T);
     L.off_fftwork = take(std::max<size_t>(fft_bytes, 1));
     L.off_epart = take(2 * energy_blocks_for(d.N) * sizeof(double));
     L.off_cnt = take(CNT_COUNT * sizeof(unsigned long long));
@@ -426,6 +430,8 @@ int pic_init(const pic_config* cfg, const pic_species* species, int nspecies, vo
     s->Sh = w + L.off_Sh;
     s->Rn = w + L.off_Rn;
     s->Tab = w + L.off_Tab;
+    s->K = (double*)(w + L.off_K);
+    s->Kt = w + L.off_Kt;
     s->fftwork = w + L.off_fftwork;
     s->epart = (double*)(w + L.off_epart);
     s->energy_blocks = energy_blocks_for(s->d.N);
@@ -489,7 +495,7 @@ int pic_init(const pic_config* cfg, const pic_species* species, int nspecies, vo
     }
     INIT_TRY(set_force_sort(s, st));
     INIT_TRY(sort_particles(s, st));
-    count_launches(s, 3);   // tables, initial fields, scaled copy
+    count_launches(s, 4);   // wavenumbers, tables, initial fields, scaled copy
     INIT_TRY(launch_build_tables(s, st));
     INIT_TRY(deposit_sources(s, PASS_DEPOSIT, st));
     INIT_TRY(exec_r2c(s, st));

@@ -112,7 +112,7 @@ struct Layout {
     size_t off_species[PIC_MAX_SPECIES][8];   // cell, off x/y/z, u x/y/z, bin_start
     size_t off_tmp[8];                        // cell, off x/y/z, u x/y/z, rank
     size_t off_key_cnt, off_key_start, off_tile_sum;
-    size_t off_F, off_S, off_EBh, off_EBs, off_Sh, off_Rn, off_Tab;
+    size_t off_F, off_S, off_EBh, off_EBs, off_Sh, off_Rn, off_Tab, off_K, off_Kt;
     size_t off_fftwork;
     size_t off_epart;
     size_t off_cnt, off_status;
@@ -145,6 +145,8 @@ struct pic_sim {
     void* Sh;    // spectra of Jx, Jy, Jz, rho^{n+1} (4M complex)
     void* Rn;    // spectral rho^n (M complex)
     void* Tab;   // per-mode factors T1..T4, A5, A6 (6M complex)
+    double* K;   // wavenumbers per axis (spectral or modified), kx[nx], ky[ny], kz[nzh], FP64
+    void* Kt;    // the same in the run's precision
     void* fftwork;
     double* epart;
     int energy_blocks;

@@ -53,6 +53,63 @@ __device__ __forceinline__ int signed_index(int i, int n) { return i < (n + 1) /
 
 __device__ __forceinline__ double sinc_d(double a, double sa) { return a == 0.0 ? 1.0 : sa / a; }
 
+// Weights of the centred difference of even order p (at most 128):
+// f'(x) ~ (1/d) sum_{l=1}^{p/2} a_l (f(x + l d) - f(x - l d)).
+struct StencilWeights {
+    int m;            // p / 2; 0 = spectral (no stencil)
+    double a[64];
+};
+
+// a_l = (-1)^(l+1) (m!)^2 / (l (m-l)! (m+l)!), evaluated as the running product
+// prod_{j<=l} (m - j + 1)/(m + j) so that no factorial overflows.
+StencilWeights stencil_weights(int p) {
+    StencilWeights w;
+    w.m = p / 2;
+    double r = 1.0;
+    for (int l = 1; l <= w.m; ++l) {
+        r *= (double)(w.m - l + 1) / (double)(w.m + l);
+        w.a[l - 1] = (l & 1 ? r : -r) / l;
+    }
+    return w;
+}
+
+// Wavenumbers of the three axes in FFT order, kx[nx], ky[ny], kz[nzh] (half axis),
+// one thread per entry, FP64: spectral 2 pi s/(n d) for the signed index s, or the
+// symbol of the centred difference (2/d) sum_l a_l sin(2 pi l s / n), with the phase
+// l s reduced modulo n in integers and sin(pi x) taken by sinpi; 0 on the Nyquist
+// entry of an even axis for a finite stencil. Written in FP64 and in T.
+template <typename T>
+__global__ void wavenumbers_kernel(double* __restrict__ K, T* __restrict__ Kt, int nx, int ny, int nzh,
+                                   int nz, double dx, double dy, double dz, StencilWeights w) {
+    const int total = nx + ny + nzh;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        int n, s;
+        double d;
+        if (i < nx) {
+            n = nx, d = dx, s = signed_index(i, nx);
+        } else if (i < nx + ny) {
+            n = ny, d = dy, s = signed_index(i - nx, ny);
+        } else {
+            n = nz, d = dz, s = i - nx - ny;
+        }
+        double k;
+        if (w.m == 0) {
+            k = 2.0 * M_PI * ((double)s * (1.0 / ((double)n * d)));
+        } else if ((n & 1) == 0 && (s == n / 2 || s == -n / 2)) {
+            k = 0.0;
+        } else {
+            double acc = 0.0;
+            for (int l = 1; l <= w.m; ++l) {
+                const long long r = ((long long)l * s) % n;   // sign of s, |r| < n
+                acc += w.a[l - 1] * sinpi(2.0 * (double)r / (double)n);
+            }
+            k = 2.0 * acc / d;
+        }
+        K[i] = k;
+        Kt[i] = (T)k;
+    }
+}
+
 // Per-mode factors, FP64 throughout.
 //
 // With phi = c k dt, nu = k.v_gal/(c k), theta = exp(i nu phi/2) and
@@ -81,12 +138,10 @@ __device__ __forceinline__ double sinc_d(double a, double sa) { return a == 0.0 
 // the modes kx and -kx share them, and likewise along y: the kernel then evaluates
 // one representative mx <= nx/2 (my <= ny/2) and writes its mirrors too.
 template <typename C>
-__global__ void build_tables_kernel(C* __restrict__ tab, int nx, int ny, int nz, int nzh, int64_t M,
-                                    double dx, double dy, double dz, double dt, double vx, double vy,
+__global__ void build_tables_kernel(C* __restrict__ tab, const double* __restrict__ K, int nx, int ny,
+                                    int nz, int nzh, int64_t M, double dt, double vx, double vy,
                                     double vz, double c, double eps0, int cc, GaussLegendre gl, int fx,
                                     int fy) {
-    const double two_pi = 2.0 * M_PI;
-    const double inx = 1.0 / (nx * dx), iny = 1.0 / (ny * dy), inz = 1.0 / (nz * dz);
     const int X = fx ? nx / 2 + 1 : nx, Y = fy ? ny / 2 + 1 : ny;
     const int64_t Mrep = (int64_t)X * Y * nzh;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < Mrep;
@@ -96,9 +151,7 @@ __global__ void build_tables_kernel(C* __restrict__ tab, int nx, int ny, int nz,
         int my = (int)(r % Y);
         int mx = (int)(r / Y);
         const int64_t m = ((int64_t)mx * ny + my) * nzh + mz;
-        double kx = two_pi * (signed_index(mx, nx) * inx);
-        double ky = two_pi * (signed_index(my, ny) * iny);
-        double kz = two_pi * (mz * inz);
+        const double kx = K[mx], ky = K[nx + my], kz = K[nx + ny + mz];
         double k2 = kx * kx + ky * ky + kz * kz;
         double2 T1, T2, T3, T4, A5, A6;
         if (k2 == 0.0) {
@@ -187,7 +240,9 @@ struct KParams {
     const C* tab;    // T1, T2, T3, T4, A5, A6
     int64_t M;
     int nx, ny, nz, nzh;
-    T kfx, kfy, kfz;  // 2 pi / (n d) per axis
+    const T* kx;      // wavenumbers per axis: kx[nx], ky[ny], kz[nzh]
+    const T* ky;
+    const T* kz;
     T c2;             // c^2
     T invN;
     T bg[3];          // N rho_bg v_gal: background current at k = 0
@@ -222,9 +277,7 @@ __global__ void __launch_bounds__(256) kspace_update_kernel(KParams<T> p) {
             p.Rn[m] = z;
             continue;
         }
-        T kx = p.kfx * (T)signed_index(mx, p.nx);
-        T ky = p.kfy * (T)signed_index(my, p.ny);
-        T kz = p.kfz * (T)mz;
+        const T kx = p.kx[mx], ky = p.ky[my], kz = p.kz[mz];
         C Ex = p.EBh[0 * M + m], Ey = p.EBh[1 * M + m], Ez = p.EBh[2 * M + m];
         C Bx = p.EBh[3 * M + m], By = p.EBh[4 * M + m], Bz = p.EBh[5 * M + m];
         C Jx = p.Sh[0 * M + m], Jy = p.Sh[1 * M + m], Jz = p.Sh[2 * M + m];
@@ -286,7 +339,7 @@ __global__ void __launch_bounds__(256) kspace_update_kernel(KParams<T> p) {
 //   init 0: E = B = 0.  k = 0 and Nyquist modes: E = B = 0; rho^n = rho^0 (0 on Nyquist).
 template <typename C>
 __global__ void init_fields_kernel(C* EBh, C* Rn, const C* Sh, int64_t M, int nx, int ny, int nz,
-                                   int nzh, double kfx, double kfy, double kfz, double bx, double by,
+                                   int nzh, const double* __restrict__ K, double bx, double by,
                                    double bz, double c, double eps0, int mode) {
     for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M;
          m += (int64_t)gridDim.x * blockDim.x) {
@@ -298,7 +351,7 @@ __global__ void init_fields_kernel(C* EBh, C* Rn, const C* Sh, int64_t M, int nx
         double2 E[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
         double2 B[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
         bool nyq = is_nyquist(mx, my, mz, nx, ny, nz);
-        double kx = kfx * signed_index(mx, nx), ky = kfy * signed_index(my, ny), kz = kfz * mz;
+        const double kx = K[mx], ky = K[nx + my], kz = K[nx + ny + mz];
         double k2 = kx * kx + ky * ky + kz * kz;
         if (mode == 1 && !nyq && k2 > 0.0) {
             double kb = kx * bx + ky * by + kz * bz;
@@ -423,14 +476,24 @@ int launch_build_tables(pic_sim* s, cudaStream_t st) {
     GaussLegendre gl = gauss_legendre();
     const int fx = c.vgal[0] == 0.0, fy = c.vgal[1] == 0.0;
     const int64_t rep = (int64_t)(fx ? s->d.nx / 2 + 1 : s->d.nx) * (fy ? s->d.ny / 2 + 1 : s->d.ny) * s->d.nzh;
+    // wavenumbers first: the tables, the initial field and every k-space update read them
+    const StencilWeights sw = stencil_weights(c.stencil_order);
+    const int nk = s->d.nx + s->d.ny + s->d.nzh;
+    if (c.precision == 64)
+        wavenumbers_kernel<double><<<(nk + 127) / 128, 128, 0, st>>>(
+            s->K, (double*)s->Kt, s->d.nx, s->d.ny, s->d.nzh, s->d.nz, c.dx, c.dy, c.dz, sw);
+    else
+        wavenumbers_kernel<float><<<(nk + 127) / 128, 128, 0, st>>>(
+            s->K, (float*)s->Kt, s->d.nx, s->d.ny, s->d.nzh, s->d.nz, c.dx, c.dy, c.dz, sw);
+    GP_CUDA(cudaGetLastError());
     int grid = grid_for(rep, 128);
     if (c.precision == 64)
         build_tables_kernel<double2><<<grid, 128, 0, st>>>(
-            (double2*)s->Tab, s->d.nx, s->d.ny, s->d.nz, s->d.nzh, s->d.M, c.dx, c.dy, c.dz, c.dt,
+            (double2*)s->Tab, s->K, s->d.nx, s->d.ny, s->d.nz, s->d.nzh, s->d.M, c.dt,
             c.vgal[0], c.vgal[1], c.vgal[2], c.c, c.eps0, c.current_correction, gl, fx, fy);
     else
         build_tables_kernel<float2><<<grid, 128, 0, st>>>(
-            (float2*)s->Tab, s->d.nx, s->d.ny, s->d.nz, s->d.nzh, s->d.M, c.dx, c.dy, c.dz, c.dt,
+            (float2*)s->Tab, s->K, s->d.nx, s->d.ny, s->d.nz, s->d.nzh, s->d.M, c.dt,
             c.vgal[0], c.vgal[1], c.vgal[2], c.c, c.eps0, c.current_correction, gl, fx, fy);
     GP_CUDA(cudaGetLastError());
     return PIC_OK;
@@ -451,9 +514,9 @@ static int kspace_typed(pic_sim* s, cudaStream_t st) {
     p.ny = s->d.ny;
     p.nz = s->d.nz;
     p.nzh = s->d.nzh;
-    p.kfx = (T)(2.0 * M_PI / (c.nx * c.dx));
-    p.kfy = (T)(2.0 * M_PI / (c.ny * c.dy));
-    p.kfz = (T)(2.0 * M_PI / (c.nz * c.dz));
+    p.kx = (const T*)s->Kt;
+    p.ky = p.kx + s->d.nx;
+    p.kz = p.ky + s->d.ny;
     p.c2 = (T)(c.c * c.c);
     p.invN = (T)(1.0 / (double)s->d.N);
     for (int d = 0; d < 3; ++d) p.bg[d] = (T)((double)s->d.N * c.rho_bg * c.vgal[d]);
@@ -469,18 +532,16 @@ int launch_kspace_update(pic_sim* s, cudaStream_t st) {
 
 int launch_init_fields(pic_sim* s, cudaStream_t st) {
     const pic_config& c = s->cfg;
-    double kfx = 2.0 * M_PI / (c.nx * c.dx), kfy = 2.0 * M_PI / (c.ny * c.dy),
-           kfz = 2.0 * M_PI / (c.nz * c.dz);
     int grid = grid_for(s->d.M, 256);
     if (c.precision == 64)
         init_fields_kernel<double2><<<grid, 256, 0, st>>>(
             (double2*)s->EBh, (double2*)s->Rn, (const double2*)s->Sh, s->d.M, s->d.nx, s->d.ny,
-            s->d.nz, s->d.nzh, kfx, kfy, kfz, c.beta_init[0], c.beta_init[1], c.beta_init[2], c.c,
+            s->d.nz, s->d.nzh, s->K, c.beta_init[0], c.beta_init[1], c.beta_init[2], c.c,
             c.eps0, c.init_fields);
     else
         init_fields_kernel<float2><<<grid, 256, 0, st>>>(
             (float2*)s->EBh, (float2*)s->Rn, (const float2*)s->Sh, s->d.M, s->d.nx, s->d.ny,
-            s->d.nz, s->d.nzh, kfx, kfy, kfz, c.beta_init[0], c.beta_init[1], c.beta_init[2], c.c,
+            s->d.nz, s->d.nzh, s->K, c.beta_init[0], c.beta_init[1], c.beta_init[2], c.c,
             c.eps0, c.init_fields);
     GP_CUDA(cudaGetLastError());
     return PIC_OK;

@@ -33,7 +33,7 @@ class PicConfig(ctypes.Structure):
                 ("beta_init", c_double * 3),
                 ("nx", c_int32), ("ny", c_int32), ("nz", c_int32), ("shape_order", c_int32),
                 ("precision", c_int32), ("current_correction", c_int32), ("init_fields", c_int32),
-                ("tile_margin", c_int32), ("deposit", c_int32)]
+                ("tile_margin", c_int32), ("deposit", c_int32), ("stencil_order", c_int32)]
 
 
 class PicSpecies(ctypes.Structure):
@@ -114,7 +114,8 @@ def _stream_ptr(stream: Optional[torch.cuda.Stream]) -> c_void_p:
 
 def make_config(nx: int, ny: int, nz: int, *, dx=1.0, dy=1.0, dz=1.0, dt=1.0, vgal=(0.0, 0.0, 0.0),
                 c=1.0, eps0=1.0, rho_bg=0.0, beta_init=(0.0, 0.0, 0.0), shape_order=1,
-                precision=32, current_correction=1, init_fields=1, tile_margin=1, deposit=0) -> PicConfig:
+                precision=32, current_correction=1, init_fields=1, tile_margin=1, deposit=0,
+                stencil_order=0) -> PicConfig:
     cfg = PicConfig()
     cfg.dx, cfg.dy, cfg.dz, cfg.dt = dx, dy, dz, dt
     cfg.vgal[:] = list(vgal)
@@ -125,6 +126,7 @@ def make_config(nx: int, ny: int, nz: int, *, dx=1.0, dy=1.0, dz=1.0, dt=1.0, vg
     cfg.current_correction, cfg.init_fields = current_correction, init_fields
     cfg.tile_margin = tile_margin
     cfg.deposit = deposit
+    cfg.stencil_order = stencil_order
     return cfg
 
 
@@ -336,7 +338,8 @@ def sim_from_workload(wl, precision: Optional[int] = None, stream=None, device="
                       c=wl.c, eps0=wl.eps0, rho_bg=wl.rho_bg, beta_init=wl.beta_init,
                       shape_order=wl.shape_order, precision=prec,
                       current_correction=wl.current_correction, init_fields=wl.init_fields,
-                      tile_margin=tile_margin, deposit=deposit)
+                      tile_margin=tile_margin, deposit=deposit,
+                      stencil_order=getattr(wl, "stencil_order", 0))
     ncells = wl.nx * wl.ny * wl.nz
     sp = []
     for k, s in enumerate(wl.species):

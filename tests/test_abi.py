@@ -50,6 +50,10 @@ def test_invalid_config_is_rejected_without_a_gpu(binding):
     assert binding.lib.pic_footprint(ctypes.byref(cfg), None, 0, ctypes.byref(n)) == -1
     cfg = binding.make_config(8, 8, 8, shape_order=4)
     assert binding.lib.pic_footprint(ctypes.byref(cfg), None, 0, ctypes.byref(n)) == -1
+    for bad in (-2, 3, 130):                      # stencil order: 0 or even in [2, 128]
+        cfg = binding.make_config(8, 8, 8, stencil_order=bad)
+        assert binding.lib.pic_footprint(ctypes.byref(cfg), None, 0, ctypes.byref(n)) == -1
+        assert b"stencil_order" in binding.lib.pic_last_error()
 
 
 PROBE = r"""
