@@ -19,6 +19,8 @@ Modules:
 * ``shapes``       - B-spline particle shapes evaluated from their definition;
 * ``stencils``     - modified wavenumbers of centred differences of even order p
   (finite-order spectral stencils; order 0 is the paper's spectral k);
+* ``two_grid``     - several plasmas, each on its own Galilean grid, sharing E and B
+  by superposition (field parts moved between grids by the exact Fourier shift);
 * ``pic``          - grid, deposit, gather, Boris push, Galilean drift,
   spectral current correction, the update, energy and residual diagnostics
   and the full step.
