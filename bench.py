@@ -546,6 +546,60 @@ def lab_snapshots(wl, lines, step0):
     return out
 
 
+def coupled_run(args):
+    """Two plasmas streaming along +z and -z at gamma = 130 (the bench plasma and its
+    mirror image), each on the Galilean grid that moves with it, sharing E and B
+    (pic_step_coupled): time per coupled step, the same two runs stepped alone (the
+    cost of the coupling is the difference), and the total field energy."""
+    import dataclasses
+    import torch
+    from paper_1608_00215_gb300 import build
+    build.build()
+    from paper_1608_00215_gb300 import galpic as gp
+    import galpic_inputs as gi
+    grid = tuple(int(x) for x in args.grid.split(","))
+    mirror = gi.drifting_plasma(*grid, GAMMA, galilean=True, shape_order=args.order, precision=32,
+                                ppc=(2, 2, 2), jitter=1e-3, seed=3, direction=-1,
+                                name=f"drifting_plasma_{grid[0]}x{grid[1]}x{grid[2]}_minus_z")
+    wls = [workload(grid, order=args.order, stencil_order=args.stencil_order),
+           dataclasses.replace(mirror, stencil_order=args.stencil_order)]
+    sims = [gp.sim_from_workload(wl, precision=32, tile_margin=args.margin, deposit=args.deposit)
+            for wl in wls]
+    P = sum(wl.nparticles for wl in wls)
+    gp.step_coupled(sims, 0)                  # total fields on both grids
+    W0 = sims[0].energy()
+    gp.step_coupled(sims, args.warmup)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    gp.step_coupled(sims, args.steps)
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    W1 = sims[0].energy()
+    for s in sims:                            # graph capture outside the timed region
+        s.step(1)
+    torch.cuda.synchronize()
+    a.record()
+    for s in sims:
+        s.step(args.steps)
+    b.record()
+    b.synchronize()
+    ms_alone = a.elapsed_time(b)
+    out = {"mode": "coupled_run", "grid": list(grid), "runs": [wl.name for wl in wls], "particles": P,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+           "pushes_per_s": P * args.steps / (ms * 1e-3), "ms_per_step_stepped_alone": ms_alone / args.steps,
+           "coupling_ms_per_step": (ms - ms_alone) / args.steps, "W_over_W0": W1 / W0,
+           "config": {"tile_margin": args.margin, "deposit": args.deposit, "shape_order": args.order,
+                      "stencil_order": args.stencil_order, "precision": 32,
+                      "v_gal": [list(wl.vgal) for wl in wls]},
+           "status": [s.status() for s in sims]}
+    for s in sims:
+        s.close()
+    print(json.dumps(out), flush=True)
+
+
 def lwfa_run(args):
     """Boosted-frame laser-wakefield run (384x384x1536, gamma_boost = 10, a0 = 2 laser,
     FP32, cubic): on-axis Ez and the field energy every `--lwfa-every` steps and the
@@ -701,6 +755,8 @@ def main():
     ap.add_argument("--long-run-oracle-grid", default="32,32,64", help="grid of the oracle comparison")
     ap.add_argument("--long-run-order", type=int, default=1,
                     help="shape order of the long run (1: the config-1 plasma; 3: the bench plasma)")
+    ap.add_argument("--coupled", action="store_true",
+                    help="two counter-streaming plasmas on their own Galilean grids sharing E and B")
     ap.add_argument("--lwfa", action="store_true",
                     help="boosted-frame laser-wakefield run (on-axis Ez, field energy) instead")
     ap.add_argument("--lwfa-grid", default="384,384,1536")
@@ -724,6 +780,9 @@ def main():
         return
     if args.lwfa:
         lwfa_run(args)
+        return
+    if args.coupled:
+        coupled_run(args)
         return
     if args.serving_only:
         from paper_1608_00215_gb300 import build

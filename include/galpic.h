@@ -195,6 +195,30 @@ int pic_step(pic_sim* sim, int nsteps, void* stream);
 /* Advance several runs by nsteps each, all enqueued on one stream. */
 int pic_step_many(pic_sim** sims, int nsims, int nsteps, void* stream);
 
+/* Several plasmas, each on its own Galilean grid, sharing E and B (the
+ * generalisation proposed in the paper's conclusion for counter-streaming
+ * plasmas: separate grids in different Galilean coordinates, only the
+ * electromagnetic field shared, by superposition). Each run's spectral state
+ * holds the part of the field its own plasma drives, advanced by the
+ * Galilean-PSATD update with its own v_gal; the grids coincide at t = 0, so
+ * node x' of run j sits at x' + v_gal,j t. Every step pushes each run's
+ * particles with the TOTAL field on its own nodes: the other runs' parts moved
+ * onto its grid by the exact Fourier shift exp(i k.(v_gal,j - v_gal,i) t)
+ * (spectral k, whatever the stencil order), added before its inverse FFT.
+ *   sims:   nsims (1..16) distinct runs with equal nx, ny, nz, dx, dy, dz, dt,
+ *           c, eps0 and precision, all at the same step count; the caller keeps
+ *           ownership.
+ *   nsteps: steps to take (>= 0; 0 only forms the total fields).
+ * On return every run's real E, B (PIC_BUF_E, PIC_BUF_B) is the total field at
+ * the new step; its spectral E, B stay its own part. Once coupled, runs should
+ * only be stepped through this call (pic_step would advance one part alone and
+ * gather only that part). Not graph-captured: each step enqueues each run's
+ * particle pass, forward FFT and k-space update, then per run and per other run
+ * two small kernels (shift phases, shifted add) and its inverse FFT.
+ * Errors: PIC_EINVAL for a bad array, a repeated run, mismatched grids or step
+ * counts; otherwise as pic_step. */
+int pic_step_coupled(pic_sim** sims, int nsims, int nsteps, void* stream);
+
 /* Field energy W = (eps0/2) sum (|E|^2 + c^2 |B|^2) dV of the real E^n, B^n,
  * written as one double to the DEVICE address out_dev. Sets
  * PIC_STATUS_NONFINITE in the status word if any field value is not finite. */

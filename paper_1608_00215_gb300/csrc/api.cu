@@ -174,6 +174,7 @@ void make_layout(const pic_config& c, const Dims& d, const int64_t* n, int ns, s
     L.off_Tab = take(6 * d.M * 2 * T);
     L.off_K = take((size_t)(d.nx + d.ny + d.nzh) * 8);
     L.off_Kt = take((size_t)(d.nx + d.ny + d.nzh) * T);
+    L.off_Ph = take((size_t)(d.nx + d.ny + d.nzh) * 2 * T);
     L.off_fftwork = take(std::max<size_t>(fft_bytes, 1));
     L.off_epart = take(2 * energy_blocks_for(d.N) * sizeof(double));
     L.off_cnt = take(CNT_COUNT * sizeof(unsigned long long));
@@ -302,18 +303,60 @@ int gather_push(pic_sim* s, cudaStream_t st) {
     return deposit_sources(s, PASS_STEP, st);
 }
 
-int field_update(pic_sim* s, cudaStream_t st) {
+// Forward transform of the sources and the k-space update (master spectrum and its
+// scaled copy for the inverse transform).
+int field_update_spectral(pic_sim* s, cudaStream_t st) {
     {
         StageTimer t(s, STAGE_R2C, st);
         GP_CHECK(exec_r2c(s, st));
     }
-    {
-        StageTimer t(s, STAGE_KSPACE, st);
-        count_launches(s, 1);
-        GP_CHECK(launch_kspace_update(s, st));
-    }
+    StageTimer t(s, STAGE_KSPACE, st);
+    count_launches(s, 1);
+    return launch_kspace_update(s, st);
+}
+
+int field_update(pic_sim* s, cudaStream_t st) {
+    GP_CHECK(field_update_spectral(s, st));
     StageTimer t(s, STAGE_C2R, st);
     return exec_c2r(s, st);
+}
+
+// Coupled runs: for every run, its inverse-transform copy (its own master / N when
+// `rescale`, else as the k-space update left it) plus the other runs' masters moved
+// onto its grid at the common time, then the inverse transform: the gathered field
+// of every run is the total field.
+int couple_fields(pic_sim** sims, int n, bool rescale, cudaStream_t st) {
+    const double t = (double)sims[0]->steps * sims[0]->cfg.dt;
+    for (int j = 0; j < n; ++j) {
+        pic_sim* s = sims[j];
+        if (rescale) {
+            count_launches(s, 1);
+            GP_CHECK(launch_master_to_scratch(s, st));
+        }
+        for (int i = 0; i < n; ++i) {
+            if (i == j) continue;
+            count_launches(s, 2);
+            GP_CHECK(launch_add_shifted(s, sims[i], t, st));
+        }
+        StageTimer tm(s, STAGE_C2R, st);
+        GP_CHECK(exec_c2r(s, st));
+    }
+    return PIC_OK;
+}
+
+int check_coupled(pic_sim** sims, int n) {
+    if (!sims || n < 1 || n > 16) return fail(PIC_EINVAL, "coupled runs: need 1 to 16 sims");
+    for (int j = 0; j < n; ++j) {
+        if (!sims[j]) return fail(PIC_EINVAL, "sims[" + std::to_string(j) + "] is NULL");
+        for (int i = 0; i < j; ++i)
+            if (sims[i] == sims[j]) return fail(PIC_EINVAL, "a sim appears twice in a coupled step");
+        const pic_config &a = sims[0]->cfg, &b = sims[j]->cfg;
+        if (a.nx != b.nx || a.ny != b.ny || a.nz != b.nz || a.dx != b.dx || a.dy != b.dy || a.dz != b.dz ||
+            a.dt != b.dt || a.c != b.c || a.eps0 != b.eps0 || a.precision != b.precision)
+            return fail(PIC_EINVAL, "coupled runs must share grid, cell size, dt, c, eps0 and precision");
+        if (sims[j]->steps != sims[0]->steps) return fail(PIC_EINVAL, "coupled runs must be at the same step");
+    }
+    return PIC_OK;
 }
 
 int capture_step(pic_sim* s) {
@@ -432,6 +475,7 @@ int pic_init(const pic_config* cfg, const pic_species* species, int nspecies, vo
     s->Tab = w + L.off_Tab;
     s->K = (double*)(w + L.off_K);
     s->Kt = w + L.off_Kt;
+    s->Ph = w + L.off_Ph;
     s->fftwork = w + L.off_fftwork;
     s->epart = (double*)(w + L.off_epart);
     s->energy_blocks = energy_blocks_for(s->d.N);
@@ -572,6 +616,22 @@ int pic_step_many(pic_sim** sims, int nsims, int nsteps, void* stream) {
     for (int k = 0; k < nsims; ++k) {
         sims[k]->steps += nsteps;
         sims[k]->launches += (int64_t)nsteps * sims[k]->graph_kernels;
+    }
+    return PIC_OK;
+}
+
+int pic_step_coupled(pic_sim** sims, int nsims, int nsteps, void* stream) {
+    GP_CHECK(check_coupled(sims, nsims));
+    if (nsteps < 0) return fail(PIC_EINVAL, "nsteps < 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    GP_CHECK(couple_fields(sims, nsims, true, st));   // total fields at the current step
+    for (int i = 0; i < nsteps; ++i) {
+        for (int k = 0; k < nsims; ++k) GP_CHECK(gather_push(sims[k], st));
+        for (int k = 0; k < nsims; ++k) {
+            GP_CHECK(field_update_spectral(sims[k], st));
+            sims[k]->steps += 1;
+        }
+        GP_CHECK(couple_fields(sims, nsims, false, st));
     }
     return PIC_OK;
 }

@@ -112,7 +112,7 @@ struct Layout {
     size_t off_species[PIC_MAX_SPECIES][8];   // cell, off x/y/z, u x/y/z, bin_start
     size_t off_tmp[8];                        // cell, off x/y/z, u x/y/z, rank
     size_t off_key_cnt, off_key_start, off_tile_sum;
-    size_t off_F, off_S, off_EBh, off_EBs, off_Sh, off_Rn, off_Tab, off_K, off_Kt;
+    size_t off_F, off_S, off_EBh, off_EBs, off_Sh, off_Rn, off_Tab, off_K, off_Kt, off_Ph;
     size_t off_fftwork;
     size_t off_epart;
     size_t off_cnt, off_status;
@@ -147,6 +147,7 @@ struct pic_sim {
     void* Tab;   // per-mode factors T1..T4, A5, A6 (6M complex)
     double* K;   // wavenumbers per axis (spectral or modified), kx[nx], ky[ny], kz[nzh], FP64
     void* Kt;    // the same in the run's precision
+    void* Ph;    // per-axis shift phases of a coupled step (nx + ny + nzh complex)
     void* fftwork;
     double* epart;
     int energy_blocks;
@@ -181,6 +182,9 @@ int launch_build_tables(pic_sim* s, cudaStream_t st);
 int launch_kspace_update(pic_sim* s, cudaStream_t st);
 int launch_init_fields(pic_sim* s, cudaStream_t st);
 int launch_master_to_scratch(pic_sim* s, cudaStream_t st);
+// Adds src's spectral master, moved onto dst's grid at time t and scaled by 1/N, to
+// dst's inverse-transform copy (two kernels: per-axis phases, then the add).
+int launch_add_shifted(pic_sim* dst, const pic_sim* src, double t, cudaStream_t st);
 // Adds six spectra (`add`, [6][M] complex) to the spectral master, Nyquist modes excluded.
 int launch_add_spectra(pic_sim* s, const void* add, cudaStream_t st);
 int launch_energy(pic_sim* s, double* out_dev, cudaStream_t st);

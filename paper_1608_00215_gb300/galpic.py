@@ -65,6 +65,7 @@ def _load():
         "pic_field_update": (c_int, [P, P]),
         "pic_step": (c_int, [P, c_int, P]),
         "pic_step_many": (c_int, [POINTER(P), c_int, c_int, P]),
+        "pic_step_coupled": (c_int, [POINTER(P), c_int, c_int, P]),
         "pic_diag_energy": (c_int, [P, P, P]),
         "pic_get": (c_int, [P, c_int, P, c_size_t, P]),
         "pic_set": (c_int, [P, c_int, P, c_size_t, P]),
@@ -93,7 +94,7 @@ lib = _load()
 
 # the exported names, as declared in include/galpic.h
 EXPORTS = ("pic_version", "pic_last_error", "pic_footprint", "pic_init", "pic_destroy", "pic_deposit",
-           "pic_gather_push", "pic_field_update", "pic_step", "pic_step_many", "pic_diag_energy",
+           "pic_gather_push", "pic_field_update", "pic_step", "pic_step_many", "pic_step_coupled", "pic_diag_energy",
            "pic_get", "pic_set", "pic_get_particles", "pic_set_particles", "pic_status",
            "pic_counters", "pic_sizes", "pic_profile", "pic_profile_read", "pic_sort",
            "pic_field_energy_noalloc", "pic_add_fields", "pic_sort_policy", "pic_tune", "pic_get_line")
@@ -327,6 +328,13 @@ def field_energy_noalloc(fields: torch.Tensor, n_cells: int, precision: int, eps
 def step_many(sims: Sequence[Sim], nsteps: int, stream=None):
     arr = (c_void_p * len(sims))(*[s.handle for s in sims])
     check(lib.pic_step_many(arr, len(sims), nsteps, _stream_ptr(stream)))
+
+
+def step_coupled(sims: Sequence[Sim], nsteps: int, stream=None):
+    """pic_step_coupled: runs on separate Galilean grids sharing E and B (each gathers
+    the total field; each spectral state keeps its own plasma's part)."""
+    arr = (c_void_p * len(sims))(*[s.handle for s in sims])
+    check(lib.pic_step_coupled(arr, len(sims), nsteps, _stream_ptr(stream)))
 
 
 def sim_from_workload(wl, precision: Optional[int] = None, stream=None, device="cuda",
