@@ -21,6 +21,8 @@ Modules:
   (finite-order spectral stencils; order 0 is the paper's spectral k);
 * ``two_grid``     - several plasmas, each on its own Galilean grid, sharing E and B
   by superposition (field parts moved between grids by the exact Fourier shift);
+* ``cylindrical``  - the quasi-cylindrical field solver, one azimuthal mode with a
+  discrete Hankel transform in r (field part only; no particles, no CUDA path yet);
 * ``pic``          - grid, deposit, gather, Boris push, Galilean drift,
   spectral current correction, the update, energy and residual diagnostics
   and the full step.
