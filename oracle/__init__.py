@@ -22,7 +22,10 @@ Modules:
 * ``two_grid``     - several plasmas, each on its own Galilean grid, sharing E and B
   by superposition (field parts moved between grids by the exact Fourier shift);
 * ``cylindrical``  - the quasi-cylindrical field solver, one azimuthal mode with a
-  discrete Hankel transform in r (field part only; no particles, no CUDA path yet);
+  discrete Hankel transform in r;
+* ``cylindrical_pic`` - the particle side of the quasi-cylindrical step (deposit and
+  gather per azimuthal mode, the fold across the axis) and the full step (no CUDA
+  path exists for this geometry yet);
 * ``pic``          - grid, deposit, gather, Boris push, Galilean drift,
   spectral current correction, the update, energy and residual diagnostics
   and the full step.

@@ -1,9 +1,8 @@
 """Quasi-cylindrical spectral field solver: one azimuthal mode of the Galilean-PSATD
 update in (r, z) with a discrete Hankel transform in r.
 
-Test infrastructure only (see ``oracle/__init__``). Field part only: the particle
-side of a quasi-cylindrical step (deposit and gather per azimuthal mode) is not
-written yet, and no CUDA path exists for this geometry.
+Test infrastructure only (see ``oracle/__init__``). The particle side and the full
+step are in ``oracle.cylindrical_pic``; no CUDA path exists for this geometry.
 
 The paper runs its boosted-frame results in the quasi-cylindrical code it names
 (the implementation paragraph after the update equations). Reading, from general
@@ -40,6 +39,7 @@ from dataclasses import dataclass
 import numpy as np
 from scipy.special import jn_zeros, jv
 
+from . import coefficients as coef
 from . import pic
 
 
@@ -147,6 +147,13 @@ def _cartesian(cfg: CylConfig):
     return pc, (KR.ravel(), np.zeros(KR.size), KZ.ravel())
 
 
+@functools.lru_cache(maxsize=32)
+def _tables(cfg: CylConfig):
+    """The update's coefficients at every spectral node of ``cfg`` (cached)."""
+    pc, (a, b, c) = _cartesian(cfg)
+    return coef.coefficients(a, b, c, pc.vgal, pc.c, pc.dt, pc.eps0)
+
+
 def field_update(cfg: CylConfig, E_hat, B_hat, J_hat, rho_old_hat, rho_new_hat):
     """Galilean-PSATD update of one mode's spectral E, B (Cartesian amplitudes at phi =
     0), with the current correction when configured: the Cartesian update at
@@ -157,5 +164,6 @@ def field_update(cfg: CylConfig, E_hat, B_hat, J_hat, rho_old_hat, rho_new_hat):
     J = flat(J_hat)
     if cfg.current_correction:
         J = pic.current_correction(pc, J, flat(rho_old_hat), flat(rho_new_hat), k=k)
-    E, B = pic.field_update(pc, flat(E_hat), flat(B_hat), J, flat(rho_old_hat), flat(rho_new_hat), k=k)
+    E, B = pic.field_update(pc, flat(E_hat), flat(B_hat), J, flat(rho_old_hat), flat(rho_new_hat), k=k,
+                            t=_tables(cfg))
     return _zero_nyquist_z(cfg, E.reshape(shp)), _zero_nyquist_z(cfg, B.reshape(shp))

@@ -291,20 +291,22 @@ def current_correction(cfg: Config, J_hat, rho_old_hat, rho_new_hat, k=None):
     return np.stack([J_hat[0] + kx * g, J_hat[1] + ky * g, J_hat[2] + kz * g])
 
 
-def field_update(cfg: Config, E_hat, B_hat, J_hat, rho_old_hat, rho_new_hat, k=None):
+def field_update(cfg: Config, E_hat, B_hat, J_hat, rho_old_hat, rho_new_hat, k=None, t=None):
     """The Galilean-PSATD update of spectral E and B from n to n+1 (paper's update equations):
 
     B^{n+1} = T1 B^n - T2 (i k x E^n) + T3 (i k x J^{n+1/2})
     E^{n+1} = T1 E^n + c^2 T2 (i k x B^n) + T4 J^{n+1/2} - (T5 rho^{n+1} - T6 rho^n) i k
     with T1..T6 from ``oracle.coefficients``. ``k`` = (kx, ky, kz) selects other modes
-    than the whole grid (1-D arrays of the modes, data of shape (3, nmodes) / (nmodes,)).
+    than the whole grid (1-D arrays of the modes, data of shape (3, nmodes) / (nmodes,));
+    ``t``, the coefficients of those modes when the caller holds them already.
     """
     if k is None:
         t = tables(cfg)
         kx, ky, kz = kvectors(cfg)
     else:
         kx, ky, kz = k
-        t = coef.coefficients(kx, ky, kz, cfg.vgal, cfg.c, cfg.dt, cfg.eps0)
+        if t is None:
+            t = coef.coefficients(kx, ky, kz, cfg.vgal, cfg.c, cfg.dt, cfg.eps0)
     kvec = np.stack(np.broadcast_arrays(kx, ky, kz)).astype(np.complex128)
     ik = 1j * kvec
     B_new = t["T1"] * B_hat - t["T2"] * cross(ik, E_hat) + t["T3"] * cross(ik, J_hat)
