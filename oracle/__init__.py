@@ -26,6 +26,8 @@ Modules:
 * ``cylindrical_pic`` - the particle side of the quasi-cylindrical step (deposit and
   gather per azimuthal mode, the fold across the axis) and the full step (no CUDA
   path exists for this geometry yet);
+* ``domain_decomposition`` - the field update on subdomains along z with guard
+  cells, for finite-order stencils (no CUDA path);
 * ``pic``          - grid, deposit, gather, Boris push, Galilean drift,
   spectral current correction, the update, energy and residual diagnostics
   and the full step.
