@@ -17,8 +17,8 @@ the update's reach short enough that guard cells of modest width suffice. Readin
   exchanged again before the next update.
 * No Nyquist plane is zeroed inside a window: the window's wrap makes the field jump
   there, the Nyquist component of a window is not small, and removing it would
-  change every cell of the window. (A finite-order stencil leaves the Nyquist plane
-  of the window unchanged by the update, [k] = 0 there.)
+  change every cell of the window. (With a finite-order stencil [k] = 0 on the
+  window's Nyquist plane, so the update there only adds the source term, as at k = 0.)
 * Sources are deposited on the global grid, which equals summing the guard-cell
   deposits of neighbouring subdomains (the current exchange).
 * Decomposed runs go without the spectral current correction: it divides by k^2
