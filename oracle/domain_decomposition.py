@@ -17,14 +17,18 @@ the update's reach short enough that guard cells of modest width suffice. Readin
   exchanged again before the next update.
 * No Nyquist plane is zeroed inside a window: the window's wrap makes the field jump
   there, the Nyquist component of a window is not small, and removing it would
-  change every cell of the window. (With a finite-order stencil [k] = 0 on the
-  window's Nyquist plane, so the update there only adds the source term, as at k = 0.)
+  change every cell of the window. (With a finite-order stencil [k_z] = 0 on the
+  window's z-Nyquist plane, so the update there has no z derivative and acts only
+  through k_x and k_y.)
 * Sources are deposited on the global grid, which equals summing the guard-cell
   deposits of neighbouring subdomains (the current exchange).
 * Decomposed runs go without the spectral current correction: it divides by k^2
   (a Poisson solve), so its reach is the whole grid whatever the stencil, and a
   window's correction differs from the global one however wide the guards. The
-  update's own charge terms are analytic in k^2 and stay local.
+  update's own charge terms are analytic in k^2 and stay local. ``field_update``
+  applies the correction per window whenever ``cfg.current_correction`` is set (the
+  Config default), which is wrong for P > 1: callers of a decomposed run must set
+  ``current_correction=0``; the pins keep it on only to show that it is not local.
 * A window that covers the whole periodic grid (2 ng + N/P = N) reproduces the
   undecomposed update; with a finite-order stencil the result converges to it as ng
   grows, with the spectral solver (order 0) it does not (its update has unbounded

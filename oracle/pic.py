@@ -3,8 +3,7 @@
 Test infrastructure only (see ``oracle/__init__``). Plain NumPy/SciPy; every
 stage is a separate function in the order the paper lists the stages.
 
-Conventions (readings of points the paper leaves open; each is listed in
-DESIGN.md):
+Conventions (readings of points the paper leaves open):
 
 * Grid: collocated nodes at integer multiples of (dx, dy, dz), periodic. A
   particle position is ``(cell + offset) * d`` per axis, offset in [0, 1).

@@ -241,7 +241,7 @@ def test_bad_particle_input_is_rejected(gp):
 
 
 def test_config1_nci_fp64(gp):
-    """BASELINE config 1 (32x32x64, gamma = 130, linear shapes, FP64, 200 steps):
+    """The 32x32x64 drifting plasma (gamma = 130, linear shapes, FP64, 200 steps):
     field energy stays at noise level with v_gal = v_drift and grows by more
     than 1e3 with v_gal = 0; the first steps match the oracle at full size."""
     ratios = {}
