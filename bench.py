@@ -174,10 +174,10 @@ def pass_kernel_name(order, margin, deposit, equal_pair):
     choice: three CTAs per SM for linear shapes and for the grouped quadratic/cubic
     deposit at tile margin 0, two for the row and combined-J-and-rho deposits; two
     species of equal size share groups in the grouped and combined deposits."""
-    dep = ("GROUP", "ROW", "JR")[deposit] if order > 1 else "GROUP"
+    dep = ("GROUP", "ROW", "JR", "ROWU")[deposit] if order > 1 else "GROUP"
     if order == 1 or (margin == 0 and dep == "GROUP"):
         suffix = "_3"
-    elif dep in ("ROW", "JR"):
+    elif dep in ("ROW", "JR", "ROWU"):
         suffix = "_2"
     else:
         suffix = ""
@@ -268,7 +268,8 @@ def run_ours(args, rank, world, local_rank):
     grid = tuple(int(x) for x in args.grid.split(","))
     wl = workload(grid, order=args.order, stencil_order=args.stencil_order)
     P, N = wl.nparticles, wl.ncells
-    sim = gp.sim_from_workload(wl, precision=32, tile_margin=args.margin, deposit=args.deposit)
+    sim = gp.sim_from_workload(wl, precision=32, tile_margin=args.margin, deposit=args.deposit,
+                               deterministic=int(args.deterministic))
     # the autotuner picks tile margin and deposit strategy on this run (real steps)
     tuned = sim.tune() if not args.no_tune else {"tile_margin": args.margin, "deposit": args.deposit}
     torch.cuda.synchronize()
@@ -306,7 +307,7 @@ def run_ours(args, rank, world, local_rank):
 
     # end to end through the C ABI from pinned host buffers: H2D of the initial
     # particles inside pic_init, K steps each followed by a D2H read of the field energy
-    e2e = (e2e_run(gp, wl, args.steps, tuned) if not args.no_e2e
+    e2e = (e2e_run(gp, wl, args.steps, tuned, int(args.deterministic)) if not args.no_e2e
            else {"seconds": float("nan"), "h2d": 0, "d2h": 0})
 
     ms_max, e2e_max = slowest_rank(ms, e2e["seconds"], world, "cuda")
@@ -341,7 +342,7 @@ def run_ours(args, rank, world, local_rank):
                                          "v_gal=v_drift, FP32 with FP64-built tables)",
                    "grid": list(grid), "particles": P, "cells": N, "shape_order": args.order, "precision": 32,
                    "parallelism": f"replicas x{world}", "tuned": tuned,
-                   "stencil_order": args.stencil_order,
+                   "stencil_order": args.stencil_order, "deterministic": int(args.deterministic),
                    "l2": "inputs larger than L2 (15 GB of particles, 0.8 GB of fields); no flush"},
         "cell_updates_per_s": N * args.steps * world / (ms_max * 1e-3),
         "stages_ms_per_step": {k: v["ms"] / max(1, v["count"]) for k, v in stages.items() if v["count"]},
@@ -680,7 +681,7 @@ def lwfa_run(args):
     print(json.dumps(out), flush=True)
 
 
-def e2e_run(gp, wl, steps, tuned):
+def e2e_run(gp, wl, steps, tuned, deterministic=0):
     """The same workload end to end through the public API: particles from pinned host
     memory, the tile margin and deposit strategy the autotuner chose on the first run
     (a caller keeps them), pic_init and K steps with a D2H read of the field energy each."""
@@ -706,7 +707,8 @@ def e2e_run(gp, wl, steps, tuned):
                          c=wl.c, eps0=wl.eps0, rho_bg=wl.rho_bg, beta_init=wl.beta_init,
                          shape_order=wl.shape_order, precision=32,
                          current_correction=wl.current_correction, init_fields=wl.init_fields,
-                         tile_margin=tuned["tile_margin"], deposit=tuned["deposit"])
+                         tile_margin=tuned["tile_margin"], deposit=tuned["deposit"],
+                         deterministic=deterministic)
     species = [gp.copied_species(s.q, s.m, wl.weight(s), d["cell"], d["off"], d["u"])
                for s, d in zip(wl.species, pinned)]
     out = torch.empty(1, dtype=torch.float64).pin_memory()
@@ -742,6 +744,8 @@ def main():
                     help="skip the autotuner (pic_tune) and use --margin and --deposit")
     ap.add_argument("--stencil-order", type=int, default=0,
                     help="0: spectral derivatives (the paper's solver); even p: finite-order stencil")
+    ap.add_argument("--deterministic", action="store_true",
+                    help="order-independent fixed-point deposit (pic_config.deterministic)")
     ap.add_argument("--deposit", type=int, default=0,
                     help="deposit strategy without the autotuner (0 grouped, 1 row, 2 grouped J+rho)")
     ap.add_argument("--serving-requests", type=int, default=32,

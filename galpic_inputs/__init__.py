@@ -96,6 +96,7 @@ class Workload:
     init_fields: int = 1      # 1 = boosted-Coulomb field of rho^0, 0 = zero fields
     current_correction: int = 1
     stencil_order: int = 0    # 0: spectral derivatives; even p: order-p centred differences
+    deterministic: int = 0    # 1: order-independent (fixed-point) deposit in the CUDA runs
     steps: int = 1
     seed: int = 1
     laser: Optional["LaserSpec"] = None   # external field added to the initial state

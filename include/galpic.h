@@ -91,12 +91,17 @@ typedef struct {
                                    takes the global-memory path and counts toward the
                                    re-sort threshold; 1: particles up to one cell out
                                    still use the tile)                                 */
-    int32_t deposit;            /* deposit strategy of FP32 quadratic/cubic passes:
+    int32_t deposit;            /* deposit strategy. FP32 quadratic/cubic passes:
                                    0: grouped by cell, J and rho in separate group
                                    passes (many particles per cell), 1: by stencil row
                                    (few particles per cell), 2: grouped by cell, J and
-                                   rho in one group pass; other passes always group by
-                                   cell (linear: J and rho together). pic_tune picks. */
+                                   rho in one group pass, 3: by stencil row with the
+                                   row's nodes in registers (z starts unrolled).
+                                   Linear passes (FP32 or FP64): 0: grouped by cell, J
+                                   and rho together, 4: one thread per cell, the cell's
+                                   2x2x2 stencil accumulated in registers (particles at
+                                   rest on the grid). Other combinations use 0; FP64
+                                   quadratic/cubic passes always use 0. pic_tune picks. */
     int32_t stencil_order;      /* 0: spectral derivatives i k (the paper's solver);
                                    even p in [2, 128]: finite-order spectral stencil,
                                    every k_d of the update (curl, |k|, k.v_gal, current
@@ -105,6 +110,25 @@ typedef struct {
                                    grid, [k_d] = (2/d) sum_{l<=p/2} a_l sin(l k_d d)
                                    (the arbitrary-order solvers the paper's conclusion
                                    names for domain decomposition); 0 on Nyquist planes */
+    int32_t deterministic;      /* 0: the deposit sums in floating point through
+                                   atomics, so its rounding depends on the order in
+                                   which threads add (results agree to rounding, not
+                                   bit for bit); 1: every deposited value
+                                   q w v S(x_node - x)/dV and q w S/dV is rounded to an
+                                   integer multiple of delta = 2^e and summed as a 64-bit
+                                   integer, e being the smallest integer with
+                                   max(1, c) sum_s |q_s w_s| n_s / dV < 2^(62 + e) (no
+                                   node's sum can overflow); integer sums do not depend on the
+                                   order, so J, rho and every later stage are bitwise
+                                   reproducible: a run gives the same bits alone, next
+                                   to other runs, and continued from a checkpoint
+                                   (pic_get / pic_set / pic_get_particles). The
+                                   particle order inside a cell may still differ after a
+                                   re-sort; the particles as a set do not. Uses the
+                                   grouped deposit (pic_config.deposit is ignored) and
+                                   4*N int64 of extra workspace. delta is far below FP32
+                                   rounding; in FP64 runs a node's error is about delta
+                                   times the square root of its number of contributions */
 } pic_config;
 
 /* One particle species. Particles are either generated on the device on a
@@ -192,8 +216,33 @@ int pic_field_update(pic_sim* sim, void* stream);
  * CUDA graph captured on the first call. */
 int pic_step(pic_sim* sim, int nsteps, void* stream);
 
-/* Advance several runs by nsteps each, all enqueued on one stream. */
-int pic_step_many(pic_sim** sims, int nsims, int nsteps, void* stream);
+/* Serving many runs: several runs of one grid shape advanced in shared launches (the
+ * continuous-batching pattern of many small independent runs, which one GPU only keeps
+ * busy when their work goes out together). Each step of every run goes through one launch
+ * per stage for all of them: the re-sort check (per species slot), the particle pass (one
+ * CTA per run and bin), one batched forward transform over all runs' sources, one k-space
+ * update (one block row per run), one batched inverse transform; one such step of the set
+ * is captured once as a CUDA graph (cached for this workspace and set of runs) and
+ * replayed nsteps times. Each run's arithmetic is its single-run step's: results equal
+ * pic_step's to rounding (bitwise in deterministic mode).
+ *   sims:      nsims (1 .. 4096) distinct runs with equal nx, ny, nz, precision, shape
+ *              order, tile margin, deposit strategy (as chosen by pic_config.deposit or
+ *              pic_tune), species count and deterministic mode; other parameters (cell
+ *              size, dt, v_gal, c, species, stencil order, ...) may differ.
+ *   workspace: caller-owned device memory, 256-byte aligned, of at least
+ *              pic_many_footprint(sims[0], nsims) bytes: one slot per run (rounded up to a
+ *              power of two) for the sources, their spectra, the inverse-transform input
+ *              and the real E, B, plus the parameter tables and the FFT work area. Runs
+ *              keep their state in their own workspaces; the call copies their real E, B
+ *              in at the start and E, B, the sources and source spectra back at the end.
+ *              Two calls that overlap on the GPU must not share a workspace.
+ * Asynchronous on `stream`. The first call for a new set of runs (or a changed strategy)
+ * creates the batched cuFFT plans for its slot count (shared for the life of the process)
+ * and captures the step; pic_destroy forgets the captured steps of a destroyed run.
+ * Errors: PIC_EINVAL (bad arguments, runs that cannot share launches), PIC_ENOMEM
+ * (workspace too small), PIC_ECUDA, PIC_ECUFFT. */
+int pic_many_footprint(const pic_sim* sim, int capacity, size_t* bytes_out);
+int pic_step_many(pic_sim** sims, int nsims, int nsteps, void* workspace, size_t ws_bytes, void* stream);
 
 /* Several plasmas, each on its own Galilean grid, sharing E and B (the
  * generalisation proposed in the paper's conclusion for counter-streaming

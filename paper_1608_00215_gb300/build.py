@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libgalpic.so")
-SOURCES = ("pass_fp32.cu", "pass_fp64.cu", "particles.cu", "api.cu", "fields.cu", "noalloc.cu")
+SOURCES = ("pass_fp32.cu", "pass_fp64.cu", "particles.cu", "api.cu", "fields.cu", "noalloc.cu", "many.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")

@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -56,9 +57,10 @@ int validate(const pic_config* c, const pic_species* sp, int ns) {
     if (c->init_fields == 1 && !(b2 < 1.0)) return fail(PIC_EINVAL, "|beta_init| must be below 1");
     if (c->init_fields != 0 && c->init_fields != 1) return fail(PIC_EINVAL, "init_fields must be 0 or 1");
     if (c->tile_margin != 0 && c->tile_margin != 1) return fail(PIC_EINVAL, "tile_margin must be 0 or 1");
-    if (c->deposit < 0 || c->deposit > 2) return fail(PIC_EINVAL, "deposit must be 0, 1 or 2");
+    if (c->deposit < 0 || c->deposit > 4) return fail(PIC_EINVAL, "deposit must be 0 .. 4");
     if (c->stencil_order < 0 || c->stencil_order > 128 || (c->stencil_order & 1))
         return fail(PIC_EINVAL, "stencil_order must be 0 or an even number in [2, 128]");
+    if (c->deterministic != 0 && c->deterministic != 1) return fail(PIC_EINVAL, "deterministic must be 0 or 1");
     if (ns < 0 || ns > PIC_MAX_SPECIES) return fail(PIC_EINVAL, "nspecies out of range");
     if (ns > 0 && !sp) return fail(PIC_EINVAL, "species array is NULL");
     int64_t ncell = (int64_t)c->nx * c->ny * c->nz;
@@ -158,13 +160,14 @@ void make_layout(const pic_config& c, const Dims& d, const int64_t* n, int ns, s
         L.off_species[k][0] = take(n[k] * 4);
         for (int q = 1; q <= 6; ++q) L.off_species[k][q] = take(n[k] * T);
         L.off_species[k][7] = take((d.nbins + 1) * 4);
+        L.off_species[k][8] = take((sort_keys(d) + 1) * 4);
     }
     L.off_tmp[0] = take(nmax * 4);
     for (int q = 1; q <= 6; ++q) L.off_tmp[q] = take(nmax * T);
     L.off_tmp[7] = take(nmax * 4);
     L.off_key_cnt = take(sort_keys(d) * 4);
-    L.off_key_start = take(sort_keys(d) * 4);
     L.off_tile_sum = take(sort_tiles(d) * 4);
+    L.off_S64 = take(c.deterministic ? 4 * d.N * 8 : 0);
     L.off_F = take(6 * d.N * T);
     L.off_S = take(4 * d.N * T);
     L.off_EBh = take(6 * d.M * 2 * T);
@@ -291,10 +294,36 @@ int sort_particles(pic_sim* s, cudaStream_t st) {
 }
 
 int deposit_sources(pic_sim* s, int mode, cudaStream_t st) {
+    if (s->S64) {   // deterministic mode: integer sums, then the real sources from them
+        GP_CUDA(cudaMemsetAsync(s->S64, 0, 4 * s->d.N * sizeof(long long), st));
+        StageTimer t(s, STAGE_PARTICLES, st);
+        count_launches(s, 2);
+        GP_CHECK(launch_particle_pass(s, mode, st));
+        return launch_fixed_to_real(s, st);
+    }
     GP_CUDA(cudaMemsetAsync(s->S, 0, 4 * s->d.N * real_bytes(s), st));
     StageTimer t(s, STAGE_PARTICLES, st);
     count_launches(s, 1);
     return launch_particle_pass(s, mode, st);
+}
+
+// Deterministic mode: the fixed-point unit delta = 2^e, e the smallest integer with
+// max(1, c) sum_s |q_s w_s| n_s / dV < 2^(62 + e): a node's sum of deposited values is at
+// most that sum in magnitude, so its integer sum stays below 2^62 plus half a unit per
+// term (fewer than 2^40 terms), inside int64; partial sums may wrap, the total cannot.
+int fixed_point_exponent(const pic_config& c, const pic_species* sp, int ns) {
+    double B = 0.0;
+    const double dV = c.dx * c.dy * c.dz;
+    for (int k = 0; k < ns; ++k) B += fabs(sp[k].q * sp[k].w) * (double)sp[k].n / dV;
+    B *= std::max(1.0, c.c);
+    int e = -62;
+    if (B > 0.0 && std::isfinite(B)) {
+        int E = 0;
+        frexp(B, &E);    // B = m 2^E, 1/2 <= m < 1, so B < 2^E
+        e = E - 62;
+    }
+    // 1/delta must stay finite in the run's precision
+    return std::max(e, c.precision == 32 ? -120 : -1000);
 }
 
 int gather_push(pic_sim* s, cudaStream_t st) {
@@ -456,6 +485,7 @@ int pic_init(const pic_config* cfg, const pic_species* species, int nspecies, vo
             sp.u[dd] = w + L.off_species[k][4 + dd];
         }
         sp.bin_start = (int32_t*)(w + L.off_species[k][7]);
+        sp.cell_start = (int32_t*)(w + L.off_species[k][8]);
     }
     s->tmp_cell = (int32_t*)(w + L.off_tmp[0]);
     for (int dd = 0; dd < 3; ++dd) {
@@ -464,10 +494,11 @@ int pic_init(const pic_config* cfg, const pic_species* species, int nspecies, vo
     }
     s->tmp_rank = (int32_t*)(w + L.off_tmp[7]);
     s->key_cnt = (int32_t*)(w + L.off_key_cnt);
-    s->key_start = (int32_t*)(w + L.off_key_start);
     s->tile_sum = (int32_t*)(w + L.off_tile_sum);
     s->F = w + L.off_F;
     s->S = w + L.off_S;
+    s->S64 = cfg->deterministic ? (long long*)(w + L.off_S64) : nullptr;
+    s->fix_exp = fixed_point_exponent(*cfg, species, nspecies);
     s->EBh = w + L.off_EBh;
     s->EBs = w + L.off_EBs;
     s->Sh = w + L.off_Sh;
@@ -517,6 +548,8 @@ int pic_init(const pic_config* cfg, const pic_species* species, int nspecies, vo
         // every bin range starts empty (a species with no particles is never sorted)
         INIT_TRY(cudaMemsetAsync(s->sp[k].bin_start, 0, (s->d.nbins + 1) * sizeof(int32_t), st) ==
                          cudaSuccess ? PIC_OK : fail(PIC_ECUDA, "memset bin_start"));
+        INIT_TRY(cudaMemsetAsync(s->sp[k].cell_start, 0, (sort_keys(s->d) + 1) * sizeof(int32_t), st) ==
+                         cudaSuccess ? PIC_OK : fail(PIC_ECUDA, "memset cell_start"));
     }
     for (int k = 0; k < nspecies; ++k) {
         const pic_species& spec = species[k];
@@ -566,6 +599,7 @@ int pic_destroy(pic_sim* s) {
     // Only the run's own graph, private stream and events are released here; the
     // caller has finished (or synchronised) the work it enqueued on its streams.
     if (s->priv) cudaStreamSynchronize(s->priv);
+    many_forget(s);
     if (s->graph_ok) cudaGraphExecDestroy(s->graph);
     for (auto& r : s->recs) {
         cudaEventDestroy(r.a);
@@ -600,23 +634,6 @@ int pic_step(pic_sim* s, int nsteps, void* stream) {
     for (int i = 0; i < nsteps; ++i) GP_CUDA(cudaGraphLaunch(s->graph, st));
     s->steps += nsteps;
     s->launches += (int64_t)nsteps * s->graph_kernels;
-    return PIC_OK;
-}
-
-int pic_step_many(pic_sim** sims, int nsims, int nsteps, void* stream) {
-    if (!sims || nsims < 0) return fail(PIC_EINVAL, "bad sims array");
-    if (nsteps < 0) return fail(PIC_EINVAL, "nsteps < 0");
-    for (int k = 0; k < nsims; ++k) {
-        if (!sims[k]) return fail(PIC_EINVAL, "sims[" + std::to_string(k) + "] is NULL");
-        if (!sims[k]->graph_ok) GP_CHECK(capture_step(sims[k]));
-    }
-    cudaStream_t st = (cudaStream_t)stream;
-    for (int i = 0; i < nsteps; ++i)
-        for (int k = 0; k < nsims; ++k) GP_CUDA(cudaGraphLaunch(sims[k]->graph, st));
-    for (int k = 0; k < nsims; ++k) {
-        sims[k]->steps += nsteps;
-        sims[k]->launches += (int64_t)nsteps * sims[k]->graph_kernels;
-    }
     return PIC_OK;
 }
 
@@ -711,13 +728,26 @@ int pic_tune(pic_sim* s, int32_t chosen[2], void* stream) {
     } a, b;
     GP_CUDA(cudaEventCreate(&a.e));
     GP_CUDA(cudaEventCreate(&b.e));
-    const int nstrat = (s->cfg.precision == 32 && s->cfg.shape_order >= 2) ? 3 : 1;
+    // candidate deposit strategies: FP32 quadratic/cubic 0..3, linear 0 and 4 (one thread
+    // per cell), deterministic runs their single fixed-point deposit
+    int cand[4] = {0, 0, 0, 0};
+    int nstrat = 1;
+    if (!s->cfg.deterministic) {
+        if (s->cfg.precision == 32 && s->cfg.shape_order >= 2) {
+            nstrat = 4;
+            for (int k = 0; k < 4; ++k) cand[k] = k;
+        } else if (s->cfg.shape_order == 1) {
+            nstrat = 2;
+            cand[1] = 4;
+        }
+    }
     const int keep_m = s->d.margin, keep_d = s->cfg.deposit;
     int best_m = keep_m, best_d = keep_d;
     float tbest = 0.f;
     bool first = true;
     for (int m = 0; m < 2; ++m)
-        for (int k = 0; k < nstrat; ++k) {
+        for (int ki = 0; ki < nstrat; ++ki) {
+            const int k = cand[ki];
             s->d.margin = m;
             s->cfg.deposit = k;
             // one full step to settle (a re-sort may be due), then two timed ones;

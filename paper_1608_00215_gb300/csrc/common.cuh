@@ -105,13 +105,15 @@ struct SpeciesDev {
     void* off[3];
     void* u[3];
     int32_t* bin_start;   // nbins + 1
+    int32_t* cell_start;  // nbins * BX*BY*BZ + 1: first particle of each cell key as of the last sort
 };
 
 struct Layout {
     size_t total;
-    size_t off_species[PIC_MAX_SPECIES][8];   // cell, off x/y/z, u x/y/z, bin_start
+    size_t off_species[PIC_MAX_SPECIES][9];   // cell, off x/y/z, u x/y/z, bin_start, cell_start
     size_t off_tmp[8];                        // cell, off x/y/z, u x/y/z, rank
-    size_t off_key_cnt, off_key_start, off_tile_sum;
+    size_t off_key_cnt, off_tile_sum;
+    size_t off_S64;
     size_t off_F, off_S, off_EBh, off_EBs, off_Sh, off_Rn, off_Tab, off_K, off_Kt, off_Ph;
     size_t off_fftwork;
     size_t off_epart;
@@ -140,6 +142,8 @@ struct pic_sim {
     size_t ws_bytes;
     void* F;     // real E (3N) then B (3N)
     void* S;     // real Jx, Jy, Jz, rho (4N)
+    long long* S64;   // deterministic mode: the sources in 64-bit fixed point (4N), else NULL
+    int fix_exp;      // deterministic mode: delta = 2^fix_exp (units of the fixed-point sources)
     void* EBh;   // spectral master E, B (6M complex)
     void* EBs;   // C2R input: master / N (6M complex)
     void* Sh;    // spectra of Jx, Jy, Jz, rho^{n+1} (4M complex)
@@ -156,7 +160,6 @@ struct pic_sim {
     void* tmp_u[3];
     int32_t* tmp_rank;
     int32_t* key_cnt;     // sort: particles per cell key
-    int32_t* key_start;   // sort: first particle of each cell key
     int32_t* tile_sum;    // sort: scan partial sums
     unsigned long long* cnt;
     int32_t* status;
@@ -195,8 +198,45 @@ int launch_generate(pic_sim* s, int species, const pic_species* spec, cudaStream
 int launch_sort(pic_sim* s, cudaStream_t st);
 int launch_sanitize(pic_sim* s, int species, cudaStream_t st);
 int launch_particle_pass(pic_sim* s, int mode, cudaStream_t st);
+// Deterministic mode: real sources S = delta * S64 (4N values).
+int launch_fixed_to_real(pic_sim* s, cudaStream_t st);
 int launch_pass_fp32(pic_sim* s, int mode, cudaStream_t st);   // pass_fp32.cu
 int launch_pass_fp64(pic_sim* s, int mode, cudaStream_t st);   // pass_fp64.cu
+
+// Shared launches over several runs of one shape class (pic_step_many, many.cu).
+// Particle pass: parameter blocks (one per run, F, S, S64 redirected to a staging area)
+// and the launch over all of them; the variant code says which runs can share it.
+size_t pass_desc_bytes_fp32();
+size_t pass_desc_bytes_fp64();
+void fill_pass_desc_fp32(const pic_sim* s, void* out, const void* F, void* S, long long* S64);
+void fill_pass_desc_fp64(const pic_sim* s, void* out, const void* F, void* S, long long* S64);
+int launch_pass_many_fp32(pic_sim* s0, const void* descs, int nruns, cudaStream_t st);
+int launch_pass_many_fp64(pic_sim* s0, const void* descs, int nruns, cudaStream_t st);
+int pass_variant_of(const pic_sim* s);
+// K-space update: parameter blocks (EBs, Sh redirected) and the launch over them.
+size_t kspace_desc_bytes(int precision);
+void fill_kspace_desc(const pic_sim* s, void* out, void* EBs, const void* Sh);
+int launch_kspace_many(const pic_sim* s0, const void* descs, int nruns, cudaStream_t st);
+// Re-sort check of every run for one species slot: descriptor blocks and the kernels.
+size_t sort_desc_bytes(int precision);
+void fill_sort_desc(const pic_sim* s, int species, void* out);
+int launch_sort_many(const pic_sim* s0, const void* descs, int nruns, int64_t nmax, cudaStream_t st);
+// After the re-sort checks of every species: per run, a performed re-sort is counted and
+// the request cleared, and the stray counts are cleared for the next pass.
+int launch_sort_finish_many(unsigned long long* const* cnts_dev, int nruns, cudaStream_t st);
+// Copies of `n` (dst, src, bytes) triples listed in device memory, one launch.
+struct CopyDesc {
+    void* dst;
+    const void* src;
+    size_t bytes;
+};
+int launch_copy_many(const CopyDesc* descs_dev, int n, size_t max_bytes, cudaStream_t st);
+// Forget the captured shared-launch steps that involve a run (called by pic_destroy).
+void many_forget(pic_sim* s);
+// Deterministic mode over a staging area: real sources from fixed-point sums, run r of
+// nruns at S64 + r n (its unit 2^e[r], e in device memory).
+int launch_fixed_to_real_many(const long long* S64, void* S, int64_t n, const int* e_dev, int nruns,
+                              int precision, cudaStream_t st);
 
 enum { PASS_STEP = 0, PASS_DEPOSIT = 1 };
 enum { STAGE_SORT = 0, STAGE_PARTICLES = 1, STAGE_R2C = 2, STAGE_KSPACE = 3, STAGE_C2R = 4,

@@ -5,6 +5,9 @@
 //   * init_fields    - boosted-Coulomb field of rho^0 (or zero fields);
 //   * energy         - field energy W = (eps0/2) sum (|E|^2 + c^2 |B|^2) dV.
 #include <math.h>
+#include <string.h>
+
+#include <algorithm>
 
 #include <vector>
 
@@ -258,7 +261,7 @@ __device__ __forceinline__ bool is_nyquist(int mx, int my, int mz, int nx, int n
 // writes E, B (master and scaled copy) and rho^n. Every array is read or
 // written once, coalesced; this kernel is bound by HBM bandwidth.
 template <typename T>
-__global__ void __launch_bounds__(256) kspace_update_kernel(KParams<T> p) {
+__device__ __forceinline__ void kspace_update_body(const KParams<T>& p) {
     typedef typename cplx<T>::type C;
     const int64_t M = p.M;
     for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M;
@@ -332,6 +335,24 @@ __global__ void __launch_bounds__(256) kspace_update_kernel(KParams<T> p) {
         p.EBs[5 * M + m] = cscale(nBz, p.invN);
         p.Rn[m] = r1;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) kspace_update_kernel(KParams<T> p) {
+    kspace_update_body<T>(p);
+}
+
+// The k-space update of several runs of one grid shape in one launch: blockIdx.y picks
+// the run, whose parameters are copied from a device table into shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256) kspace_update_many_kernel(const KParams<T>* __restrict__ descs) {
+    __shared__ __align__(16) KParams<T> P;
+    static_assert(sizeof(KParams<T>) % 4 == 0, "KParams is copied as 32-bit words");
+    const int* a = reinterpret_cast<const int*>(descs + blockIdx.y);
+    int* d = reinterpret_cast<int*>(&P);
+    for (int i = threadIdx.x; i < (int)(sizeof(KParams<T>) / 4); i += blockDim.x) d[i] = a[i];
+    __syncthreads();
+    kspace_update_body<T>(P);
 }
 
 // Initial spectral state from rho^0 (fourth source spectrum). FP64 arithmetic.
@@ -548,13 +569,13 @@ int launch_build_tables(pic_sim* s, cudaStream_t st) {
 }
 
 template <typename T>
-static int kspace_typed(pic_sim* s, cudaStream_t st) {
+static void fill_kparams(const pic_sim* s, KParams<T>& p, void* EBs, const void* Sh) {
     typedef typename cplx<T>::type C;
     const pic_config& c = s->cfg;
-    KParams<T> p;
+    memset(&p, 0, sizeof(p));
     p.EBh = (C*)s->EBh;
-    p.EBs = (C*)s->EBs;
-    p.Sh = (const C*)s->Sh;
+    p.EBs = (C*)(EBs ? EBs : s->EBs);
+    p.Sh = (const C*)(Sh ? Sh : s->Sh);
     p.Rn = (C*)s->Rn;
     p.tab = (const C*)s->Tab;
     p.M = s->d.M;
@@ -569,6 +590,12 @@ static int kspace_typed(pic_sim* s, cudaStream_t st) {
     p.invN = (T)(1.0 / (double)s->d.N);
     for (int d = 0; d < 3; ++d) p.bg[d] = (T)((double)s->d.N * c.rho_bg * c.vgal[d]);
     p.cc = c.current_correction;
+}
+
+template <typename T>
+static int kspace_typed(pic_sim* s, cudaStream_t st) {
+    KParams<T> p;
+    fill_kparams<T>(s, p, nullptr, nullptr);
     kspace_update_kernel<T><<<grid_for(s->d.M, 256), 256, 0, st>>>(p);
     GP_CUDA(cudaGetLastError());
     return PIC_OK;
@@ -576,6 +603,29 @@ static int kspace_typed(pic_sim* s, cudaStream_t st) {
 
 int launch_kspace_update(pic_sim* s, cudaStream_t st) {
     return s->cfg.precision == 64 ? kspace_typed<double>(s, st) : kspace_typed<float>(s, st);
+}
+
+size_t kspace_desc_bytes(int precision) {
+    return precision == 64 ? sizeof(KParams<double>) : sizeof(KParams<float>);
+}
+
+void fill_kspace_desc(const pic_sim* s, void* out, void* EBs, const void* Sh) {
+    if (s->cfg.precision == 64)
+        fill_kparams<double>(s, *static_cast<KParams<double>*>(out), EBs, Sh);
+    else
+        fill_kparams<float>(s, *static_cast<KParams<float>*>(out), EBs, Sh);
+}
+
+int launch_kspace_many(const pic_sim* s0, const void* descs, int nruns, cudaStream_t st) {
+    // every run has the same mode count; the grid-stride loop covers it per run
+    const int gx = std::max(1, grid_for(s0->d.M, 256) / std::max(1, std::min(nruns, 16)));
+    const dim3 grid(gx, nruns);
+    if (s0->cfg.precision == 64)
+        kspace_update_many_kernel<double><<<grid, 256, 0, st>>>((const KParams<double>*)descs);
+    else
+        kspace_update_many_kernel<float><<<grid, 256, 0, st>>>((const KParams<float>*)descs);
+    GP_CUDA(cudaGetLastError());
+    return PIC_OK;
 }
 
 int launch_init_fields(pic_sim* s, cudaStream_t st) {

@@ -1,0 +1,352 @@
+// Shared launches over several runs of one grid shape: pic_many_footprint, pic_step_many.
+//
+// Each step of every run in the call goes through one launch per stage for all of them:
+// the re-sort check (per species slot), the particle pass (one CTA per run and bin), the
+// forward transform (one batched cuFFT plan over all runs' sources), the k-space update
+// (blockIdx.y = run) and the inverse transform (one batched plan). The runs keep their
+// state (particles, spectral E, B, rho^n) in their own workspaces; the arrays the
+// batched transforms read and write (sources, their spectra, the inverse-transform copy
+// and the real E, B the particles gather from) live in one caller-owned staging area
+// with a slot per run, so that one plan covers them with a fixed stride. The real E, B
+// are copied into the slots at the start of a call, and E, B, the sources and their
+// spectra back to the runs at its end. One step of the whole set is captured once as a
+// CUDA graph (cached per workspace and set of runs) and replayed nsteps times.
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "common.cuh"
+
+namespace galpic {
+namespace {
+
+size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+
+int pow2_at_least(int n) {
+    int c = 1;
+    while (c < n) c <<= 1;
+    return c;
+}
+
+struct ManyLayout {
+    size_t pass_bytes, kspace_bytes, sort_bytes;
+    size_t pass_desc, kspace_desc, sort_desc, copy_in, copy_out, cnt_ptrs, exps, desc_end;
+    size_t S, S64, Sh, EBs, F, work;
+    size_t total;
+};
+
+ManyLayout many_layout(const pic_sim* s, int C, size_t fft_work) {
+    const size_t T = s->cfg.precision == 64 ? 8 : 4;
+    const size_t N = (size_t)s->d.N, M = (size_t)s->d.M, c = (size_t)C;
+    ManyLayout L;
+    size_t o = 0;
+    auto take = [&](size_t b) {
+        size_t at = o;
+        o = up256(o + b);
+        return at;
+    };
+    L.pass_bytes = s->cfg.precision == 64 ? pass_desc_bytes_fp64() : pass_desc_bytes_fp32();
+    L.kspace_bytes = kspace_desc_bytes(s->cfg.precision);
+    L.sort_bytes = sort_desc_bytes(s->cfg.precision);
+    L.pass_desc = take(c * L.pass_bytes);
+    L.kspace_desc = take(c * L.kspace_bytes);
+    L.sort_desc = take((size_t)std::max(1, s->nspecies) * c * L.sort_bytes);
+    L.copy_in = take(c * sizeof(CopyDesc));
+    L.copy_out = take(3 * c * sizeof(CopyDesc));
+    L.cnt_ptrs = take(c * sizeof(void*));
+    L.exps = take(c * sizeof(int));
+    L.desc_end = o;
+    L.S = take(c * 4 * N * T);
+    L.S64 = take(s->cfg.deterministic ? c * 4 * N * 8 : 0);
+    L.Sh = take(c * 4 * M * 2 * T);
+    L.EBs = take(c * 6 * M * 2 * T);
+    L.F = take(c * 6 * N * T);
+    L.work = take(std::max<size_t>(fft_work, 1));
+    L.total = o;
+    return L;
+}
+
+// Batched cuFFT plans over C slots: R2C of 4C real grids, C2R of 6C spectra, contiguous.
+struct ManyPlan {
+    cufftHandle r2c = 0, c2r = 0;
+    size_t work = 0;
+    std::mutex mu;
+};
+
+std::mutex g_plan_mu;
+std::map<std::tuple<int, int, int, int, int, int>, std::unique_ptr<ManyPlan>> g_plans;
+
+int many_plan(const pic_sim* s, int C, ManyPlan** out) {
+    int dev = 0;
+    GP_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto key = std::make_tuple(dev, s->d.nx, s->d.ny, s->d.nz, s->cfg.precision, C);
+    auto it = g_plans.find(key);
+    if (it == g_plans.end()) {
+        std::unique_ptr<ManyPlan> e(new ManyPlan());
+        long long n[3] = {s->d.nx, s->d.ny, s->d.nz};
+        long long cn[3] = {s->d.nx, s->d.ny, s->d.nzh};
+        size_t w1 = 0, w2 = 0;
+        const bool dbl = s->cfg.precision == 64;
+        auto fail_plan = [&](cufftResult r, const char* what) {
+            if (e->r2c) cufftDestroy(e->r2c);
+            if (e->c2r) cufftDestroy(e->c2r);
+            return fail(PIC_ECUFFT, std::string(what) + ": cufft error " + std::to_string((int)r));
+        };
+        cufftResult r;
+        if ((r = cufftCreate(&e->r2c)) != CUFFT_SUCCESS) return fail_plan(r, "create");
+        if ((r = cufftCreate(&e->c2r)) != CUFFT_SUCCESS) return fail_plan(r, "create");
+        if ((r = cufftSetAutoAllocation(e->r2c, 0)) != CUFFT_SUCCESS) return fail_plan(r, "auto allocation");
+        if ((r = cufftSetAutoAllocation(e->c2r, 0)) != CUFFT_SUCCESS) return fail_plan(r, "auto allocation");
+        if ((r = cufftMakePlanMany64(e->r2c, 3, n, n, 1, s->d.N, cn, 1, s->d.M, dbl ? CUFFT_D2Z : CUFFT_R2C,
+                                     4LL * C, &w1)) != CUFFT_SUCCESS)
+            return fail_plan(r, "batched R2C plan");
+        if ((r = cufftMakePlanMany64(e->c2r, 3, n, cn, 1, s->d.M, n, 1, s->d.N, dbl ? CUFFT_Z2D : CUFFT_C2R,
+                                     6LL * C, &w2)) != CUFFT_SUCCESS)
+            return fail_plan(r, "batched C2R plan");
+        e->work = std::max(w1, w2);
+        it = g_plans.emplace(key, std::move(e)).first;
+    }
+    *out = it->second.get();
+    return PIC_OK;
+}
+
+// One captured step of a set of runs, replayed while the same runs are stepped together
+// in the same workspace.
+struct ManyGraph {
+    void* ws = nullptr;
+    int C = 0;
+    std::vector<pic_sim*> sims;
+    std::vector<int> variant;
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;
+};
+
+std::mutex g_graph_mu;
+std::vector<ManyGraph> g_graphs;
+constexpr size_t MAX_GRAPHS = 32;
+
+// Everything a captured step depends on besides the workspace contents: the runs, their
+// pass variant and tile margin (the autotuner may change both between calls).
+std::vector<int> variants_of(pic_sim* const* sims, int n) {
+    std::vector<int> v;
+    for (int r = 0; r < n; ++r) {
+        v.push_back(pass_variant_of(sims[r]));
+        v.push_back(sims[r]->d.margin);
+    }
+    return v;
+}
+
+int check_compatible(pic_sim* const* sims, int n) {
+    const pic_sim* a = sims[0];
+    for (int r = 0; r < n; ++r) {
+        const pic_sim* b = sims[r];
+        if (!b) return fail(PIC_EINVAL, "sims[" + std::to_string(r) + "] is NULL");
+        for (int q = 0; q < r; ++q)
+            if (sims[q] == b) return fail(PIC_EINVAL, "a sim appears twice in pic_step_many");
+        if (b->d.nx != a->d.nx || b->d.ny != a->d.ny || b->d.nz != a->d.nz ||
+            b->cfg.precision != a->cfg.precision || b->cfg.shape_order != a->cfg.shape_order ||
+            b->d.margin != a->d.margin || b->nspecies != a->nspecies ||
+            b->cfg.deterministic != a->cfg.deterministic || pass_variant_of(b) != pass_variant_of(a))
+            return fail(PIC_EINVAL, "pic_step_many: runs of one call must share grid, precision, shape order, "
+                                    "tile margin, deposit strategy, species count and deterministic mode");
+    }
+    return PIC_OK;
+}
+
+int capture_many(pic_sim** sims, int n, int C, char* ws, const ManyLayout& L, ManyPlan* mp, ManyGraph& g) {
+    pic_sim* s0 = sims[0];
+    const size_t T = s0->cfg.precision == 64 ? 8 : 4;
+    const int64_t N = s0->d.N;
+    int64_t nmax = 0;
+    for (int r = 0; r < n; ++r)
+        for (int k = 0; k < sims[r]->nspecies; ++k) nmax = std::max(nmax, sims[r]->sp[k].n);
+    cudaStream_t st = s0->priv;
+    cudaGraph_t graph = nullptr;
+    GP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    int64_t kernels = 0;
+    auto body = [&]() -> int {
+        for (int k = 0; k < s0->nspecies; ++k) {
+            GP_CHECK(launch_sort_many(s0, ws + L.sort_desc + (size_t)k * C * L.sort_bytes, n, nmax, st));
+            kernels += 7;
+        }
+        GP_CHECK(launch_sort_finish_many((unsigned long long* const*)(ws + L.cnt_ptrs), n, st));
+        kernels += 1;
+        if (s0->cfg.deterministic)
+            GP_CUDA(cudaMemsetAsync(ws + L.S64, 0, (size_t)C * 4 * N * 8, st));
+        else
+            GP_CUDA(cudaMemsetAsync(ws + L.S, 0, (size_t)C * 4 * N * T, st));
+        if (s0->cfg.precision == 64)
+            GP_CHECK(launch_pass_many_fp64(s0, ws + L.pass_desc, n, st));
+        else
+            GP_CHECK(launch_pass_many_fp32(s0, ws + L.pass_desc, n, st));
+        kernels += 1;
+        if (s0->cfg.deterministic) {
+            GP_CHECK(launch_fixed_to_real_many((const long long*)(ws + L.S64), ws + L.S, 4 * N,
+                                               (const int*)(ws + L.exps), n, s0->cfg.precision, st));
+            kernels += 1;
+        }
+        {
+            std::lock_guard<std::mutex> lk(mp->mu);
+            GP_CUFFT(cufftSetWorkArea(mp->r2c, ws + L.work));
+            GP_CUFFT(cufftSetStream(mp->r2c, st));
+            if (s0->cfg.precision == 64)
+                GP_CUFFT(cufftExecD2Z(mp->r2c, (cufftDoubleReal*)(ws + L.S), (cufftDoubleComplex*)(ws + L.Sh)));
+            else
+                GP_CUFFT(cufftExecR2C(mp->r2c, (cufftReal*)(ws + L.S), (cufftComplex*)(ws + L.Sh)));
+        }
+        GP_CHECK(launch_kspace_many(s0, ws + L.kspace_desc, n, st));
+        kernels += 1;
+        {
+            std::lock_guard<std::mutex> lk(mp->mu);
+            GP_CUFFT(cufftSetWorkArea(mp->c2r, ws + L.work));
+            GP_CUFFT(cufftSetStream(mp->c2r, st));
+            if (s0->cfg.precision == 64)
+                GP_CUFFT(cufftExecZ2D(mp->c2r, (cufftDoubleComplex*)(ws + L.EBs), (cufftDoubleReal*)(ws + L.F)));
+            else
+                GP_CUFFT(cufftExecC2R(mp->c2r, (cufftComplex*)(ws + L.EBs), (cufftReal*)(ws + L.F)));
+        }
+        return PIC_OK;
+    };
+    const int rc = body();
+    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    if (rc != PIC_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(PIC_ECUDA, std::string("pic_step_many capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(PIC_ECUDA, std::string("pic_step_many instantiate: ") + cudaGetErrorString(e));
+    g.kernels = kernels;
+    return PIC_OK;
+}
+
+}  // namespace
+
+// Drop the captured steps that involve a run being destroyed.
+void many_forget(pic_sim* s) {
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (size_t i = 0; i < g_graphs.size();) {
+        if (std::find(g_graphs[i].sims.begin(), g_graphs[i].sims.end(), s) != g_graphs[i].sims.end()) {
+            cudaGraphExecDestroy(g_graphs[i].exec);
+            g_graphs.erase(g_graphs.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+}
+
+}  // namespace galpic
+
+using namespace galpic;
+
+extern "C" {
+
+int pic_many_footprint(const pic_sim* sim, int capacity, size_t* bytes_out) {
+    if (!sim || !bytes_out) return fail(PIC_EINVAL, "sim or bytes_out is NULL");
+    if (capacity < 1 || capacity > 4096) return fail(PIC_EINVAL, "capacity must be in [1, 4096]");
+    const int C = pow2_at_least(capacity);
+    ManyPlan* mp = nullptr;
+    GP_CHECK(many_plan(sim, C, &mp));
+    *bytes_out = many_layout(sim, C, mp->work).total;
+    return PIC_OK;
+}
+
+int pic_step_many(pic_sim** sims, int nsims, int nsteps, void* workspace, size_t ws_bytes, void* stream) {
+    if (!sims || nsims < 1 || nsims > 4096) return fail(PIC_EINVAL, "pic_step_many: need 1 to 4096 sims");
+    if (nsteps < 0) return fail(PIC_EINVAL, "nsteps < 0");
+    if (!sims[0]) return fail(PIC_EINVAL, "sims[0] is NULL");
+    GP_CHECK(check_compatible(sims, nsims));
+    if (!workspace) return fail(PIC_EINVAL, "pic_step_many: workspace is NULL");
+    if ((uintptr_t)workspace % 256) return fail(PIC_EINVAL, "pic_step_many: workspace must be 256-byte aligned");
+    if (nsteps == 0) return PIC_OK;
+    pic_sim* s0 = sims[0];
+    const int C = pow2_at_least(nsims);
+    ManyPlan* mp = nullptr;
+    GP_CHECK(many_plan(s0, C, &mp));
+    const ManyLayout L = many_layout(s0, C, mp->work);
+    if (ws_bytes < L.total)
+        return fail(PIC_ENOMEM, "pic_step_many: workspace has " + std::to_string(ws_bytes) + " bytes, needs " +
+                                    std::to_string(L.total) + " (pic_many_footprint)");
+    char* ws = (char*)workspace;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t T = s0->cfg.precision == 64 ? 8 : 4;
+    const size_t N = (size_t)s0->d.N, M = (size_t)s0->d.M;
+
+    // parameter blocks and copy lists of this set of runs (written every call: another set
+    // may have used the workspace in between)
+    std::vector<char> host(L.desc_end, 0);
+    CopyDesc* cin = (CopyDesc*)(host.data() + L.copy_in);
+    CopyDesc* cout = (CopyDesc*)(host.data() + L.copy_out);
+    unsigned long long** cnts = (unsigned long long**)(host.data() + L.cnt_ptrs);
+    int* exps = (int*)(host.data() + L.exps);
+    for (int r = 0; r < nsims; ++r) {
+        pic_sim* s = sims[r];
+        char* F = ws + L.F + (size_t)r * 6 * N * T;
+        char* S = ws + L.S + (size_t)r * 4 * N * T;
+        long long* S64 = s0->cfg.deterministic ? (long long*)(ws + L.S64 + (size_t)r * 4 * N * 8) : nullptr;
+        char* Sh = ws + L.Sh + (size_t)r * 4 * M * 2 * T;
+        char* EBs = ws + L.EBs + (size_t)r * 6 * M * 2 * T;
+        if (s0->cfg.precision == 64)
+            fill_pass_desc_fp64(s, host.data() + L.pass_desc + (size_t)r * L.pass_bytes, F, S, S64);
+        else
+            fill_pass_desc_fp32(s, host.data() + L.pass_desc + (size_t)r * L.pass_bytes, F, S, S64);
+        fill_kspace_desc(s, host.data() + L.kspace_desc + (size_t)r * L.kspace_bytes, EBs, Sh);
+        for (int k = 0; k < s->nspecies; ++k)
+            fill_sort_desc(s, k, host.data() + L.sort_desc + ((size_t)k * C + r) * L.sort_bytes);
+        cnts[r] = s->cnt;
+        exps[r] = s->fix_exp;
+        cin[r] = CopyDesc{F, s->F, 6 * N * T};
+        cout[3 * r + 0] = CopyDesc{s->F, F, 6 * N * T};
+        cout[3 * r + 1] = CopyDesc{s->S, S, 4 * N * T};
+        cout[3 * r + 2] = CopyDesc{s->Sh, Sh, 4 * M * 2 * T};
+    }
+    // pageable source: the copy is staged before the call returns
+    GP_CUDA(cudaMemcpyAsync(ws, host.data(), L.desc_end, cudaMemcpyHostToDevice, st));
+    GP_CHECK(launch_copy_many((const CopyDesc*)(ws + L.copy_in), nsims, 6 * N * T, st));
+
+    std::vector<pic_sim*> key(sims, sims + nsims);
+    const std::vector<int> var = variants_of(sims, nsims);
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        for (auto& g : g_graphs)
+            if (g.ws == workspace && g.C == C && g.sims == key && g.variant == var) {
+                exec = g.exec;
+                kernels = g.kernels;
+                break;
+            }
+    }
+    if (!exec) {
+        ManyGraph g;
+        GP_CHECK(capture_many(sims, nsims, C, ws, L, mp, g));
+        g.ws = workspace;
+        g.C = C;
+        g.sims = key;
+        g.variant = var;
+        exec = g.exec;
+        kernels = g.kernels;
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        if (g_graphs.size() >= MAX_GRAPHS) {
+            cudaGraphExecDestroy(g_graphs.front().exec);
+            g_graphs.erase(g_graphs.begin());
+        }
+        g_graphs.push_back(std::move(g));
+    }
+    for (int i = 0; i < nsteps; ++i) GP_CUDA(cudaGraphLaunch(exec, st));
+    GP_CHECK(launch_copy_many((const CopyDesc*)(ws + L.copy_out), 3 * nsims, 6 * N * T, st));
+    for (int r = 0; r < nsims; ++r) sims[r]->steps += nsteps;
+    // shared launches are counted once, on the first run of the call
+    s0->launches += (int64_t)nsteps * kernels + 2;
+    return PIC_OK;
+}
+
+}  // extern "C"

@@ -10,6 +10,7 @@
 #pragma once
 
 #include <math.h>
+#include <string.h>
 
 #include "common.cuh"
 
@@ -220,16 +221,18 @@ struct RowStage {
 };
 
 // Deposit strategies: grouped by cell, J and rho in separate group passes (all
-// passes; linear passes always combine them), by stencil row (FP32, NW = 4), or grouped
-// by cell with J and rho in one group pass (FP32, NW = 4).
-enum { DEP_GROUP = 0, DEP_ROW = 1, DEP_JR = 2 };
+// passes; linear passes always combine them), by stencil row (FP32, NW = 4), grouped
+// by cell with J and rho in one group pass (FP32, NW = 4), or grouped by cell in 64-bit
+// fixed point (deterministic mode, all shapes and precisions).
+enum { DEP_GROUP = 0, DEP_ROW = 1, DEP_JR = 2, DEP_ROWU = 3, DEP_CELL = 4, DEP_FIXED = 8 };
 
 // Rows of the grouped staging area: velocity, x, y, z weights; the combined J and rho
 // pass adds a flag row and the x^{n+1} weights.
 __host__ __device__ constexpr int stage_rows(int NW, bool jr) { return jr ? 4 + 6 * NW : 3 + 3 * NW; }
 
 __host__ __device__ constexpr size_t stage_bytes(int NW, size_t T, int dep) {
-    return (T == 4 && NW == 4 && dep == DEP_ROW)
+    return dep == DEP_CELL ? 0
+           : (T == 4 && NW == 4 && (dep == DEP_ROW || dep == DEP_ROWU))
                ? RowStage::BYTES
                : align16((size_t)stage_rows(NW, NW == 2 || dep == DEP_JR) * 34 * T);
 }
@@ -241,7 +244,8 @@ struct PassSmem {
         size_t tb = step ? (T == 4 ? FieldTile<float>::bytes_per_node : FieldTile<double>::bytes_per_node) : 0;
         tile = 0;
         dep = align16(tb * (size_t)R);
-        stage = align16(dep + 4 * (size_t)R * T);
+        // the deposit tile holds four components per node, 64-bit integers in fixed point
+        stage = align16(dep + 4 * (size_t)R * (strategy == DEP_FIXED ? 8 : T));
         total = align16(stage + (size_t)PASS_WARPS * stage_bytes(NW, T, strategy));
     }
 };
@@ -261,6 +265,7 @@ struct SpeciesK {
     T* off[3];
     T* u[3];
     const int32_t* bin_start;
+    const int32_t* cell_start;   // first particle of each cell key (bin-major) as of the last sort
     T qw_dv;   // q w / dV
     T qdt2m;   // q dt / (2 m)
 };
@@ -269,6 +274,8 @@ template <typename T>
 struct PassK {
     const T* F;     // real E (3N) then B (3N)
     T* S;           // real Jx, Jy, Jz, rho (4N)
+    long long* S64;   // deterministic mode: the same sources in fixed point (units of delta)
+    T inv_delta;      // deterministic mode: 1/delta = 2^-e, a power of two
     int64_t N;
     int nx, ny, nz;
     FastDiv div_nynz, div_nz;
@@ -386,6 +393,43 @@ __device__ __forceinline__ void smem_add_batch(T* const (&addr)[K], const T (&va
             const U prev = atomicCAS(reinterpret_cast<U*>(addr[k]), old[k], as_bits(from_bits(old[k]) + val[k]));
             done[k] = prev == old[k];
             old[k] = prev;
+        }
+    }
+}
+
+// ---- deterministic mode: 64-bit fixed point ---------------------------------
+// A deposited value x (already multiplied by 1/delta) becomes the integer nearest to
+// it; integer additions are associative, so the sums below do not depend on the
+// order of members, groups, warps or CTAs. The weight product is formed in one order,
+// wx * (wy * wz) * value, on the tile path and on the out-of-tile path alike, so a
+// particle contributes the same integers whichever path it takes.
+template <typename T> __device__ __forceinline__ long long to_fixed(T x);
+template <> __device__ __forceinline__ long long to_fixed<float>(float x) { return __float2ll_rn(x); }
+template <> __device__ __forceinline__ long long to_fixed<double>(double x) { return __double2ll_rn(x); }
+
+template <typename T>
+__device__ __forceinline__ long long fixed_contrib(T wx, T wy, T wz, T v) {
+    return to_fixed<T>(wx * (wy * wz) * v);
+}
+
+__device__ __forceinline__ void add_fixed(long long* p, long long v) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+}
+
+// Out-of-tile deposit in fixed point: Q values (already scaled by q w/(dV delta)) at
+// one particle's stencil, straight into the global integer grids.
+template <typename T, int NW, int J0>
+__device__ void deposit_global_fixed(const PassK<T>& p, int ix, int iy, int iz, const T* wx, const T* wy,
+                                     const T* wz, int q0, int Q, const T* val) {
+#pragma unroll 1
+    for (int n = 0; n < NW * NW * NW; ++n) {
+        const int a = n / (NW * NW), b = (n / NW) % NW, c = n % NW;
+        const T xa = pick<T, NW>(wx, a), yb = pick<T, NW>(wy, b), zc = pick<T, NW>(wz, c);
+        const int64_t g = ((int64_t)wrapi(ix + J0 + a, p.nx) * p.ny + wrapi(iy + J0 + b, p.ny)) * p.nz +
+                          wrapi(iz + J0 + c, p.nz);
+        for (int q = 0; q < Q; ++q) {
+            const long long v = fixed_contrib<T>(xa, yb, zc, val[q]);
+            if (v) add_fixed(p.S64 + (int64_t)(q0 + q) * p.N + g, v);
         }
     }
 }
@@ -520,6 +564,71 @@ __device__ void group_deposit(T* sD, const Stage<T, NW>& stg, bool member, int k
                 T* addr[1] = {&sD[(q0 + q) * R + gkey + (ax * TE + by) * TE + cz]};
                 const T val[1] = {(A.x + A.y) * qw};
                 smem_add_batch<T, 1>(addr, val);
+            }
+        }
+    }
+}
+
+// Grouped deposit of one warp in fixed point (deterministic mode), for every shape and
+// precision. Roles as in group_deposit; the staged value rows hold the members' values
+// already multiplied by q w/(dV delta) (J: rows 0..2 = that times v; rho: row 0). Each
+// member's contribution is rounded to an integer before it is summed, and each role's
+// integer sum is added to the integer tile. Every lane of the warp must call this.
+template <typename T, int NW, int Q, int TE>
+__device__ void group_deposit_fixed(long long* sD, const Stage<T, NW>& stg, bool member, int key, int lane) {
+    constexpr int q0 = (Q == 3) ? 0 : 3;
+    constexpr int R = TE * TE * TE;
+    unsigned pending = __ballot_sync(0xffffffffu, member);
+    while (pending) {
+        const int leader = __ffs(pending) - 1;
+        const int gkey = __shfl_sync(0xffffffffu, key, leader);
+        const unsigned grp = __ballot_sync(0xffffffffu, member && key == gkey);
+        pending &= ~grp;
+        if (NW == 4) {
+            // lane -> y-z node (b, c) = (bc >> 2, bc & 3), bc = lane & 15, and x nodes h, h + 2
+            const int bc = lane & 15, h = lane >> 4, b = bc >> 2, c = bc & 3;
+            const T* xh = stg.xrow(h);
+            const T* xh2 = stg.xrow(h + 2);
+            const T* yb = stg.yrow(b);
+            const T* zc = stg.zrow(c);
+            long long A[Q], A2[Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) A[q] = A2[q] = 0;
+            unsigned g = grp;
+            while (g) {
+                const int m = __ffs(g) - 1;
+                g &= g - 1;
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const T v = stg.vrow(Q == 3 ? q : 0)[m];
+                    A[q] += fixed_contrib<T>(xh[m], yb[m], zc[m], v);
+                    A2[q] += fixed_contrib<T>(xh2[m], yb[m], zc[m], v);
+                }
+            }
+            const int n0 = gkey + (h * TE + b) * TE + c;
+            const int n1 = n0 + 2 * TE * TE;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                if (A[q]) add_fixed(&sD[(q0 + q) * R + n0], A[q]);
+                if (A2[q]) add_fixed(&sD[(q0 + q) * R + n1], A2[q]);
+            }
+        } else {
+            // NW == 2: lane -> (component q = lane / 8, node j = lane % 8)
+            if (lane < 8 * Q) {
+                const int q = lane >> 3, j = lane & 7;
+                const int ax = j >> 2, by = (j >> 1) & 1, cz = j & 1;
+                const T* xa = stg.xrow(ax);
+                const T* yb = stg.yrow(by);
+                const T* zc = stg.zrow(cz);
+                const T* vq = stg.vrow(Q == 3 ? q : 0);
+                long long A = 0;
+                unsigned g = grp;
+                while (g) {
+                    const int m = __ffs(g) - 1;
+                    g &= g - 1;
+                    A += fixed_contrib<T>(xa[m], yb[m], zc[m], vq[m]);
+                }
+                if (A) add_fixed(&sD[(q0 + q) * R + gkey + (ax * TE + by) * TE + cz], A);
             }
         }
     }
@@ -820,8 +929,108 @@ __device__ void row_deposit(float* sD, const float* stg, bool mJ, int rowJ, int 
     }
 }
 
+// Row deposit with the z starts unrolled (FP32, NW = 4, tile extent TE): the same
+// grouping and lane roles as row_deposit, but the row's nodes are register pairs
+// acc[0 .. TE-1] indexed at compile time. For each stencil start j (unrolled) the
+// members whose J and rho both start at (row, j) add into acc[j .. j+3]; the touched
+// nodes are then added to the shared tile once each. Members whose J and rho start at
+// different nodes (or only one of them in this row) add their parts straight to the
+// shared tile by compare-and-swap (rare: a particle crossing a cell boundary between
+// x^{n+1/2} and x^{n+1}). Every lane of the warp must call this.
+template <int TE>
+__device__ void row_deposit_unrolled(float* sD, const float* stg, bool mJ, int rowJ, int zJ, bool mR, int rowR,
+                                     int zR, int lane) {
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int R = TE * TE * TE;
+    constexpr int M = RowStage::MEMBER;
+    constexpr int J = TE - 3;   // stencil starts 0 .. TE-4
+    const int h = lane >> 4, a = (lane >> 2) & 3, b = lane & 3;
+    const bool hi = h != 0;
+    const float* sx = stg + RowStage::XV + 8 * h + 2 * a;
+    const float* sy = stg + RowStage::Y + 8 * h + 2 * b;
+    const float* sz = stg + RowStage::Z + 8 * h;
+    unsigned pendJ = __ballot_sync(FULL, mJ), pendR = __ballot_sync(FULL, mR);
+    while (pendJ | pendR) {
+        const int leader = __ffs(pendJ ? pendJ : pendR) - 1;
+        const int cur = __shfl_sync(FULL, pendJ ? rowJ : rowR, leader);
+        const bool inJ = mJ && rowJ == cur, inR = mR && rowR == cur;
+        const unsigned gJ = __ballot_sync(FULL, inJ), gR = __ballot_sync(FULL, inR);
+        pendJ &= ~gJ;
+        pendR &= ~gR;
+        const bool both = inJ && inR && zJ == zR;
+        const unsigned gB = __ballot_sync(FULL, both);
+        const int node0 = (cur + a * TE + b) * TE;
+        float* const p0 = sD + (2 * h) * R + node0;
+        float* const p1 = sD + (2 * h + 1) * R + node0;
+        float2 acc[TE];
+#pragma unroll
+        for (int j = 0; j < TE; ++j) acc[j] = make_float2(0.f, 0.f);
+        unsigned touched = 0u;
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const unsigned mm = __ballot_sync(FULL, both && zJ == j);
+            if (!mm) continue;   // warp-uniform
+            touched |= 0xfu << j;
+            const int lo = __ffs(mm) - 1, len = __popc(mm);
+            auto add = [&](int m) {
+                const float2 c = pmul(ld2(sx + m * M), ld2(sy + m * M));
+                const float4 z01 = *reinterpret_cast<const float4*>(sz + m * M);
+                const float4 z23 = *reinterpret_cast<const float4*>(sz + m * M + 4);
+                acc[j] = pfma(c, make_float2(z01.x, z01.y), acc[j]);
+                acc[j + 1] = pfma(c, make_float2(z01.z, z01.w), acc[j + 1]);
+                acc[j + 2] = pfma(c, make_float2(z23.x, z23.y), acc[j + 2]);
+                acc[j + 3] = pfma(c, make_float2(z23.z, z23.w), acc[j + 3]);
+            };
+            if ((mm >> lo) == (len == 32 ? FULL : ((1u << len) - 1u))) {   // one run of lanes
+#pragma unroll 1
+                for (int m = lo; m < lo + len; ++m) add(m);
+            } else {
+                unsigned g = mm;
+#pragma unroll 1
+                while (g) {
+                    const int m = __ffs(g) - 1;
+                    g &= g - 1;
+                    add(m);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < TE; ++j) {
+            if ((touched >> j) & 1u) {   // warp-uniform
+                atomicAdd(p0 + j, acc[j].x);
+                atomicAdd(p1 + j, acc[j].y);
+            }
+        }
+        // members whose J and rho parts do not start together in this row
+        unsigned rest = (gJ | gR) & ~gB;
+        while (rest) {
+            const int k = __ffs(rest) - 1;
+            rest &= rest - 1;
+            const int kzJ = __shfl_sync(FULL, zJ, k), kzR = __shfl_sync(FULL, zR, k);
+            const bool kJ = (gJ >> k) & 1u, kR = (gR >> k) & 1u;
+            const float2 ck = pmul(ld2(sx + k * M), ld2(sy + k * M));
+            const float4 z01 = *reinterpret_cast<const float4*>(sz + k * M);
+            const float4 z23 = *reinterpret_cast<const float4*>(sz + k * M + 4);
+            const float zc[8] = {z01.x, z01.y, z01.z, z01.w, z23.x, z23.y, z23.z, z23.w};
+            // J part (both components of h = 0; the first of h = 1) at kzJ
+            if (kJ) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    atomicAdd(p0 + kzJ + c, ck.x * zc[2 * c]);
+                    if (!hi) atomicAdd(p1 + kzJ + c, ck.y * zc[2 * c + 1]);
+                }
+            }
+            // rho part (the second component of h = 1) at kzR
+            if (kR && hi) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) atomicAdd(p1 + kzR + c, ck.y * zc[2 * c + 1]);
+            }
+        }
+    }
+}
+
 template <typename T, int ORDER, int MODE, int MARGIN, int DEP, bool MIX>
-__device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
+__device__ __forceinline__ void particle_pass_body(const PassK<T>& p, const int b) {
     typedef Shape<ORDER> SH;
     typedef typename Pair<T>::type P2;
     constexpr int NW = SH::NW;
@@ -829,19 +1038,22 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
     constexpr int R = TileGeom<NW, MARGIN>::R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const PassSmem L(R, NW, sizeof(T), MODE == PASS_STEP, DEP);
-    static_assert(DEP == DEP_GROUP || (sizeof(T) == 4 && NW == 4), "row deposit: FP32, NW = 4 only");
+    static_assert(DEP == DEP_GROUP || DEP == DEP_FIXED || (sizeof(T) == 4 && NW == 4),
+                  "row deposit: FP32, NW = 4 only");
     static_assert(!MIX || (NW == 4 && (DEP == DEP_GROUP || DEP == DEP_JR)),
                   "mixed-species groups: NW = 4, grouped deposits");
     static_assert(DEP != DEP_JR || (sizeof(T) == 4 && NW == 4), "combined J and rho groups: FP32, NW = 4 only");
+    static_assert(DEP != DEP_FIXED || !MIX, "fixed-point deposit: one species at a time");
+    constexpr bool FIX = DEP == DEP_FIXED;
     FieldTile<T> tile;
     tile.init(smem_raw + L.tile, R);
     T* sD = reinterpret_cast<T*>(smem_raw + L.dep);
+    long long* const sD64 = reinterpret_cast<long long*>(smem_raw + L.dep);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     Stage<T, NW> stg;
     stg.base = reinterpret_cast<T*>(smem_raw + L.stage + warp * stage_bytes(NW, sizeof(T), DEP));
     float* const rstg = reinterpret_cast<float*>(stg.base);
 
-    const int b = blockIdx.x;
     const int bz = b % p.nbz, by = (b / p.nbz) % p.nby, bx = b / (p.nbz * p.nby);
     const int x0 = bx * BIN, y0 = by * BIN, z0 = bz * BIN;
     // global node of tile index 0 along each axis
@@ -862,7 +1074,12 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
             tile.store(idx, v);
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) sD[q * R + idx] = (T)0;
+        for (int q = 0; q < 4; ++q) {
+            if constexpr (FIX)
+                sD64[q * R + idx] = 0;
+            else
+                sD[q * R + idx] = (T)0;
+        }
     }
     __syncthreads();
 
@@ -929,13 +1146,15 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
                         P2 wzp[NW];
 #pragma unroll
                         for (int cc = 0; cc < NW; ++cc) wzp[cc] = Pair<T>::make(wz[cc], wz[cc]);
+                        // one runtime base index; every node is a compile-time offset from it
+                        const int base0 = (rx * TE + ry) * TE + rz;
 #pragma unroll
                         for (int a = 0; a < NW; ++a)
 #pragma unroll
                             for (int bb = 0; bb < NW; ++bb) {
                                 const T wxy = wx[a] * wy[bb];
                                 const P2 wxyp = Pair<T>::make(wxy, wxy);
-                                const int base_t = ((rx + a) * TE + (ry + bb)) * TE + rz;
+                                const int base_t = base0 + (a * TE + bb) * TE;
 #pragma unroll
                                 for (int cc = 0; cc < NW; ++cc) {
                                     const P2 w2 = pmul(wxyp, wzp[cc]);
@@ -998,7 +1217,7 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
             }
             // ---- deposit J (phase 0: at x^{n+1/2} with v^{n+1/2}) and rho (phase 1:
             // at x^{n+1}); DEPOSIT mode: both at the current x
-            if constexpr (NW == 2 || DEP == DEP_JR) {
+            if constexpr (!FIX && (NW == 2 || DEP == DEP_JR)) {
                 // both stencils first, then one combined J and rho group pass
                 // (group_deposit_jr / group_deposit_jr4)
                 bool mJ = false, mR = false, same = false;
@@ -1075,7 +1294,7 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
                     group_deposit<T, NW, 1, TE, MIX>(sD, stg, restR, keyR, lane, MIX ? (T)1 : sp.qw_dv);
                     __syncwarp();
                 }
-            } else if constexpr (DEP == DEP_ROW) {
+            } else if constexpr (DEP == DEP_ROW || DEP == DEP_ROWU) {
                 // few particles per cell: both stencils first, then one pass by stencil row
                 bool mJ = false, mR = false;
                 int rowJ = 0, zJ = 0, rowR = 0, zR = 0;
@@ -1128,7 +1347,10 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
                                    (float)qvx, (float)qvy, (float)qvz, (float)sp.qw_dv);
                 }
                 __syncwarp();
-                row_deposit<TE>(reinterpret_cast<float*>(sD), rstg, mJ, rowJ, zJ, mR, rowR, zR, lane);
+                if constexpr (DEP == DEP_ROWU)
+                    row_deposit_unrolled<TE>(reinterpret_cast<float*>(sD), rstg, mJ, rowJ, zJ, mR, rowR, zR, lane);
+                else
+                    row_deposit<TE>(reinterpret_cast<float*>(sD), rstg, mJ, rowJ, zJ, mR, rowR, zR, lane);
                 __syncwarp();
             } else
 #pragma unroll
@@ -1155,10 +1377,23 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
                         val[0] = sp.qw_dv;
                         val[1] = val[2] = (T)0;
                     }
+                    if constexpr (FIX) {   // values carry q w / (dV delta)
+                        const T qs = sp.qw_dv * p.inv_delta;
+                        if (phase == 0) {
+                            val[0] = qs * vx;
+                            val[1] = qs * vy;
+                            val[2] = qs * vz;
+                        } else {
+                            val[0] = qs;
+                        }
+                    }
                     if (in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz)) {
                         member = true;
                         key = (rx * TE + ry) * TE + rz;
-                        if constexpr (MIX) {   // values carry q w / dV (members of both species)
+                        if constexpr (FIX) {
+                            stage_record<T, NW>(stg, lane, wx, wy, wz, phase == 0 ? val : nullptr);
+                            if (phase == 1) stg.vrow(0)[lane] = val[0];
+                        } else if constexpr (MIX) {   // values carry q w / dV (members of both species)
                             const T qvel[3] = {sp.qw_dv * vx, sp.qw_dv * vy, sp.qw_dv * vz};
                             stage_record<T, NW>(stg, lane, wx, wy, wz, phase == 0 ? qvel : nullptr);
                             if (phase == 1) stg.vrow(0)[lane] = sp.qw_dv;
@@ -1168,17 +1403,31 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
                         }
                     } else {
                         if (phase == 1) far++;
-                        if (phase == 0)
-                            deposit_global<T, NW, SH::J0>(p, ix, iy, iz, wx, wy, wz, 0, 3, val);
-                        else
-                            deposit_global<T, NW, SH::J0>(p, ix, iy, iz, wx, wy, wz, 3, 1, val);
+                        if constexpr (FIX) {
+                            if (phase == 0)
+                                deposit_global_fixed<T, NW, SH::J0>(p, ix, iy, iz, wx, wy, wz, 0, 3, val);
+                            else
+                                deposit_global_fixed<T, NW, SH::J0>(p, ix, iy, iz, wx, wy, wz, 3, 1, val);
+                        } else {
+                            if (phase == 0)
+                                deposit_global<T, NW, SH::J0>(p, ix, iy, iz, wx, wy, wz, 0, 3, val);
+                            else
+                                deposit_global<T, NW, SH::J0>(p, ix, iy, iz, wx, wy, wz, 3, 1, val);
+                        }
                     }
                 }
                 __syncwarp();
-                if (phase == 0)
-                    group_deposit<T, NW, 3, TE, MIX>(sD, stg, member, key, lane, MIX ? (T)1 : sp.qw_dv);
-                else
-                    group_deposit<T, NW, 1, TE, MIX>(sD, stg, member, key, lane, MIX ? (T)1 : sp.qw_dv);
+                if constexpr (FIX) {
+                    if (phase == 0)
+                        group_deposit_fixed<T, NW, 3, TE>(sD64, stg, member, key, lane);
+                    else
+                        group_deposit_fixed<T, NW, 1, TE>(sD64, stg, member, key, lane);
+                } else {
+                    if (phase == 0)
+                        group_deposit<T, NW, 3, TE, MIX>(sD, stg, member, key, lane, MIX ? (T)1 : sp.qw_dv);
+                    else
+                        group_deposit<T, NW, 1, TE, MIX>(sD, stg, member, key, lane, MIX ? (T)1 : sp.qw_dv);
+                }
                 __syncwarp();
             }
             if (valid && MODE == PASS_STEP) {
@@ -1206,8 +1455,13 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
                     wrap_near(oz + rz, p.nz);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            T v = sD[q * R + idx];
-            if (v != (T)0) atomicAdd(&p.S[q * N + g], v);
+            if constexpr (FIX) {
+                const long long v = sD64[q * R + idx];
+                if (v) add_fixed(p.S64 + q * N + g, v);
+            } else {
+                T v = sD[q * R + idx];
+                if (v != (T)0) atomicAdd(&p.S[q * N + g], v);
+            }
         }
     }
 
@@ -1223,31 +1477,336 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p) {
     }
 }
 
+// ---- linear shapes: one thread per cell -----------------------------------------
+// Particles are sorted by cell (cell_start ranges of the last sort). A thread takes one
+// cell of the bin and walks that cell's particles of every species. A particle still in
+// the cell gathers E, B from the cell's eight tile nodes (compile-time offsets from one
+// base), and its J^{n+1/2} and rho^{n+1}, when their stencils still start at the cell,
+// add into 32 register accumulators (8 nodes x Jx, Jy, Jz, rho) that go to the shared
+// tile once per cell. A particle that has left the cell since the sort, or whose J or
+// rho stencil starts elsewhere, uses the tile at its own position (per-node shared
+// atomics) or, outside the tile, global memory.
+constexpr int CELL_THREADS = 256;
+
+// 2x2x2 gather from the tile at base index `base` (node (a, b, c) at base + (a TE + b) TE + c).
+template <typename T, int TE>
+__device__ __forceinline__ void gather2(const FieldTile<T>& tile, int base, const T* wx, const T* wy,
+                                        const T* wz, T* E, T* B) {
+    typedef typename Pair<T>::type P2;
+    P2 a0 = Pair<T>::make(0, 0), a1 = a0, a2 = a0;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const T wxy = wx[a] * wy[b];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const T w = wxy * wz[c];
+                const P2 w2 = Pair<T>::make(w, w);
+                P2 f0, f1, f2;
+                tile.load(base + (a * TE + b) * TE + c, f0, f1, f2);
+                a0 = pfma(w2, f0, a0);
+                a1 = pfma(w2, f1, a1);
+                a2 = pfma(w2, f2, a2);
+            }
+        }
+    E[0] = a0.x; E[1] = a0.y; E[2] = a1.x;
+    B[0] = a1.y; B[1] = a2.x; B[2] = a2.y;
+}
+
+// Per-node shared-memory atomics of Q values at a 2x2x2 stencil in the tile.
+template <typename T, int TE>
+__device__ __forceinline__ void tile_atomic2(T* sD, int base, const T* wx, const T* wy, const T* wz, int q0,
+                                             int Q, const T* val) {
+    constexpr int R = TE * TE * TE;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const T w = wx[a] * wy[b] * wz[c];
+                const int idx = base + (a * TE + b) * TE + c;
+                for (int q = 0; q < Q; ++q) atomicAdd(&sD[(q0 + q) * R + idx], w * val[q]);
+            }
+}
+
+// Tile coordinate of cell i along an axis whose bin starts at o (tile node 0 = o - MARGIN):
+// the periodic image of i nearest to the bin, so that a particle that crossed the
+// periodic boundary next to the bin still finds its nodes in the tile.
+__device__ __forceinline__ int tile_coord(int i, int o, int n, int margin) {
+    int d = i - o;
+    if (2 * d > n) d -= n;
+    else if (2 * d < -n) d += n;
+    return d + margin;
+}
+
+template <typename T, int MODE, int MARGIN>
+__device__ __forceinline__ void cell_pass_body(const PassK<T>& p, const int b) {
+    typedef typename Pair<T>::type P2;
+    typedef Shape<1> SH;
+    constexpr int NW = 2;
+    constexpr int TE = TileGeom<NW, MARGIN>::E;
+    constexpr int R = TileGeom<NW, MARGIN>::R;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const PassSmem L(R, NW, sizeof(T), MODE == PASS_STEP, DEP_CELL);
+    FieldTile<T> tile;
+    tile.init(smem_raw + L.tile, R);
+    T* sD = reinterpret_cast<T*>(smem_raw + L.dep);
+    const int lane = threadIdx.x & 31;
+    const int bz = b % p.nbz, by = (b / p.nbz) % p.nby, bx = b / (p.nbz * p.nby);
+    const int x0 = bx * BIN, y0 = by * BIN, z0 = bz * BIN;
+    const int ox = x0 - MARGIN, oy = y0 - MARGIN, oz = z0 - MARGIN;
+    const int64_t N = p.N;
+    for (int idx = threadIdx.x; idx < R; idx += blockDim.x) {
+        const int rx = idx / (TE * TE);
+        const int rem = idx - rx * (TE * TE);
+        const int ry = rem / TE;
+        const int rz = rem - ry * TE;
+        if (MODE == PASS_STEP) {
+            int64_t g = ((int64_t)wrap_near(ox + rx, p.nx) * p.ny + wrap_near(oy + ry, p.ny)) * p.nz +
+                        wrap_near(oz + rz, p.nz);
+            T v[6];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) v[q] = p.F[q * N + g];
+            tile.store(idx, v);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sD[q * R + idx] = (T)0;
+    }
+    __syncthreads();
+
+    unsigned long long miss = 0, far = 0;
+    for (int lc = threadIdx.x; lc < BIN * BIN * BIN; lc += CELL_THREADS) {
+        const int lx = lc >> 6, ly = (lc >> 3) & 7, lz = lc & 7;
+        const int hx = x0 + lx, hy = y0 + ly, hz = z0 + lz;
+        const int key = b * (BIN * BIN * BIN) + lc;
+        // cells past the grid's edge in a partial bin hold no particles (empty ranges)
+        const int home = (hx * p.ny + hy) * p.nz + hz;
+        const int hrx = lx + MARGIN, hry = ly + MARGIN, hrz = lz + MARGIN;
+        const int hbase = (hrx * TE + hry) * TE + hrz;
+        P2 aJ[8];
+        T aZ[8], aR[8];
+#pragma unroll
+        for (int n = 0; n < 8; ++n) {
+            aJ[n] = Pair<T>::make(0, 0);
+            aZ[n] = aR[n] = (T)0;
+        }
+        for (int s = 0; s < p.nspecies; ++s) {
+            const SpeciesK<T>& sp = p.sp[s];
+            const int beg = sp.cell_start[key], end = sp.cell_start[key + 1];
+            for (int i = beg; i < end; ++i) {
+                const int c = sp.cell[i];
+                T fx = sp.off[0][i], fy = sp.off[1][i], fz = sp.off[2][i];
+                T ux = sp.u[0][i], uy = sp.u[1][i], uz = sp.u[2][i];
+                int ix = hx, iy = hy, iz = hz, rx = hrx, ry = hry, rz = hrz;
+                if (c != home) {   // moved since the sort
+                    ix = p.div_nynz.div(c);
+                    const int rem = c - ix * (p.ny * p.nz);
+                    iy = p.div_nz.div(rem);
+                    iz = rem - iy * p.nz;
+                    rx = tile_coord(ix, x0, p.nx, MARGIN);
+                    ry = tile_coord(iy, y0, p.ny, MARGIN);
+                    rz = tile_coord(iz, z0, p.nz, MARGIN);
+                }
+                T wx[2], wy[2], wz[2];
+                if (MODE == PASS_STEP) {
+                    // ---- gather E^n, B^n at x^n
+                    SH::w(fx, wx);
+                    SH::w(fy, wy);
+                    SH::w(fz, wz);
+                    T E[3], B[3];
+                    if (c == home) {
+                        gather2<T, TE>(tile, hbase, wx, wy, wz, E, B);
+                    } else if (in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz)) {
+                        gather2<T, TE>(tile, (rx * TE + ry) * TE + rz, wx, wy, wz, E, B);
+                    } else {
+                        far++;
+                        for (int q = 0; q < 3; ++q) E[q] = B[q] = (T)0;
+#pragma unroll
+                        for (int a = 0; a < 2; ++a)
+#pragma unroll
+                            for (int bb = 0; bb < 2; ++bb) {
+                                const T wxy = wx[a] * wy[bb];
+                                const int64_t gb =
+                                    ((int64_t)wrapi(ix + a, p.nx) * p.ny + wrapi(iy + bb, p.ny)) * p.nz;
+#pragma unroll
+                                for (int cc = 0; cc < 2; ++cc) {
+                                    const T w = wxy * wz[cc];
+                                    const int64_t g = gb + wrapi(iz + cc, p.nz);
+                                    E[0] += w * p.F[0 * N + g];
+                                    E[1] += w * p.F[1 * N + g];
+                                    E[2] += w * p.F[2 * N + g];
+                                    B[0] += w * p.F[3 * N + g];
+                                    B[1] += w * p.F[4 * N + g];
+                                    B[2] += w * p.F[5 * N + g];
+                                }
+                            }
+                    }
+                    // ---- relativistic Boris push u^{n-1/2} -> u^{n+1/2}
+                    const T a = sp.qdt2m;
+                    const T umx = ux + a * E[0], umy = uy + a * E[1], umz = uz + a * E[2];
+                    const T igm = (T)1 / sqrt((T)1 + (umx * umx + umy * umy + umz * umz) * p.inv_c2);
+                    const T tx = a * B[0] * igm, ty = a * B[1] * igm, tz = a * B[2] * igm;
+                    const T s2 = (T)2 / ((T)1 + tx * tx + ty * ty + tz * tz);
+                    const T sx = s2 * tx, sy = s2 * ty, sz = s2 * tz;
+                    const T upx = umx + (umy * tz - umz * ty);
+                    const T upy = umy + (umz * tx - umx * tz);
+                    const T upz = umz + (umx * ty - umy * tx);
+                    ux = umx + (upy * sz - upz * sy) + a * E[0];
+                    uy = umy + (upz * sx - upx * sz) + a * E[1];
+                    uz = umz + (upx * sy - upy * sx) + a * E[2];
+                }
+                const T igam = (T)1 / sqrt((T)1 + (ux * ux + uy * uy + uz * uz) * p.inv_c2);
+                const T vx = ux * igam, vy = uy * igam, vz = uz * igam;
+                // ---- J^{n+1/2} at x^{n+1/2} with v^{n+1/2} (DEPOSIT mode: at x with v)
+                if (MODE == PASS_STEP) {
+                    rx += drift_axis(ix, fx, (vx - p.vgal[0]) * p.hd[0], p.nx);
+                    ry += drift_axis(iy, fy, (vy - p.vgal[1]) * p.hd[1], p.ny);
+                    rz += drift_axis(iz, fz, (vz - p.vgal[2]) * p.hd[2], p.nz);
+                    SH::w(fx, wx);
+                    SH::w(fy, wy);
+                    SH::w(fz, wz);
+                } else {
+                    SH::w(fx, wx);
+                    SH::w(fy, wy);
+                    SH::w(fz, wz);
+                }
+                const T qv[3] = {sp.qw_dv * vx, sp.qw_dv * vy, sp.qw_dv * vz};
+                if (rx == hrx && ry == hry && rz == hrz) {
+                    const P2 qxy = Pair<T>::make(qv[0], qv[1]);
+#pragma unroll
+                    for (int a = 0; a < 2; ++a)
+#pragma unroll
+                        for (int bb = 0; bb < 2; ++bb) {
+                            const T wxy = wx[a] * wy[bb];
+#pragma unroll
+                            for (int cc = 0; cc < 2; ++cc) {
+                                const T w = wxy * wz[cc];
+                                const int n = (a * 2 + bb) * 2 + cc;
+                                aJ[n] = pfma(Pair<T>::make(w, w), qxy, aJ[n]);
+                                aZ[n] = fma(w, qv[2], aZ[n]);
+                            }
+                        }
+                } else if (in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz)) {
+                    tile_atomic2<T, TE>(sD, (rx * TE + ry) * TE + rz, wx, wy, wz, 0, 3, qv);
+                } else {
+                    deposit_global<T, NW, 0>(p, ix, iy, iz, wx, wy, wz, 0, 3, qv);
+                }
+                // ---- rho^{n+1} at x^{n+1} (DEPOSIT mode: at x)
+                if (MODE == PASS_STEP) {
+                    rx += drift_axis(ix, fx, (vx - p.vgal[0]) * p.hd[0], p.nx);
+                    ry += drift_axis(iy, fy, (vy - p.vgal[1]) * p.hd[1], p.ny);
+                    rz += drift_axis(iz, fz, (vz - p.vgal[2]) * p.hd[2], p.nz);
+                    SH::w(fx, wx);
+                    SH::w(fy, wy);
+                    SH::w(fz, wz);
+                }
+                const T qr[1] = {sp.qw_dv};
+                if (rx == hrx && ry == hry && rz == hrz) {
+#pragma unroll
+                    for (int a = 0; a < 2; ++a)
+#pragma unroll
+                        for (int bb = 0; bb < 2; ++bb) {
+                            const T wxy = wx[a] * wy[bb];
+#pragma unroll
+                            for (int cc = 0; cc < 2; ++cc)
+                                aR[(a * 2 + bb) * 2 + cc] = fma(wxy * wz[cc], qr[0], aR[(a * 2 + bb) * 2 + cc]);
+                        }
+                } else if (in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz)) {
+                    tile_atomic2<T, TE>(sD, (rx * TE + ry) * TE + rz, wx, wy, wz, 3, 1, qr);
+                } else {
+                    far++;
+                    deposit_global<T, NW, 0>(p, ix, iy, iz, wx, wy, wz, 3, 1, qr);
+                }
+                if (MODE == PASS_STEP) {
+                    sp.cell[i] = (ix * p.ny + iy) * p.nz + iz;
+                    sp.off[0][i] = fx;
+                    sp.off[1][i] = fy;
+                    sp.off[2][i] = fz;
+                    sp.u[0][i] = ux;
+                    sp.u[1][i] = uy;
+                    sp.u[2][i] = uz;
+                    if (ix < x0 || ix >= x0 + BIN || iy < y0 || iy >= y0 + BIN || iz < z0 || iz >= z0 + BIN)
+                        miss++;
+                }
+            }
+        }
+        // the cell's accumulated nodes, once (neighbouring lanes are neighbouring cells along
+        // z, so one node index per instruction never makes two lanes meet)
+#pragma unroll
+        for (int n = 0; n < 8; ++n) {
+            const int a = n >> 2, bb = (n >> 1) & 1, cc = n & 1;
+            const int idx = hbase + (a * TE + bb) * TE + cc;
+            if (aJ[n].x != (T)0) atomicAdd(&sD[0 * R + idx], aJ[n].x);
+            if (aJ[n].y != (T)0) atomicAdd(&sD[1 * R + idx], aJ[n].y);
+            if (aZ[n] != (T)0) atomicAdd(&sD[2 * R + idx], aZ[n]);
+            if (aR[n] != (T)0) atomicAdd(&sD[3 * R + idx], aR[n]);
+        }
+    }
+    __syncthreads();
+
+    // add the tile to the global source grids
+    for (int idx = threadIdx.x; idx < R; idx += blockDim.x) {
+        const int rx = idx / (TE * TE);
+        const int rem = idx - rx * (TE * TE);
+        const int ry = rem / TE;
+        const int rz = rem - ry * TE;
+        int64_t g = ((int64_t)wrap_near(ox + rx, p.nx) * p.ny + wrap_near(oy + ry, p.ny)) * p.nz +
+                    wrap_near(oz + rz, p.nz);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            T v = sD[q * R + idx];
+            if (v != (T)0) atomicAdd(&p.S[q * N + g], v);
+        }
+    }
+    if (MODE == PASS_STEP) {
+        for (int o = 16; o > 0; o >>= 1) {
+            miss += __shfl_down_sync(0xffffffffu, miss, o);
+            far += __shfl_down_sync(0xffffffffu, far, o);
+        }
+        if (lane == 0) {
+            if (miss) atomicAdd(&p.cnt[CNT_HOME_MISS], miss);
+            if (far) atomicAdd(&p.cnt[CNT_FAR], far);
+        }
+    }
+}
+
+template <typename T, int MODE, int MARGIN>
+__global__ void __launch_bounds__(CELL_THREADS, 2) cell_pass_kernel(PassK<T> p) {
+    cell_pass_body<T, MODE, MARGIN>(p, blockIdx.x);
+}
+
 // One CTA per bin. FP32 linear passes and FP32 grouped quadratic/cubic steps at tile
 // margin 0 fit three CTAs per SM by shared memory and have their registers held to
 // that; row-deposit and combined J and rho passes are held to two; the others are left
 // to the compiler.
 template <typename T, int ORDER, int MODE, int MARGIN, int DEP, bool MIX>
 __global__ void __launch_bounds__(PASS_THREADS) particle_pass_kernel(PassK<T> p) {
-    particle_pass_body<T, ORDER, MODE, MARGIN, DEP, MIX>(p);
+    particle_pass_body<T, ORDER, MODE, MARGIN, DEP, MIX>(p, blockIdx.x);
 }
 
 template <typename T, int ORDER, int MODE, int MARGIN, int DEP, bool MIX>
 __global__ void __launch_bounds__(PASS_THREADS, 3) particle_pass_kernel_3(PassK<T> p) {
-    particle_pass_body<T, ORDER, MODE, MARGIN, DEP, MIX>(p);
+    particle_pass_body<T, ORDER, MODE, MARGIN, DEP, MIX>(p, blockIdx.x);
 }
 
 template <typename T, int ORDER, int MODE, int MARGIN, int DEP, bool MIX>
 __global__ void __launch_bounds__(PASS_THREADS, 2) particle_pass_kernel_2(PassK<T> p) {
-    particle_pass_body<T, ORDER, MODE, MARGIN, DEP, MIX>(p);
+    particle_pass_body<T, ORDER, MODE, MARGIN, DEP, MIX>(p, blockIdx.x);
 }
 
-template <typename T, int ORDER, int MODE, int MARGIN, int DEP, bool MIX = false>
-int pass_launch(pic_sim* s, cudaStream_t st) {
+// Parameters of a run's particle pass. F, S and S64 default to the run's own grids;
+// shared launches over several runs point them at a staging area instead.
+template <typename T>
+void fill_passk(const pic_sim* s, PassK<T>& p, const void* F = nullptr, void* S = nullptr,
+                long long* S64 = nullptr) {
     const pic_config& c = s->cfg;
-    PassK<T> p;
-    p.F = (const T*)s->F;
-    p.S = (T*)s->S;
+    memset(&p, 0, sizeof(p));
+    p.F = (const T*)(F ? F : s->F);
+    p.S = (T*)(S ? S : s->S);
+    p.S64 = S64 ? S64 : s->S64;
+    p.inv_delta = (T)ldexp(1.0, -s->fix_exp);
     p.N = s->d.N;
     p.nx = s->d.nx;
     p.ny = s->d.ny;
@@ -1272,10 +1831,51 @@ int pass_launch(pic_sim* s, cudaStream_t st) {
             p.sp[k].u[d] = (T*)sp.u[d];
         }
         p.sp[k].bin_start = sp.bin_start;
+        p.sp[k].cell_start = sp.cell_start;
         p.sp[k].qw_dv = (T)(sp.q * sp.w / dV);
         p.sp[k].qdt2m = (T)(sp.q * c.dt / (2.0 * sp.m));
     }
     p.cnt = s->cnt;
+}
+
+// Shared launches over several runs of one shape class: one CTA per (run, bin), the run's
+// parameters copied from a table in device memory into shared memory first.
+template <typename T>
+__device__ __forceinline__ void load_passk(PassK<T>& dst, const PassK<T>* src) {
+    static_assert(sizeof(PassK<T>) % 4 == 0, "PassK is copied as 32-bit words");
+    const int* a = reinterpret_cast<const int*>(src);
+    int* d = reinterpret_cast<int*>(&dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(PassK<T>) / 4); i += blockDim.x) d[i] = a[i];
+}
+
+template <typename T, int ORDER, int MODE, int MARGIN, int DEP, bool MIX, int MINB>
+__global__ void __launch_bounds__(PASS_THREADS, MINB)
+    particle_pass_many_kernel(const PassK<T>* __restrict__ descs, int nbins) {
+    __shared__ __align__(16) PassK<T> P;
+    const int run = blockIdx.x / nbins;
+    load_passk(P, descs + run);
+    __syncthreads();
+    particle_pass_body<T, ORDER, MODE, MARGIN, DEP, MIX>(P, blockIdx.x - run * nbins);
+}
+
+template <typename T, int MODE, int MARGIN>
+__global__ void __launch_bounds__(CELL_THREADS, 2) cell_pass_many_kernel(const PassK<T>* __restrict__ descs,
+                                                                        int nbins) {
+    __shared__ __align__(16) PassK<T> P;
+    const int run = blockIdx.x / nbins;
+    load_passk(P, descs + run);
+    __syncthreads();
+    cell_pass_body<T, MODE, MARGIN>(P, blockIdx.x - run * nbins);
+}
+
+// A shared launch: `descs` (device) holds `nruns` parameter blocks.
+struct ManyLaunch {
+    const void* descs;
+    int nruns;
+};
+
+template <typename T, int ORDER, int MODE, int MARGIN, int DEP, bool MIX = false>
+int pass_launch(pic_sim* s, cudaStream_t st, const ManyLaunch* many) {
     const PassSmem L(TileGeom<Shape<ORDER>::NW, MARGIN>::R, Shape<ORDER>::NW, sizeof(T), MODE == PASS_STEP, DEP);
     // FP32 grouped quadratic/cubic steps at tile margin 0 (70 KB of shared memory) run
     // three CTAs per SM: registers held to 80 (a few spill) and the largest shared
@@ -1283,52 +1883,92 @@ int pass_launch(pic_sim* s, cudaStream_t st) {
     // cubic plasma.
     constexpr bool three = sizeof(T) == 4 && ORDER >= 2 && MARGIN == 0 && DEP == DEP_GROUP &&
                            MODE == PASS_STEP;
+    constexpr int MINB = (DEP == DEP_CELL) ? 2
+                         : (sizeof(T) == 4 && (ORDER == 1 || three) && DEP != DEP_FIXED) ? 3
+                         : (DEP == DEP_ROW || DEP == DEP_ROWU || DEP == DEP_JR) ? 2 : 1;
+    const int threads = DEP == DEP_CELL ? CELL_THREADS : PASS_THREADS;
+    if (many) {
+        void (*kern)(const PassK<T>*, int);
+        if constexpr (DEP == DEP_CELL)
+            kern = cell_pass_many_kernel<T, MODE, MARGIN>;
+        else
+            kern = particle_pass_many_kernel<T, ORDER, MODE, MARGIN, DEP, MIX, MINB>;
+        GP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+        if constexpr (three)
+            GP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        kern<<<(unsigned)s->d.nbins * (unsigned)many->nruns, threads, L.total, st>>>(
+            (const PassK<T>*)many->descs, s->d.nbins);
+        GP_CUDA(cudaGetLastError());
+        return PIC_OK;
+    }
+    PassK<T> p;
+    fill_passk<T>(s, p);
     void (*kern)(PassK<T>);
-    if constexpr (sizeof(T) == 4 && (ORDER == 1 || three))
+    if constexpr (DEP == DEP_CELL) {
+        static_assert(ORDER == 1, "one thread per cell: linear shapes only");
+        kern = cell_pass_kernel<T, MODE, MARGIN>;
+    } else if constexpr (MINB == 3)
         kern = particle_pass_kernel_3<T, ORDER, MODE, MARGIN, DEP, MIX>;
-    else if constexpr (DEP == DEP_ROW || DEP == DEP_JR)
+    else if constexpr (MINB == 2)
         kern = particle_pass_kernel_2<T, ORDER, MODE, MARGIN, DEP, MIX>;
     else
         kern = particle_pass_kernel<T, ORDER, MODE, MARGIN, DEP, MIX>;
     GP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
     if constexpr (three)
         GP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    kern<<<s->d.nbins, PASS_THREADS, L.total, st>>>(p);
+    kern<<<s->d.nbins, threads, L.total, st>>>(p);
     GP_CUDA(cudaGetLastError());
     return PIC_OK;
 }
 
+// Deposit variant a run's pass uses (strategy, and whether two equal species share groups):
+// runs advanced by one shared launch must agree on it.
+inline int pass_variant(const pic_sim* s) {
+    const bool mix = s->nspecies == 2 && s->sp[0].n == s->sp[1].n;
+    if (s->cfg.deterministic) return DEP_FIXED;
+    if (s->cfg.shape_order == 1) return s->cfg.deposit == DEP_CELL ? DEP_CELL : DEP_GROUP;
+    if (s->cfg.precision != 32) return DEP_GROUP;
+    if (s->cfg.deposit == DEP_ROW || s->cfg.deposit == DEP_ROWU) return s->cfg.deposit;
+    const int d = s->cfg.deposit == DEP_JR ? DEP_JR : DEP_GROUP;
+    return d + (mix ? 16 : 0);
+}
+
 template <typename T, int ORDER, int MODE, int MARGIN>
-int pass_strategy(pic_sim* s, cudaStream_t st) {
+int pass_strategy(pic_sim* s, cudaStream_t st, const ManyLaunch* many) {
+    if (s->cfg.deterministic) return pass_launch<T, ORDER, MODE, MARGIN, DEP_FIXED>(s, st, many);
     if constexpr (sizeof(T) == 4) {
-        if (s->cfg.deposit == DEP_ROW) return pass_launch<T, ORDER, MODE, MARGIN, DEP_ROW>(s, st);
+        if (s->cfg.deposit == DEP_ROW) return pass_launch<T, ORDER, MODE, MARGIN, DEP_ROW>(s, st, many);
+        if (s->cfg.deposit == DEP_ROWU) return pass_launch<T, ORDER, MODE, MARGIN, DEP_ROWU>(s, st, many);
         // two species of equal size (the neutral plasmas): one group per cell for both
         const bool mix = MODE == PASS_STEP && s->nspecies == 2 && s->sp[0].n == s->sp[1].n;
         if (s->cfg.deposit == DEP_JR) {
             if constexpr (MODE == PASS_STEP) {
-                if (mix) return pass_launch<T, ORDER, MODE, MARGIN, DEP_JR, true>(s, st);
-                return pass_launch<T, ORDER, MODE, MARGIN, DEP_JR>(s, st);
+                if (mix) return pass_launch<T, ORDER, MODE, MARGIN, DEP_JR, true>(s, st, many);
+                return pass_launch<T, ORDER, MODE, MARGIN, DEP_JR>(s, st, many);
             }
         }
         if constexpr (MODE == PASS_STEP) {
-            if (mix) return pass_launch<T, ORDER, MODE, MARGIN, DEP_GROUP, true>(s, st);
+            if (mix) return pass_launch<T, ORDER, MODE, MARGIN, DEP_GROUP, true>(s, st, many);
         }
     }
-    return pass_launch<T, ORDER, MODE, MARGIN, DEP_GROUP>(s, st);
+    return pass_launch<T, ORDER, MODE, MARGIN, DEP_GROUP>(s, st, many);
 }
 
 template <typename T, int MODE, int MARGIN>
-int pass_order(pic_sim* s, cudaStream_t st) {
+int pass_order(pic_sim* s, cudaStream_t st, const ManyLaunch* many) {
     switch (s->cfg.shape_order) {
-        case 1: return pass_launch<T, 1, MODE, MARGIN, DEP_GROUP>(s, st);
-        case 2: return pass_strategy<T, 2, MODE, MARGIN>(s, st);
-        default: return pass_strategy<T, 3, MODE, MARGIN>(s, st);
+        case 1:
+            if (s->cfg.deterministic) return pass_launch<T, 1, MODE, MARGIN, DEP_FIXED>(s, st, many);
+            if (s->cfg.deposit == DEP_CELL) return pass_launch<T, 1, MODE, MARGIN, DEP_CELL>(s, st, many);
+            return pass_launch<T, 1, MODE, MARGIN, DEP_GROUP>(s, st, many);
+        case 2: return pass_strategy<T, 2, MODE, MARGIN>(s, st, many);
+        default: return pass_strategy<T, 3, MODE, MARGIN>(s, st, many);
     }
 }
 
 template <typename T, int MODE>
-int pass_margin(pic_sim* s, cudaStream_t st) {
-    return s->d.margin == 0 ? pass_order<T, MODE, 0>(s, st) : pass_order<T, MODE, 1>(s, st);
+int pass_margin(pic_sim* s, cudaStream_t st, const ManyLaunch* many = nullptr) {
+    return s->d.margin == 0 ? pass_order<T, MODE, 0>(s, st, many) : pass_order<T, MODE, 1>(s, st, many);
 }
 
 }  // namespace

@@ -33,7 +33,8 @@ class PicConfig(ctypes.Structure):
                 ("beta_init", c_double * 3),
                 ("nx", c_int32), ("ny", c_int32), ("nz", c_int32), ("shape_order", c_int32),
                 ("precision", c_int32), ("current_correction", c_int32), ("init_fields", c_int32),
-                ("tile_margin", c_int32), ("deposit", c_int32), ("stencil_order", c_int32)]
+                ("tile_margin", c_int32), ("deposit", c_int32), ("stencil_order", c_int32),
+                ("deterministic", c_int32)]
 
 
 class PicSpecies(ctypes.Structure):
@@ -64,7 +65,8 @@ def _load():
         "pic_gather_push": (c_int, [P, P]),
         "pic_field_update": (c_int, [P, P]),
         "pic_step": (c_int, [P, c_int, P]),
-        "pic_step_many": (c_int, [POINTER(P), c_int, c_int, P]),
+        "pic_many_footprint": (c_int, [P, c_int, POINTER(c_size_t)]),
+        "pic_step_many": (c_int, [POINTER(P), c_int, c_int, P, c_size_t, P]),
         "pic_step_coupled": (c_int, [POINTER(P), c_int, c_int, P]),
         "pic_diag_energy": (c_int, [P, P, P]),
         "pic_get": (c_int, [P, c_int, P, c_size_t, P]),
@@ -94,7 +96,8 @@ lib = _load()
 
 # the exported names, as declared in include/galpic.h
 EXPORTS = ("pic_version", "pic_last_error", "pic_footprint", "pic_init", "pic_destroy", "pic_deposit",
-           "pic_gather_push", "pic_field_update", "pic_step", "pic_step_many", "pic_step_coupled", "pic_diag_energy",
+           "pic_gather_push", "pic_field_update", "pic_step", "pic_many_footprint", "pic_step_many",
+           "pic_step_coupled", "pic_diag_energy",
            "pic_get", "pic_set", "pic_get_particles", "pic_set_particles", "pic_status",
            "pic_counters", "pic_sizes", "pic_profile", "pic_profile_read", "pic_sort",
            "pic_field_energy_noalloc", "pic_add_fields", "pic_sort_policy", "pic_tune", "pic_get_line")
@@ -116,7 +119,7 @@ def _stream_ptr(stream: Optional[torch.cuda.Stream]) -> c_void_p:
 def make_config(nx: int, ny: int, nz: int, *, dx=1.0, dy=1.0, dz=1.0, dt=1.0, vgal=(0.0, 0.0, 0.0),
                 c=1.0, eps0=1.0, rho_bg=0.0, beta_init=(0.0, 0.0, 0.0), shape_order=1,
                 precision=32, current_correction=1, init_fields=1, tile_margin=1, deposit=0,
-                stencil_order=0) -> PicConfig:
+                stencil_order=0, deterministic=0) -> PicConfig:
     cfg = PicConfig()
     cfg.dx, cfg.dy, cfg.dz, cfg.dt = dx, dy, dz, dt
     cfg.vgal[:] = list(vgal)
@@ -128,6 +131,7 @@ def make_config(nx: int, ny: int, nz: int, *, dx=1.0, dy=1.0, dz=1.0, dt=1.0, vg
     cfg.tile_margin = tile_margin
     cfg.deposit = deposit
     cfg.stencil_order = stencil_order
+    cfg.deterministic = deterministic
     return cfg
 
 
@@ -325,9 +329,38 @@ def field_energy_noalloc(fields: torch.Tensor, n_cells: int, precision: int, eps
                                        c_void_p(out.data_ptr()), _stream_ptr(stream)))
 
 
-def step_many(sims: Sequence[Sim], nsteps: int, stream=None):
+def many_footprint(sim: Sim, capacity: int) -> int:
+    """Bytes of shared-launch workspace for up to `capacity` runs shaped like `sim`."""
+    n = c_size_t(0)
+    check(lib.pic_many_footprint(sim.handle, int(capacity), ctypes.byref(n)))
+    return int(n.value)
+
+
+class ManyWorkspace:
+    """Device workspace for pic_step_many (a torch uint8 tensor), grown on demand."""
+
+    def __init__(self, device="cuda"):
+        self.device = device
+        self.buf = None
+
+    def for_runs(self, sims: Sequence[Sim]) -> torch.Tensor:
+        need = many_footprint(sims[0], len(sims))
+        if self.buf is None or self.buf.numel() < need:
+            self.buf = None
+            self.buf = torch.empty(need, dtype=torch.uint8, device=self.device)
+        return self.buf
+
+
+def step_many(sims: Sequence[Sim], nsteps: int, workspace: Optional[torch.Tensor] = None, stream=None):
+    """pic_step_many: advance runs of one grid shape in shared launches. `workspace`: a device
+    uint8 tensor of at least many_footprint(sims[0], len(sims)) bytes (allocated here if None)."""
+    if workspace is None:
+        workspace = torch.empty(many_footprint(sims[0], len(sims)), dtype=torch.uint8,
+                                device=sims[0].device)
     arr = (c_void_p * len(sims))(*[s.handle for s in sims])
-    check(lib.pic_step_many(arr, len(sims), nsteps, _stream_ptr(stream)))
+    check(lib.pic_step_many(arr, len(sims), nsteps, c_void_p(workspace.data_ptr()),
+                            workspace.numel(), _stream_ptr(stream)))
+    return workspace
 
 
 def step_coupled(sims: Sequence[Sim], nsteps: int, stream=None):
@@ -338,7 +371,7 @@ def step_coupled(sims: Sequence[Sim], nsteps: int, stream=None):
 
 
 def sim_from_workload(wl, precision: Optional[int] = None, stream=None, device="cuda",
-                      tile_margin: int = 1, deposit: int = 0) -> Sim:
+                      tile_margin: int = 1, deposit: int = 0, deterministic: int = 0) -> Sim:
     """A run of a synthetic workload (duck-typed: grid, units, v_gal, species with
     q, m, ppc, u0, jitter, density), particles generated on the device."""
     prec = wl.precision if precision is None else precision
@@ -347,7 +380,8 @@ def sim_from_workload(wl, precision: Optional[int] = None, stream=None, device="
                       shape_order=wl.shape_order, precision=prec,
                       current_correction=wl.current_correction, init_fields=wl.init_fields,
                       tile_margin=tile_margin, deposit=deposit,
-                      stencil_order=getattr(wl, "stencil_order", 0))
+                      stencil_order=getattr(wl, "stencil_order", 0),
+                      deterministic=int(deterministic or getattr(wl, "deterministic", 0)))
     ncells = wl.nx * wl.ny * wl.nz
     sp = []
     for k, s in enumerate(wl.species):

@@ -72,7 +72,9 @@ def footprint(wl, precision: Optional[int] = None) -> int:
     cfg = gp.make_config(wl.nx, wl.ny, wl.nz, dx=wl.dx, dy=wl.dy, dz=wl.dz, dt=wl.dt, vgal=wl.vgal,
                          c=wl.c, eps0=wl.eps0, rho_bg=wl.rho_bg, beta_init=wl.beta_init,
                          shape_order=wl.shape_order, precision=prec,
-                         current_correction=wl.current_correction, init_fields=wl.init_fields)
+                         current_correction=wl.current_correction, init_fields=wl.init_fields,
+                         stencil_order=getattr(wl, "stencil_order", 0),
+                         deterministic=int(getattr(wl, "deterministic", 0)))
     ncells = wl.nx * wl.ny * wl.nz
     sp = [gp.generated_species(s.q, s.m, 1.0, ncells, s.ppc, s.u0, s.jitter, wl.seed, k)
           for k, s in enumerate(wl.species)]

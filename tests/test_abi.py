@@ -54,6 +54,9 @@ def test_invalid_config_is_rejected_without_a_gpu(binding):
         cfg = binding.make_config(8, 8, 8, stencil_order=bad)
         assert binding.lib.pic_footprint(ctypes.byref(cfg), None, 0, ctypes.byref(n)) == -1
         assert b"stencil_order" in binding.lib.pic_last_error()
+    cfg = binding.make_config(8, 8, 8, deterministic=2)
+    assert binding.lib.pic_footprint(ctypes.byref(cfg), None, 0, ctypes.byref(n)) == -1
+    assert b"deterministic" in binding.lib.pic_last_error()
 
 
 PROBE = r"""
@@ -64,6 +67,7 @@ PROBE = r"""
 int main(void) {
   printf("pic_config size %zu\npic_species size %zu\n", sizeof(pic_config), sizeof(pic_species));
   F(pic_config, vgal); F(pic_config, beta_init); F(pic_config, nx); F(pic_config, tile_margin);
+  F(pic_config, stencil_order); F(pic_config, deterministic);
   F(pic_species, n); F(pic_species, ppc); F(pic_species, species_id); F(pic_species, cell);
   F(pic_species, off); F(pic_species, u);
   return 0;
