@@ -361,45 +361,57 @@ def run_ours(args, rank, world, local_rank):
     }
     if args.serving_requests > 0 and world == 1:
         line["serving"] = serving_bench(args.serving_requests, args.serving_steps)
+        # small-run-heavy trace (32^3 and 64^3 grids only): where launches dominate
+        line["serving_small_runs"] = serving_bench(args.serving_requests, args.serving_steps,
+                                                   grids=[(32, 32, 32), (64, 64, 64)])
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(stencil_order=args.stencil_order)
     print(json.dumps(line), flush=True)
 
 
-def serving_bench(n_req, steps, chunk=25, seed=4):
+def serving_bench(n_req, steps, chunk=25, seed=4, grids=None):
     """Continuous batching vs serial execution of independent runs on one GPU: a burst
-    (all requests at t = 0) and a Poisson trace at twice the serial service rate."""
+    (all requests at t = 0) and a Poisson trace at twice the serial service rate. Arms:
+    serial (one run at a time), batched (runs on their own prioritised streams) and
+    batched with shared launches (small runs of one shape advanced together by
+    pic_step_many)."""
     import torch
     import galpic_inputs as gi
     from paper_1608_00215_gb300 import serve
-    wls = gi.serving_requests(n_req, seed=seed, steps=steps)
-    # warm-up: one short run per grid shape creates the shared FFT plans for both arms
+    kw = {} if grids is None else {"grids": grids}
+    wls = gi.serving_requests(n_req, seed=seed, steps=steps, **kw)
+    # warm-up: one short run per grid shape creates the shared FFT plans for every arm
     shapes = {}
     for wl in wls:
         shapes.setdefault((wl.nx, wl.ny, wl.nz), wl)
-    serve.serve([serve.Request(i, wl, 1, 0.0) for i, wl in enumerate(shapes.values())], chunk=1)
+    warm = [serve.Request(i, wl, 2, 0.0) for i, wl in enumerate(shapes.values())]
+    serve.serve(warm, chunk=1)
+    serve.warm_shared_plans(wls, max_slots=64)
+    serve.serve(warm + [serve.Request(100 + i, wl, 2, 0.0) for i, wl in enumerate(shapes.values())],
+                chunk=1, shared_launches=True)
     burst = [serve.Request(i, wl, steps, 0.0) for i, wl in enumerate(wls)]
+    sizes = sorted({(wl.nx, wl.ny, wl.nz) for wl in wls})
     out = {"requests": n_req, "steps_per_run": steps, "chunk_steps": chunk,
-           "trace": "grids {32^3, 64^3, 64x64x128, 128x128x256}, gamma {5,10,30,130}, v_gal {0, v_drift}, "
-                    "1-8 ppc/species, FP32, linear shapes, seed 4"}
+           "trace": f"grids {sizes}, gamma {{5,10,30,130}}, v_gal {{0, v_drift}}, 1-8 ppc/species, FP32, "
+                    f"linear shapes, seed {seed}"}
     serial = serve.serve(burst, max_slots=1, chunk=chunk)
     batched = serve.serve(burst, max_slots=64, chunk=chunk)
-    even = serve.serve(burst, max_slots=64, chunk=chunk, priorities=False)
-    uncapped = serve.serve(burst, max_slots=64, chunk=chunk, max_per_level=None)
+    shared = serve.serve(burst, max_slots=64, chunk=chunk, shared_launches=True)
     out["burst"] = {"serial": serial.summary(), "batched": batched.summary(),
-                    "batched_without_priorities": even.summary(),
-                    "batched_without_level_caps": uncapped.summary()}
+                    "batched_shared_launches": shared.summary()}
     out["stream_priority_range"] = list(torch.cuda.Stream.priority_range())
     mean_service = serial.makespan / max(1, n_req)
     arr = gi.poisson_arrivals(n_req, rate=2.0 / mean_service, seed=seed)
     trace = [serve.Request(i, wl, steps, float(a)) for i, (wl, a) in enumerate(zip(wls, arr))]
     serial_p = serve.serve(trace, max_slots=1, chunk=chunk)
     batched_p = serve.serve(trace, max_slots=64, chunk=chunk)
-    uncapped_p = serve.serve(trace, max_slots=64, chunk=chunk, max_per_level=None)
+    shared_p = serve.serve(trace, max_slots=64, chunk=chunk, shared_launches=True)
     out["poisson"] = {"rate_per_s": 2.0 / mean_service, "serial": serial_p.summary(),
-                      "batched": batched_p.summary(), "batched_without_level_caps": uncapped_p.summary()}
+                      "batched": batched_p.summary(), "batched_shared_launches": shared_p.summary()}
     out["speedup_runs_per_s"] = {"burst": batched.runs_per_s / serial.runs_per_s,
-                                 "poisson": batched_p.runs_per_s / serial_p.runs_per_s}
+                                 "burst_shared_launches": shared.runs_per_s / serial.runs_per_s,
+                                 "poisson": batched_p.runs_per_s / serial_p.runs_per_s,
+                                 "poisson_shared_launches": shared_p.runs_per_s / serial_p.runs_per_s}
     return out
 
 
@@ -751,6 +763,8 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=32,
                     help="requests of the serving leg (0 skips it)")
     ap.add_argument("--serving-steps", type=int, default=50, help="steps per serving request")
+    ap.add_argument("--serving-grids", default="",
+                    help="serving trace grids, e.g. 32x32x32,64x64x64 (default: the four config-4 grids)")
     ap.add_argument("--serving-only", action="store_true",
                     help="only the serving leg (e.g. the full trace: --serving-requests 256 --serving-steps 500)")
     ap.add_argument("--long-run", action="store_true",
@@ -790,7 +804,10 @@ def main():
     if args.serving_only:
         from paper_1608_00215_gb300 import build
         build.build()
-        out = serving_bench(args.serving_requests, args.serving_steps)
+        grids = None
+        if args.serving_grids:
+            grids = [tuple(int(x) for x in g.split("x")) for g in args.serving_grids.split(",")]
+        out = serving_bench(args.serving_requests, args.serving_steps, grids=grids)
         print(json.dumps({"mode": "serving", **out}), flush=True)
         return
     if world > 1:

@@ -64,6 +64,11 @@ extern "C" {
 #define PIC_STATUS_BADINPUT 2   /* loaded particles had a cell outside [0, N) or an
                                    offset outside [0, 1); they were clamped to cell 0 /
                                    offset 0 so that every kernel stays in bounds         */
+#define PIC_STATUS_BOUNDS 4     /* checked build (libgalpic_checked.so, compiled with
+                                   PIC_CHECKED): a particle, grid, tile or staging index
+                                   was outside its buffer's logical range; the access was
+                                   skipped. Never set by the ordinary build, which does
+                                   not test indices                                      */
 
 typedef struct pic_sim pic_sim;
 
@@ -224,7 +229,8 @@ int pic_step(pic_sim* sim, int nsteps, void* stream);
  * update (one block row per run), one batched inverse transform; one such step of the set
  * is captured once as a CUDA graph (cached for this workspace and set of runs) and
  * replayed nsteps times. Each run's arithmetic is its single-run step's: results equal
- * pic_step's to rounding (bitwise in deterministic mode).
+ * pic_step's to rounding; in deterministic mode bitwise (those runs' transforms then use
+ * their single-run cuFFT plans, one per run, since a batched plan may round differently).
  *   sims:      nsims (1 .. 4096) distinct runs with equal nx, ny, nz, precision, shape
  *              order, tile margin, deposit strategy (as chosen by pic_config.deposit or
  *              pic_tune), species count and deterministic mode; other parameters (cell
@@ -267,6 +273,31 @@ int pic_step_many(pic_sim** sims, int nsims, int nsteps, void* workspace, size_t
  * Errors: PIC_EINVAL for a bad array, a repeated run, mismatched grids or step
  * counts; otherwise as pic_step. */
 int pic_step_coupled(pic_sim** sims, int nsims, int nsteps, void* stream);
+
+/* Domain decomposition of the field update along z, all subdomains on this GPU (the
+ * paper's conclusion names decomposition with arbitrary-order spectral solvers as the route
+ * to many processors). Each step: the ordinary particle pass (global deposit), then each of
+ * the ndomains subdomains takes its nz/ndomains cells plus `guard` cells on either side
+ * (periodic) of the real E, B, J, rho^{n+1} and rho^n as a periodic window, applies the
+ * Galilean-PSATD update there with the window's own finite-order-stencil wavenumbers (the
+ * Nyquist planes of a window are updated like any mode), and keeps its own cells. All
+ * windows go through one gather kernel, one batched R2C, one k-space launch, one batched C2R
+ * and one scatter kernel. The real E, B are the state between steps; rho^n is the last
+ * deposit's rho (PIC_BUF_RHO). At the end of the call the run's spectral E, B, rho^n and
+ * source spectra are refreshed as the forward transforms of the real state (whose inverse
+ * transform gives the real state back), so that pic_step can continue from it.
+ *   ndomains: >= 1, divides nz; guard: >= 0 cells; with ndomains > 1 the run must have
+ *             current_correction = 0 (its 1/k^2 reaches the whole grid) and a finite
+ *             stencil_order (the spectral solver's update has unbounded reach).
+ *   workspace: caller-owned device memory, 256-byte aligned, of at least
+ *             pic_decomposed_footprint() bytes (windows, their spectra, the window factors,
+ *             the FFT work area). The window factors are rebuilt at every call (FP64).
+ * The batched window plans are created on first use per window shape and kept for the life
+ * of the process. Asynchronous on `stream`. Errors: PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA,
+ * PIC_ECUFFT. */
+int pic_decomposed_footprint(const pic_sim* sim, int ndomains, int guard, size_t* bytes_out);
+int pic_step_decomposed(pic_sim* sim, int ndomains, int guard, int nsteps, void* workspace, size_t ws_bytes,
+                        void* stream);
 
 /* Field energy W = (eps0/2) sum (|E|^2 + c^2 |B|^2) dV of the real E^n, B^n,
  * written as one double to the DEVICE address out_dev. Sets
@@ -334,7 +365,8 @@ int pic_set_particles(pic_sim* sim, int species, const int32_t* cell, const void
 int pic_sort(pic_sim* sim, void* stream);
 
 /* Synchronising: read the device status word (PIC_STATUS_* bits) and clear
- * it. Returns PIC_ENONFINITE if the non-finite bit was set, else PIC_OK. */
+ * it. Returns PIC_EBOUNDS if the bounds bit was set (checked build), else
+ * PIC_ENONFINITE if the non-finite bit was set, else PIC_OK. */
 int pic_status(pic_sim* sim, int32_t* status_out);
 
 /* Synchronising: read the run's counters: [0] steps taken, [1] particle

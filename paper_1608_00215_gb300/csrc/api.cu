@@ -1,6 +1,7 @@
 // C ABI of the Galilean-PSATD step (include/galpic.h): validation, workspace
 // layout, cuFFT plans, stage sequencing and CUDA-graph replay.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -11,6 +12,7 @@
 #include <new>
 #include <string>
 #include <tuple>
+#include <vector>
 
 #include "common.cuh"
 
@@ -38,6 +40,10 @@ struct PlanEntry {
 namespace {
 
 constexpr size_t ALIGN = 256;
+// Deterministic runs step through the same table-driven kernels as shared launches
+// (pic_step_many), so that a run's bits do not depend on which path advanced it: its pass
+// parameters at offset 0 and its k-space parameters at DESC_KSPACE of this region.
+constexpr size_t DESC_KSPACE = 2048, DESC_BYTES = 4096;
 
 size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 
@@ -168,6 +174,7 @@ void make_layout(const pic_config& c, const Dims& d, const int64_t* n, int ns, s
     L.off_key_cnt = take(sort_keys(d) * 4);
     L.off_tile_sum = take(sort_tiles(d) * 4);
     L.off_S64 = take(c.deterministic ? 4 * d.N * 8 : 0);
+    L.off_desc = take(c.deterministic ? DESC_BYTES : 0);
     L.off_F = take(6 * d.N * T);
     L.off_S = take(4 * d.N * T);
     L.off_EBh = take(6 * d.M * 2 * T);
@@ -298,7 +305,11 @@ int deposit_sources(pic_sim* s, int mode, cudaStream_t st) {
         GP_CUDA(cudaMemsetAsync(s->S64, 0, 4 * s->d.N * sizeof(long long), st));
         StageTimer t(s, STAGE_PARTICLES, st);
         count_launches(s, 2);
-        GP_CHECK(launch_particle_pass(s, mode, st));
+        if (mode == PASS_STEP)
+            GP_CHECK(s->cfg.precision == 64 ? launch_pass_many_fp64(s, s->desc, 1, st)
+                                            : launch_pass_many_fp32(s, s->desc, 1, st));
+        else
+            GP_CHECK(launch_particle_pass(s, mode, st));
         return launch_fixed_to_real(s, st);
     }
     GP_CUDA(cudaMemsetAsync(s->S, 0, 4 * s->d.N * real_bytes(s), st));
@@ -341,6 +352,7 @@ int field_update_spectral(pic_sim* s, cudaStream_t st) {
     }
     StageTimer t(s, STAGE_KSPACE, st);
     count_launches(s, 1);
+    if (s->desc) return launch_kspace_many(s, s->desc + DESC_KSPACE, 1, st);
     return launch_kspace_update(s, st);
 }
 
@@ -410,13 +422,24 @@ int capture_step(pic_sim* s) {
 }
 
 }  // namespace
+
+int gather_push_stage(pic_sim* s, cudaStream_t st) { return gather_push(s, st); }
+
+std::mutex* plan_mutex(pic_sim* s) { return &s->plans->mu; }
+
+int r2c_on(pic_sim* s, void* in, void* out, cudaStream_t st) { return exec_r2c_on(s, in, out, st); }
+
 }  // namespace galpic
 
 using namespace galpic;
 
 extern "C" {
 
-const char* pic_version(void) { return "galpic 0.1 (Galilean-PSATD PIC, sm_103a)"; }
+#ifdef PIC_CHECKED
+const char* pic_version(void) { return "galpic 0.2 (Galilean-PSATD PIC, sm_103a, checked build)"; }
+#else
+const char* pic_version(void) { return "galpic 0.2 (Galilean-PSATD PIC, sm_103a)"; }
+#endif
 
 const char* pic_last_error(void) { return g_err.c_str(); }
 
@@ -498,6 +521,16 @@ int pic_init(const pic_config* cfg, const pic_species* species, int nspecies, vo
     s->F = w + L.off_F;
     s->S = w + L.off_S;
     s->S64 = cfg->deterministic ? (long long*)(w + L.off_S64) : nullptr;
+    s->desc = cfg->deterministic ? (char*)(w + L.off_desc) : nullptr;
+#ifdef PIC_CHECKED
+    // the checker's own test: GALPIC_CHECKED_INJECT=gather shifts the gather's tile index
+    // by one tile (still inside the CTA's shared memory) so that its bound test must fire
+    {
+        const char* inj = getenv("GALPIC_CHECKED_INJECT");
+        const int TEc = 8 + (cfg->shape_order == 1 ? 2 : 4) - 1 + 2 * cfg->tile_margin;
+        s->inject = (inj && strcmp(inj, "gather") == 0) ? TEc * TEc * TEc : 0;
+    }
+#endif
     s->fix_exp = fixed_point_exponent(*cfg, species, nspecies);
     s->EBh = w + L.off_EBh;
     s->EBs = w + L.off_EBs;
@@ -588,6 +621,19 @@ int pic_init(const pic_config* cfg, const pic_species* species, int nspecies, vo
         INIT_TRY(e == cudaSuccess ? PIC_OK : fail(PIC_ECUDA, std::string("init: ") + cudaGetErrorString(e)));
         INIT_TRY((stv & PIC_STATUS_BADINPUT) == 0
                      ? PIC_OK : fail(PIC_EINVAL, "particle input: a cell outside [0, N) or an offset outside [0, 1)"));
+    }
+    if (s->desc) {   // the run's parameter tables (pageable source: staged before the call returns)
+        const size_t pb = s->cfg.precision == 64 ? pass_desc_bytes_fp64() : pass_desc_bytes_fp32();
+        INIT_TRY(pb <= DESC_KSPACE && kspace_desc_bytes(s->cfg.precision) <= DESC_BYTES - DESC_KSPACE
+                     ? PIC_OK : fail(PIC_EINVAL, "parameter tables larger than their region"));
+        std::vector<char> host(DESC_BYTES, 0);
+        if (s->cfg.precision == 64)
+            fill_pass_desc_fp64(s, host.data(), nullptr, nullptr, nullptr);
+        else
+            fill_pass_desc_fp32(s, host.data(), nullptr, nullptr, nullptr);
+        fill_kspace_desc(s, host.data() + DESC_KSPACE, nullptr, nullptr);
+        INIT_TRY(cudaMemcpyAsync(s->desc, host.data(), DESC_BYTES, cudaMemcpyHostToDevice, st) == cudaSuccess
+                     ? PIC_OK : fail(PIC_ECUDA, "parameter tables"));
     }
 #undef INIT_TRY
     *out = s;
@@ -873,6 +919,7 @@ int pic_status(pic_sim* s, int32_t* status_out) {
     GP_CUDA(cudaMemcpy(&v, s->status, sizeof(v), cudaMemcpyDeviceToHost));
     GP_CUDA(cudaMemset(s->status, 0, sizeof(v)));
     if (status_out) *status_out = v;
+    if (v & PIC_STATUS_BOUNDS) return fail(PIC_EBOUNDS, "an index left its buffer's range (checked build)");
     if (v & PIC_STATUS_NONFINITE) return fail(PIC_ENONFINITE, "non-finite field value seen");
     return PIC_OK;
 }

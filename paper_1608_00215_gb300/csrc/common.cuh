@@ -5,6 +5,7 @@
 #include <cufft.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -86,6 +87,21 @@ __device__ __forceinline__ bool sort_needed(const unsigned long long* cnt) {
 }
 
 // ---------------------------------------------------------------------------
+// Checked build (PIC_CHECKED): index tests that record a violation in the device status
+// word and let the caller skip the access. The ordinary build compiles them away.
+// ---------------------------------------------------------------------------
+#ifdef PIC_CHECKED
+__device__ __forceinline__ bool index_ok(int64_t i, int64_t n, int32_t* status) {
+    if (i >= 0 && i < n) return true;
+    atomicOr(status, PIC_STATUS_BOUNDS);
+    return false;
+}
+#define PIC_INDEX_OK(i, n, status) ::galpic::index_ok((int64_t)(i), (int64_t)(n), (status))
+#else
+#define PIC_INDEX_OK(i, n, status) true
+#endif
+
+// ---------------------------------------------------------------------------
 // splitmix64 (Vigna): output function applied to a counter
 // ---------------------------------------------------------------------------
 __host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
@@ -113,7 +129,7 @@ struct Layout {
     size_t off_species[PIC_MAX_SPECIES][9];   // cell, off x/y/z, u x/y/z, bin_start, cell_start
     size_t off_tmp[8];                        // cell, off x/y/z, u x/y/z, rank
     size_t off_key_cnt, off_tile_sum;
-    size_t off_S64;
+    size_t off_S64, off_desc;
     size_t off_F, off_S, off_EBh, off_EBs, off_Sh, off_Rn, off_Tab, off_K, off_Kt, off_Ph;
     size_t off_fftwork;
     size_t off_epart;
@@ -143,6 +159,7 @@ struct pic_sim {
     void* F;     // real E (3N) then B (3N)
     void* S;     // real Jx, Jy, Jz, rho (4N)
     long long* S64;   // deterministic mode: the sources in 64-bit fixed point (4N), else NULL
+    char* desc;       // deterministic mode: the run's pass and k-space parameter tables (device)
     int fix_exp;      // deterministic mode: delta = 2^fix_exp (units of the fixed-point sources)
     void* EBh;   // spectral master E, B (6M complex)
     void* EBs;   // C2R input: master / N (6M complex)
@@ -173,6 +190,7 @@ struct pic_sim {
     int64_t graph_kernels;   // own kernels in one captured step
     bool capturing;
     bool profiling;
+    int inject;   // checked build only: a deliberate tile-index offset for the checker's own test
     struct Rec { int stage; cudaEvent_t a, b; };
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> event_pool;
@@ -233,6 +251,20 @@ struct CopyDesc {
 int launch_copy_many(const CopyDesc* descs_dev, int n, size_t max_bytes, cudaStream_t st);
 // Forget the captured shared-launch steps that involve a run (called by pic_destroy).
 void many_forget(pic_sim* s);
+
+// Decomposed field update (decomp.cu): wavenumbers and factors of the window grid
+// (nx, ny, nz_w), and the k-space update of nwin windows (descriptors in device memory;
+// the Nyquist planes of a window are updated like any mode).
+int launch_window_tables(const pic_sim* s, int nz_w, double* K, void* Kt, void* tab, cudaStream_t st);
+void fill_window_kspace_desc(const pic_sim* s, void* out, int nz_w, void* spec, void* ebs, const void* Kt,
+                             const void* tab);
+int launch_kspace_windows(const pic_sim* s, const void* descs, int nwin, int64_t M_w, cudaStream_t st);
+// The mutex that serialises the set-stream / set-work-area / execute sequence of a run's
+// shared single-run cuFFT plans (api.cu).
+std::mutex* plan_mutex(pic_sim* s);
+// Pieces of the single-run step that the decomposed step reuses (api.cu).
+int gather_push_stage(pic_sim* s, cudaStream_t st);
+int r2c_on(pic_sim* s, void* in, void* out, cudaStream_t st);
 // Deterministic mode over a staging area: real sources from fixed-point sums, run r of
 // nruns at S64 + r n (its unit 2^e[r], e in device memory).
 int launch_fixed_to_real_many(const long long* S64, void* S, int64_t n, const int* e_dev, int nruns,

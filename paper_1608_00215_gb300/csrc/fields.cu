@@ -250,6 +250,7 @@ struct KParams {
     T invN;
     T bg[3];          // N rho_bg v_gal: background current at k = 0
     int cc;
+    int keep_nyquist; // 1: update the Nyquist planes like any mode (decomposed windows)
 };
 
 __device__ __forceinline__ bool is_nyquist(int mx, int my, int mz, int nx, int ny, int nz) {
@@ -270,7 +271,7 @@ __device__ __forceinline__ void kspace_update_body(const KParams<T>& p) {
         int64_t r = m / p.nzh;
         int my = (int)(r % p.ny);
         int mx = (int)(r / p.ny);
-        if (is_nyquist(mx, my, mz, p.nx, p.ny, p.nz)) {
+        if (!p.keep_nyquist && is_nyquist(mx, my, mz, p.nx, p.ny, p.nz)) {
             C z = mk<C>(0.0, 0.0);
 #pragma unroll
             for (int q = 0; q < 6; ++q) {
@@ -603,6 +604,85 @@ static int kspace_typed(pic_sim* s, cudaStream_t st) {
 
 int launch_kspace_update(pic_sim* s, cudaStream_t st) {
     return s->cfg.precision == 64 ? kspace_typed<double>(s, st) : kspace_typed<float>(s, st);
+}
+
+// Wavenumbers and per-mode factors of a grid that has the run's nx, ny, cell sizes,
+// units, v_gal and stencil order but nz_w nodes along z (the windows of a decomposed
+// field update): K (FP64) and Kt (run precision) hold nx + ny + nz_w/2 + 1 entries, tab
+// 6 nx ny (nz_w/2 + 1) complex factors.
+int launch_window_tables(const pic_sim* s, int nz_w, double* K, void* Kt, void* tab, cudaStream_t st) {
+    const pic_config& c = s->cfg;
+    const int nx = s->d.nx, ny = s->d.ny, nzh = nz_w / 2 + 1;
+    const int64_t M = (int64_t)nx * ny * nzh;
+    const StencilWeights sw = stencil_weights(c.stencil_order);
+    const int nk = nx + ny + nzh;
+    if (c.precision == 64)
+        wavenumbers_kernel<double><<<(nk + 127) / 128, 128, 0, st>>>(K, (double*)Kt, nx, ny, nzh, nz_w, c.dx, c.dy,
+                                                                     c.dz, sw);
+    else
+        wavenumbers_kernel<float><<<(nk + 127) / 128, 128, 0, st>>>(K, (float*)Kt, nx, ny, nzh, nz_w, c.dx, c.dy,
+                                                                    c.dz, sw);
+    GP_CUDA(cudaGetLastError());
+    GaussLegendre gl = gauss_legendre();
+    const int fx = c.vgal[0] == 0.0, fy = c.vgal[1] == 0.0;
+    const int64_t rep = (int64_t)(fx ? nx / 2 + 1 : nx) * (fy ? ny / 2 + 1 : ny) * nzh;
+    const int grid = grid_for(rep, 128);
+    if (c.precision == 64)
+        build_tables_kernel<double2><<<grid, 128, 0, st>>>((double2*)tab, K, nx, ny, nz_w, nzh, M, c.dt, c.vgal[0],
+                                                           c.vgal[1], c.vgal[2], c.c, c.eps0, c.current_correction,
+                                                           gl, fx, fy);
+    else
+        build_tables_kernel<float2><<<grid, 128, 0, st>>>((float2*)tab, K, nx, ny, nz_w, nzh, M, c.dt, c.vgal[0],
+                                                          c.vgal[1], c.vgal[2], c.c, c.eps0, c.current_correction,
+                                                          gl, fx, fy);
+    GP_CUDA(cudaGetLastError());
+    return PIC_OK;
+}
+
+template <typename T>
+static void fill_window_kparams(const pic_sim* s, KParams<T>& p, int nz_w, void* spec, void* ebs, const void* Kt,
+                                const void* tab) {
+    typedef typename cplx<T>::type C;
+    const pic_config& c = s->cfg;
+    const int nzh = nz_w / 2 + 1;
+    const int64_t M = (int64_t)s->d.nx * s->d.ny * nzh, N = (int64_t)s->d.nx * s->d.ny * nz_w;
+    memset(&p, 0, sizeof(p));
+    p.EBh = (C*)spec;                 // window spectra: E (3), B (3), J (3), rho^{n+1}, rho^n
+    p.Sh = (const C*)spec + 6 * M;
+    p.Rn = (C*)spec + 10 * M;
+    p.EBs = (C*)ebs;
+    p.tab = (const C*)tab;
+    p.M = M;
+    p.nx = s->d.nx;
+    p.ny = s->d.ny;
+    p.nz = nz_w;
+    p.nzh = nzh;
+    p.kx = (const T*)Kt;
+    p.ky = p.kx + s->d.nx;
+    p.kz = p.ky + s->d.ny;
+    p.c2 = (T)(c.c * c.c);
+    p.invN = (T)(1.0 / (double)N);
+    for (int d = 0; d < 3; ++d) p.bg[d] = (T)((double)N * c.rho_bg * c.vgal[d]);
+    p.cc = c.current_correction;
+    p.keep_nyquist = 1;
+}
+
+void fill_window_kspace_desc(const pic_sim* s, void* out, int nz_w, void* spec, void* ebs, const void* Kt,
+                             const void* tab) {
+    if (s->cfg.precision == 64)
+        fill_window_kparams<double>(s, *static_cast<KParams<double>*>(out), nz_w, spec, ebs, Kt, tab);
+    else
+        fill_window_kparams<float>(s, *static_cast<KParams<float>*>(out), nz_w, spec, ebs, Kt, tab);
+}
+
+int launch_kspace_windows(const pic_sim* s, const void* descs, int nwin, int64_t M_w, cudaStream_t st) {
+    const int gx = std::max(1, grid_for(M_w, 256) / std::max(1, std::min(nwin, 16)));
+    if (s->cfg.precision == 64)
+        kspace_update_many_kernel<double><<<dim3(gx, nwin), 256, 0, st>>>((const KParams<double>*)descs);
+    else
+        kspace_update_many_kernel<float><<<dim3(gx, nwin), 256, 0, st>>>((const KParams<float>*)descs);
+    GP_CUDA(cudaGetLastError());
+    return PIC_OK;
 }
 
 size_t kspace_desc_bytes(int precision) {

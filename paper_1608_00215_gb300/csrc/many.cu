@@ -192,7 +192,25 @@ int capture_many(pic_sim** sims, int n, int C, char* ws, const ManyLayout& L, Ma
                                                (const int*)(ws + L.exps), n, s0->cfg.precision, st));
             kernels += 1;
         }
-        {
+        // deterministic runs transform with their own single-run plans (a batched plan may
+        // round differently), so that a run's bits do not depend on the runs beside it
+        const bool per_run = s0->cfg.deterministic != 0;
+        const size_t sN = 4 * (size_t)N * T, sM = 4 * (size_t)s0->d.M * 2 * T;
+        const size_t eM = 6 * (size_t)s0->d.M * 2 * T, fN = 6 * (size_t)N * T;
+        if (per_run) {
+            for (int r = 0; r < n; ++r) {
+                pic_sim* s = sims[r];
+                std::lock_guard<std::mutex> lk(*plan_mutex(s));
+                GP_CUFFT(cufftSetWorkArea(s->plan_r2c, s->fftwork));
+                GP_CUFFT(cufftSetStream(s->plan_r2c, st));
+                if (s0->cfg.precision == 64)
+                    GP_CUFFT(cufftExecD2Z(s->plan_r2c, (cufftDoubleReal*)(ws + L.S + r * sN),
+                                          (cufftDoubleComplex*)(ws + L.Sh + r * sM)));
+                else
+                    GP_CUFFT(cufftExecR2C(s->plan_r2c, (cufftReal*)(ws + L.S + r * sN),
+                                          (cufftComplex*)(ws + L.Sh + r * sM)));
+            }
+        } else {
             std::lock_guard<std::mutex> lk(mp->mu);
             GP_CUFFT(cufftSetWorkArea(mp->r2c, ws + L.work));
             GP_CUFFT(cufftSetStream(mp->r2c, st));
@@ -203,7 +221,20 @@ int capture_many(pic_sim** sims, int n, int C, char* ws, const ManyLayout& L, Ma
         }
         GP_CHECK(launch_kspace_many(s0, ws + L.kspace_desc, n, st));
         kernels += 1;
-        {
+        if (per_run) {
+            for (int r = 0; r < n; ++r) {
+                pic_sim* s = sims[r];
+                std::lock_guard<std::mutex> lk(*plan_mutex(s));
+                GP_CUFFT(cufftSetWorkArea(s->plan_c2r, s->fftwork));
+                GP_CUFFT(cufftSetStream(s->plan_c2r, st));
+                if (s0->cfg.precision == 64)
+                    GP_CUFFT(cufftExecZ2D(s->plan_c2r, (cufftDoubleComplex*)(ws + L.EBs + r * eM),
+                                          (cufftDoubleReal*)(ws + L.F + r * fN)));
+                else
+                    GP_CUFFT(cufftExecC2R(s->plan_c2r, (cufftComplex*)(ws + L.EBs + r * eM),
+                                          (cufftReal*)(ws + L.F + r * fN)));
+            }
+        } else {
             std::lock_guard<std::mutex> lk(mp->mu);
             GP_CUFFT(cufftSetWorkArea(mp->c2r, ws + L.work));
             GP_CUFFT(cufftSetStream(mp->c2r, st));

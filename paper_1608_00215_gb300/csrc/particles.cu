@@ -119,11 +119,16 @@ __device__ __forceinline__ void sort_zero_body(int32_t* key_cnt, int64_t K, cons
         key_cnt[i] = 0;
 }
 
-__device__ __forceinline__ void sort_count_body(const int32_t* __restrict__ cell, int64_t n, int32_t* rank, int32_t* key_cnt, BinGeom g, const unsigned long long* cnt) {
+__device__ __forceinline__ void sort_count_body(const int32_t* __restrict__ cell, int64_t n, int32_t* rank,
+                                                int32_t* key_cnt, BinGeom g, const unsigned long long* cnt,
+                                                int64_t K, int32_t* status) {
     if (!sort_needed(cnt)) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        rank[i] = atomicAdd(&key_cnt[g.key_of(cell[i])], 1);
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int key = g.key_of(cell[i]);
+        if (!PIC_INDEX_OK(key, K, status)) continue;
+        rank[i] = atomicAdd(&key_cnt[key], 1);
+    }
 }
 
 // Block-wide exclusive scan of one value per thread (1024 threads); returns the
@@ -223,12 +228,14 @@ template <typename T>
 __device__ __forceinline__ void sort_scatter_body(const int32_t* __restrict__ cell, Ptr6<T> src, int64_t n,
                                                   const int32_t* __restrict__ rank,
                                                   const int32_t* __restrict__ cell_start, int32_t* tcell,
-                                                  Ptr6<T> dst, BinGeom g, const unsigned long long* cnt) {
+                                                  Ptr6<T> dst, BinGeom g, const unsigned long long* cnt,
+                                                  int32_t* status) {
     if (!sort_needed(cnt)) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         int c = cell[i];
         int64_t j = (int64_t)cell_start[g.key_of(c)] + rank[i];
+        if (!PIC_INDEX_OK(j, n, status)) continue;
         tcell[j] = c;
 #pragma unroll
         for (int q = 0; q < 6; ++q) dst.p[q][j] = src.p[q][i];
@@ -252,8 +259,8 @@ __global__ void sort_zero_kernel(int32_t* key_cnt, int64_t K, const unsigned lon
     sort_zero_body(key_cnt, K, cnt);
 }
 __global__ void sort_count_kernel(const int32_t* __restrict__ cell, int64_t n, int32_t* rank, int32_t* key_cnt,
-                                  BinGeom g, const unsigned long long* cnt) {
-    sort_count_body(cell, n, rank, key_cnt, g, cnt);
+                                  BinGeom g, const unsigned long long* cnt, int64_t K, int32_t* status) {
+    sort_count_body(cell, n, rank, key_cnt, g, cnt, K, status);
 }
 __global__ void __launch_bounds__(SCAN_THREADS) scan_tiles_kernel(const int32_t* key_cnt, int64_t K,
                                                                   int32_t* tile_sum,
@@ -273,8 +280,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_write_kernel(const int32_t*
 template <typename T>
 __global__ void sort_scatter_kernel(const int32_t* __restrict__ cell, Ptr6<T> src, int64_t n,
                                     const int32_t* __restrict__ rank, const int32_t* __restrict__ cell_start,
-                                    int32_t* tcell, Ptr6<T> dst, BinGeom g, const unsigned long long* cnt) {
-    sort_scatter_body<T>(cell, src, n, rank, cell_start, tcell, dst, g, cnt);
+                                    int32_t* tcell, Ptr6<T> dst, BinGeom g, const unsigned long long* cnt,
+                                    int32_t* status) {
+    sort_scatter_body<T>(cell, src, n, rank, cell_start, tcell, dst, g, cnt, status);
 }
 template <typename T>
 __global__ void sort_copyback_kernel(int32_t* cell, Ptr6<T> dst, int64_t n, const int32_t* __restrict__ tcell,
@@ -296,6 +304,7 @@ struct SortDesc {
     int32_t* bin_start;
     int32_t* cell_start;
     const unsigned long long* cnt;
+    int32_t* status;
     int64_t n, K;
     BinGeom g;
     int nt, bxyz, nbins, pad;
@@ -309,7 +318,7 @@ __global__ void sort_zero_many(const SortDesc<T>* __restrict__ d) {
 template <typename T>
 __global__ void sort_count_many(const SortDesc<T>* __restrict__ d) {
     const SortDesc<T>& r = d[blockIdx.y];
-    sort_count_body(r.cell, r.n, r.rank, r.key_cnt, r.g, r.cnt);
+    sort_count_body(r.cell, r.n, r.rank, r.key_cnt, r.g, r.cnt, r.K, r.status);
 }
 template <typename T>
 __global__ void __launch_bounds__(SCAN_THREADS) scan_tiles_many(const SortDesc<T>* __restrict__ d) {
@@ -329,7 +338,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_write_many(const SortDesc<T
 template <typename T>
 __global__ void sort_scatter_many(const SortDesc<T>* __restrict__ d) {
     const SortDesc<T>& r = d[blockIdx.y];
-    sort_scatter_body<T>(r.cell, r.own, r.n, r.rank, r.cell_start, r.tcell, r.tmp, r.g, r.cnt);
+    sort_scatter_body<T>(r.cell, r.own, r.n, r.rank, r.cell_start, r.tcell, r.tmp, r.g, r.cnt, r.status);
 }
 template <typename T>
 __global__ void sort_copyback_many(const SortDesc<T>* __restrict__ d) {
@@ -425,7 +434,7 @@ int sort_typed(pic_sim* s, cudaStream_t st) {
         if (sp.n == 0) continue;
         sort_zero_kernel<<<grid_for(K, 256), 256, 0, st>>>(s->key_cnt, K, s->cnt);
         sort_count_kernel<<<grid_for(sp.n, 256), 256, 0, st>>>(sp.cell, sp.n, s->tmp_rank,
-                                                               s->key_cnt, g, s->cnt);
+                                                               s->key_cnt, g, s->cnt, K, s->status);
         scan_tiles_kernel<<<nt, SCAN_THREADS, 0, st>>>(s->key_cnt, K, s->tile_sum, s->cnt);
         scan_sums_kernel<<<1, SCAN_THREADS, 0, st>>>(s->tile_sum, nt, s->cnt);
         scan_write_kernel<<<nt, SCAN_THREADS, 0, st>>>(s->key_cnt, K, s->tile_sum, sp.cell_start,
@@ -436,7 +445,7 @@ int sort_typed(pic_sim* s, cudaStream_t st) {
             own.p[3 + d] = (T*)sp.u[d];
         }
         sort_scatter_kernel<T><<<grid_for(sp.n, 256), 256, 0, st>>>(
-            sp.cell, own, sp.n, s->tmp_rank, sp.cell_start, s->tmp_cell, tmp, g, s->cnt);
+            sp.cell, own, sp.n, s->tmp_rank, sp.cell_start, s->tmp_cell, tmp, g, s->cnt, s->status);
         sort_copyback_kernel<T><<<grid_for(sp.n, 256), 256, 0, st>>>(sp.cell, own, sp.n,
                                                                      s->tmp_cell, tmp, s->cnt);
     }
@@ -485,6 +494,7 @@ static void fill_sort_desc_t(const pic_sim* s, int k, SortDesc<T>& r) {
     r.bin_start = sp.bin_start;
     r.cell_start = sp.cell_start;
     r.cnt = s->cnt;
+    r.status = s->status;
     r.n = sp.n;
     r.K = sort_keys(s->d);
     r.g = BinGeom{s->d.ny, s->d.nz, s->d.BX, s->d.BY, s->d.BZ, s->d.nby, s->d.nbz};

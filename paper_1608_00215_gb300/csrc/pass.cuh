@@ -230,8 +230,14 @@ enum { DEP_GROUP = 0, DEP_ROW = 1, DEP_JR = 2, DEP_ROWU = 3, DEP_CELL = 4, DEP_F
 // pass adds a flag row and the x^{n+1} weights.
 __host__ __device__ constexpr int stage_rows(int NW, bool jr) { return jr ? 4 + 6 * NW : 3 + 3 * NW; }
 
+// Per-warp particle staging of the one-thread-per-cell pass: CELL_CHUNK particles of one
+// species (cell, three offsets, three momenta), loaded and stored coalesced. A warp's 32
+// cells hold 256 particles of a species at 8 per cell, which one chunk then covers, so
+// that every lane has its cell's particles in the same chunk.
+constexpr int CELL_CHUNK = 256;
+
 __host__ __device__ constexpr size_t stage_bytes(int NW, size_t T, int dep) {
-    return dep == DEP_CELL ? 0
+    return dep == DEP_CELL ? align16((size_t)CELL_CHUNK * (4 + 6 * T))
            : (T == 4 && NW == 4 && (dep == DEP_ROW || dep == DEP_ROWU))
                ? RowStage::BYTES
                : align16((size_t)stage_rows(NW, NW == 2 || dep == DEP_JR) * 34 * T);
@@ -266,6 +272,7 @@ struct SpeciesK {
     T* u[3];
     const int32_t* bin_start;
     const int32_t* cell_start;   // first particle of each cell key (bin-major) as of the last sort
+    int32_t n;   // particles of the species (the checked build tests indices against it)
     T qw_dv;   // q w / dV
     T qdt2m;   // q dt / (2 m)
 };
@@ -286,6 +293,8 @@ struct PassK {
     int nspecies;
     SpeciesK<T> sp[PIC_MAX_SPECIES];
     unsigned long long* cnt;
+    int32_t* status;   // device status word (checked build: PIC_STATUS_BOUNDS)
+    int inject;        // checked build only: tile-index offset of the checker's own test
 };
 
 // Move (i, f) by d cells along an axis of n cells: offset back to [0, 1), periodic.
@@ -344,6 +353,7 @@ __device__ void deposit_global(const PassK<T>& p, int ix, int iy, int iz, const 
                 for (int c = 0; c < NW; ++c) {
                     const T w = wxy * wz[c];
                     const int64_t g = base + wrapi(iz + J0 + c, p.nz);
+                    if (!PIC_INDEX_OK(g, p.N, p.status)) continue;
                     for (int q = 0; q < Q; ++q) atomicAdd(&p.S[(q0 + q) * p.N + g], w * val[q]);
                 }
             }
@@ -356,6 +366,7 @@ __device__ void deposit_global(const PassK<T>& p, int ix, int iy, int iz, const 
         const T w = pick<T, NW>(wx, a) * pick<T, NW>(wy, b) * pick<T, NW>(wz, c);
         const int64_t g = ((int64_t)wrap_near(ix + J0 + a, p.nx) * p.ny + wrap_near(iy + J0 + b, p.ny)) * p.nz +
                           wrap_near(iz + J0 + c, p.nz);
+        if (!PIC_INDEX_OK(g, p.N, p.status)) continue;
         T* dst = p.S + q0 * p.N + g;
         atomicAdd(dst, w * v0);
         if (Q > 1) {
@@ -427,6 +438,7 @@ __device__ void deposit_global_fixed(const PassK<T>& p, int ix, int iy, int iz, 
         const T xa = pick<T, NW>(wx, a), yb = pick<T, NW>(wy, b), zc = pick<T, NW>(wz, c);
         const int64_t g = ((int64_t)wrapi(ix + J0 + a, p.nx) * p.ny + wrapi(iy + J0 + b, p.ny)) * p.nz +
                           wrapi(iz + J0 + c, p.nz);
+        if (!PIC_INDEX_OK(g, p.N, p.status)) continue;
         for (int q = 0; q < Q; ++q) {
             const long long v = fixed_contrib<T>(xa, yb, zc, val[q]);
             if (v) add_fixed(p.S64 + (int64_t)(q0 + q) * p.N + g, v);
@@ -1092,7 +1104,11 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p, const int 
     for (int s = 0; s < (MIX ? 1 : p.nspecies); ++s) {
         const int hs = MIX ? (int)((threadIdx.x >> 4) & 1) : s;
         const SpeciesK<T> sp = p.sp[hs];
-        const int beg = sp.bin_start[b], end = sp.bin_start[b + 1];
+        int beg = sp.bin_start[b], end = sp.bin_start[b + 1];
+        // checked build: a bin range outside the species' particles is flagged and emptied
+        if (!(PIC_INDEX_OK(beg, (int64_t)sp.n + 1, p.status) && PIC_INDEX_OK(end, (int64_t)sp.n + 1, p.status) &&
+              PIC_INDEX_OK(end - beg, (int64_t)sp.n + 1, p.status)))
+            beg = end = 0;
         int span = end - beg;
         if constexpr (MIX)
             span = max(p.sp[0].bin_start[b + 1] - p.sp[0].bin_start[b],
@@ -1111,7 +1127,8 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p, const int 
         }
         for (int off0 = 0; off0 < span; off0 += STRIDE) {
             const int i = beg + off0 + local;
-            const bool valid = i < end;
+            // checked build: a cell index outside the grid is flagged and the particle skipped
+            const bool valid = i < end && PIC_INDEX_OK(c_n, N, p.status);
             int ix = 0, iy = 0, iz = 0, rx = -1, ry = -1, rz = -1;
             T fx = f_n[0], fy = f_n[1], fz = f_n[2], ux = u_n[0], uy = u_n[1], uz = u_n[2];
             const int c = c_n;
@@ -1147,7 +1164,11 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p, const int 
 #pragma unroll
                         for (int cc = 0; cc < NW; ++cc) wzp[cc] = Pair<T>::make(wz[cc], wz[cc]);
                         // one runtime base index; every node is a compile-time offset from it
-                        const int base0 = (rx * TE + ry) * TE + rz;
+                        int base0 = (rx * TE + ry) * TE + rz;
+#ifdef PIC_CHECKED
+                        base0 += p.inject;
+                        if (!PIC_INDEX_OK(base0, R - (NW - 1) * (TE * TE + TE + 1), p.status)) base0 = 0;
+#endif
 #pragma unroll
                         for (int a = 0; a < NW; ++a)
 #pragma unroll
@@ -1232,7 +1253,8 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p, const int 
                     SH::w(fx, wx);
                     SH::w(fy, wy);
                     SH::w(fz, wz);
-                    mJ = in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz);
+                    mJ = in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz) &&
+                         PIC_INDEX_OK((rx * TE + ry) * TE + rz, R - (NW - 1) * (TE * TE + TE + 1), p.status);
                     if (mJ) {
                         keyJ = (rx * TE + ry) * TE + rz;
                     } else {
@@ -1254,7 +1276,8 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p, const int 
                             wzR[q] = wz[q];
                         }
                     }
-                    mR = in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz);
+                    mR = in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz) &&
+                         PIC_INDEX_OK((rx * TE + ry) * TE + rz, R - (NW - 1) * (TE * TE + TE + 1), p.status);
                     if (mR) {
                         keyR = (rx * TE + ry) * TE + rz;
                     } else {
@@ -1308,7 +1331,8 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p, const int 
                     SH::w(fy, wy);
                     SH::w(fz, wz);
                     const T qvx = sp.qw_dv * vx, qvy = sp.qw_dv * vy, qvz = sp.qw_dv * vz;
-                    mJ = in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz);
+                    mJ = in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz) &&
+                         PIC_INDEX_OK((rx * TE + ry) * TE + rz, R - (NW - 1) * (TE * TE + TE + 1), p.status);
                     if (mJ) {
                         rowJ = rx * TE + ry;
                         zJ = rz;
@@ -1332,7 +1356,8 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p, const int 
                             wzR[q] = wz[q];
                         }
                     }
-                    mR = in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz);
+                    mR = in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz) &&
+                         PIC_INDEX_OK((rx * TE + ry) * TE + rz, R - (NW - 1) * (TE * TE + TE + 1), p.status);
                     if (mR) {
                         rowR = rx * TE + ry;
                         zR = rz;
@@ -1387,7 +1412,8 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p, const int 
                             val[0] = qs;
                         }
                     }
-                    if (in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz)) {
+                    if (in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz) &&
+                        PIC_INDEX_OK((rx * TE + ry) * TE + rz, R - (NW - 1) * (TE * TE + TE + 1), p.status)) {
                         member = true;
                         key = (rx * TE + ry) * TE + rz;
                         if constexpr (FIX) {
@@ -1577,7 +1603,16 @@ __device__ __forceinline__ void cell_pass_body(const PassK<T>& p, const int b) {
     __syncthreads();
 
     unsigned long long miss = 0, far = 0;
-    for (int lc = threadIdx.x; lc < BIN * BIN * BIN; lc += CELL_THREADS) {
+    const int warp = threadIdx.x >> 5;
+    // this warp's particle staging: cell[CELL_CHUNK] then off x, y, z and u x, y, z
+    unsigned char* const wst = smem_raw + L.stage + (size_t)warp * stage_bytes(NW, sizeof(T), DEP_CELL);
+    int32_t* const st_cell = reinterpret_cast<int32_t*>(wst);
+    T* const st_v = reinterpret_cast<T*>(wst + CELL_CHUNK * 4);   // [6][CELL_CHUNK]
+    // warp w takes the 32 consecutive cells (keys) 32 w .. 32 w + 31, then 256 + 32 w ..;
+    // lane t the cell 32 w + t of each group: the group's particles are one contiguous
+    // range per species, staged CELL_CHUNK at a time
+    for (int g0 = 32 * warp; g0 < BIN * BIN * BIN; g0 += CELL_THREADS) {
+        const int lc = g0 + lane;
         const int lx = lc >> 6, ly = (lc >> 3) & 7, lz = lc & 7;
         const int hx = x0 + lx, hy = y0 + ly, hz = z0 + lz;
         const int key = b * (BIN * BIN * BIN) + lc;
@@ -1594,142 +1629,182 @@ __device__ __forceinline__ void cell_pass_body(const PassK<T>& p, const int b) {
         }
         for (int s = 0; s < p.nspecies; ++s) {
             const SpeciesK<T>& sp = p.sp[s];
-            const int beg = sp.cell_start[key], end = sp.cell_start[key + 1];
-            for (int i = beg; i < end; ++i) {
-                const int c = sp.cell[i];
-                T fx = sp.off[0][i], fy = sp.off[1][i], fz = sp.off[2][i];
-                T ux = sp.u[0][i], uy = sp.u[1][i], uz = sp.u[2][i];
-                int ix = hx, iy = hy, iz = hz, rx = hrx, ry = hry, rz = hrz;
-                if (c != home) {   // moved since the sort
-                    ix = p.div_nynz.div(c);
-                    const int rem = c - ix * (p.ny * p.nz);
-                    iy = p.div_nz.div(rem);
-                    iz = rem - iy * p.nz;
-                    rx = tile_coord(ix, x0, p.nx, MARGIN);
-                    ry = tile_coord(iy, y0, p.ny, MARGIN);
-                    rz = tile_coord(iz, z0, p.nz, MARGIN);
+            int beg = sp.cell_start[key], end = sp.cell_start[key + 1];
+            // checked build: a cell range outside the species' particles is flagged and emptied
+            if (!(PIC_INDEX_OK(beg, (int64_t)sp.n + 1, p.status) && PIC_INDEX_OK(end, (int64_t)sp.n + 1, p.status) &&
+                  PIC_INDEX_OK(end - beg, (int64_t)sp.n + 1, p.status)))
+                beg = end = 0;
+            int A = __shfl_sync(0xffffffffu, beg, 0), Bend = __shfl_sync(0xffffffffu, end, 31);
+            if (!PIC_INDEX_OK(Bend - A, (int64_t)sp.n + 1, p.status)) A = Bend = 0;
+            for (int lo = A; lo < Bend; lo += CELL_CHUNK) {
+                const int hi = min(lo + CELL_CHUNK, Bend);
+                // stage in, coalesced
+                for (int j = lane; j < hi - lo; j += 32) {
+                    st_cell[j] = sp.cell[lo + j];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        st_v[d * CELL_CHUNK + j] = sp.off[d][lo + j];
+                        st_v[(3 + d) * CELL_CHUNK + j] = sp.u[d][lo + j];
+                    }
                 }
-                T wx[2], wy[2], wz[2];
-                if (MODE == PASS_STEP) {
-                    // ---- gather E^n, B^n at x^n
-                    SH::w(fx, wx);
-                    SH::w(fy, wy);
-                    SH::w(fz, wz);
-                    T E[3], B[3];
-                    if (c == home) {
-                        gather2<T, TE>(tile, hbase, wx, wy, wz, E, B);
-                    } else if (in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz)) {
-                        gather2<T, TE>(tile, (rx * TE + ry) * TE + rz, wx, wy, wz, E, B);
+                __syncwarp();
+                const int i0 = max(beg, lo), i1 = min(end, hi);
+                for (int i = i0; i < i1; ++i) {
+                    const int j = i - lo;
+                    if (!PIC_INDEX_OK(j, CELL_CHUNK, p.status)) break;
+                    const int c = st_cell[j];
+                    if (!PIC_INDEX_OK(c, N, p.status)) continue;
+                    T fx = st_v[0 * CELL_CHUNK + j], fy = st_v[1 * CELL_CHUNK + j], fz = st_v[2 * CELL_CHUNK + j];
+                    T ux = st_v[3 * CELL_CHUNK + j], uy = st_v[4 * CELL_CHUNK + j], uz = st_v[5 * CELL_CHUNK + j];
+                    int ix = hx, iy = hy, iz = hz, rx = hrx, ry = hry, rz = hrz;
+                    if (c != home) {   // moved since the sort
+                        ix = p.div_nynz.div(c);
+                        const int rem = c - ix * (p.ny * p.nz);
+                        iy = p.div_nz.div(rem);
+                        iz = rem - iy * p.nz;
+                        rx = tile_coord(ix, x0, p.nx, MARGIN);
+                        ry = tile_coord(iy, y0, p.ny, MARGIN);
+                        rz = tile_coord(iz, z0, p.nz, MARGIN);
+                    }
+                    T wx[2], wy[2], wz[2];
+                    if (MODE == PASS_STEP) {
+                        // ---- gather E^n, B^n at x^n
+                        SH::w(fx, wx);
+                        SH::w(fy, wy);
+                        SH::w(fz, wz);
+                        T E[3], B[3];
+                        int gbase = hbase;
+#ifdef PIC_CHECKED
+                        gbase += p.inject;
+                        if (!PIC_INDEX_OK(gbase, R - (TE * TE + TE + 1), p.status)) gbase = 0;
+#endif
+                        if (c == home) {
+                            gather2<T, TE>(tile, gbase, wx, wy, wz, E, B);
+                        } else if (in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz)) {
+                            gather2<T, TE>(tile, (rx * TE + ry) * TE + rz, wx, wy, wz, E, B);
+                        } else {
+                            far++;
+                            for (int q = 0; q < 3; ++q) E[q] = B[q] = (T)0;
+    #pragma unroll
+                            for (int a = 0; a < 2; ++a)
+    #pragma unroll
+                                for (int bb = 0; bb < 2; ++bb) {
+                                    const T wxy = wx[a] * wy[bb];
+                                    const int64_t gb =
+                                        ((int64_t)wrapi(ix + a, p.nx) * p.ny + wrapi(iy + bb, p.ny)) * p.nz;
+    #pragma unroll
+                                    for (int cc = 0; cc < 2; ++cc) {
+                                        const T w = wxy * wz[cc];
+                                        const int64_t g = gb + wrapi(iz + cc, p.nz);
+                                        E[0] += w * p.F[0 * N + g];
+                                        E[1] += w * p.F[1 * N + g];
+                                        E[2] += w * p.F[2 * N + g];
+                                        B[0] += w * p.F[3 * N + g];
+                                        B[1] += w * p.F[4 * N + g];
+                                        B[2] += w * p.F[5 * N + g];
+                                    }
+                                }
+                        }
+                        // ---- relativistic Boris push u^{n-1/2} -> u^{n+1/2}
+                        const T a = sp.qdt2m;
+                        const T umx = ux + a * E[0], umy = uy + a * E[1], umz = uz + a * E[2];
+                        const T igm = (T)1 / sqrt((T)1 + (umx * umx + umy * umy + umz * umz) * p.inv_c2);
+                        const T tx = a * B[0] * igm, ty = a * B[1] * igm, tz = a * B[2] * igm;
+                        const T s2 = (T)2 / ((T)1 + tx * tx + ty * ty + tz * tz);
+                        const T sx = s2 * tx, sy = s2 * ty, sz = s2 * tz;
+                        const T upx = umx + (umy * tz - umz * ty);
+                        const T upy = umy + (umz * tx - umx * tz);
+                        const T upz = umz + (umx * ty - umy * tx);
+                        ux = umx + (upy * sz - upz * sy) + a * E[0];
+                        uy = umy + (upz * sx - upx * sz) + a * E[1];
+                        uz = umz + (upx * sy - upy * sx) + a * E[2];
+                    }
+                    const T igam = (T)1 / sqrt((T)1 + (ux * ux + uy * uy + uz * uz) * p.inv_c2);
+                    const T vx = ux * igam, vy = uy * igam, vz = uz * igam;
+                    // ---- J^{n+1/2} at x^{n+1/2} with v^{n+1/2} (DEPOSIT mode: at x with v)
+                    if (MODE == PASS_STEP) {
+                        rx += drift_axis(ix, fx, (vx - p.vgal[0]) * p.hd[0], p.nx);
+                        ry += drift_axis(iy, fy, (vy - p.vgal[1]) * p.hd[1], p.ny);
+                        rz += drift_axis(iz, fz, (vz - p.vgal[2]) * p.hd[2], p.nz);
+                        SH::w(fx, wx);
+                        SH::w(fy, wy);
+                        SH::w(fz, wz);
                     } else {
-                        far++;
-                        for (int q = 0; q < 3; ++q) E[q] = B[q] = (T)0;
-#pragma unroll
+                        SH::w(fx, wx);
+                        SH::w(fy, wy);
+                        SH::w(fz, wz);
+                    }
+                    const T qv[3] = {sp.qw_dv * vx, sp.qw_dv * vy, sp.qw_dv * vz};
+                    if (rx == hrx && ry == hry && rz == hrz) {
+                        const P2 qxy = Pair<T>::make(qv[0], qv[1]);
+    #pragma unroll
                         for (int a = 0; a < 2; ++a)
-#pragma unroll
+    #pragma unroll
                             for (int bb = 0; bb < 2; ++bb) {
                                 const T wxy = wx[a] * wy[bb];
-                                const int64_t gb =
-                                    ((int64_t)wrapi(ix + a, p.nx) * p.ny + wrapi(iy + bb, p.ny)) * p.nz;
-#pragma unroll
+    #pragma unroll
                                 for (int cc = 0; cc < 2; ++cc) {
                                     const T w = wxy * wz[cc];
-                                    const int64_t g = gb + wrapi(iz + cc, p.nz);
-                                    E[0] += w * p.F[0 * N + g];
-                                    E[1] += w * p.F[1 * N + g];
-                                    E[2] += w * p.F[2 * N + g];
-                                    B[0] += w * p.F[3 * N + g];
-                                    B[1] += w * p.F[4 * N + g];
-                                    B[2] += w * p.F[5 * N + g];
+                                    const int n = (a * 2 + bb) * 2 + cc;
+                                    aJ[n] = pfma(Pair<T>::make(w, w), qxy, aJ[n]);
+                                    aZ[n] = fma(w, qv[2], aZ[n]);
                                 }
                             }
+                    } else if (in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz)) {
+                        tile_atomic2<T, TE>(sD, (rx * TE + ry) * TE + rz, wx, wy, wz, 0, 3, qv);
+                    } else {
+                        deposit_global<T, NW, 0>(p, ix, iy, iz, wx, wy, wz, 0, 3, qv);
                     }
-                    // ---- relativistic Boris push u^{n-1/2} -> u^{n+1/2}
-                    const T a = sp.qdt2m;
-                    const T umx = ux + a * E[0], umy = uy + a * E[1], umz = uz + a * E[2];
-                    const T igm = (T)1 / sqrt((T)1 + (umx * umx + umy * umy + umz * umz) * p.inv_c2);
-                    const T tx = a * B[0] * igm, ty = a * B[1] * igm, tz = a * B[2] * igm;
-                    const T s2 = (T)2 / ((T)1 + tx * tx + ty * ty + tz * tz);
-                    const T sx = s2 * tx, sy = s2 * ty, sz = s2 * tz;
-                    const T upx = umx + (umy * tz - umz * ty);
-                    const T upy = umy + (umz * tx - umx * tz);
-                    const T upz = umz + (umx * ty - umy * tx);
-                    ux = umx + (upy * sz - upz * sy) + a * E[0];
-                    uy = umy + (upz * sx - upx * sz) + a * E[1];
-                    uz = umz + (upx * sy - upy * sx) + a * E[2];
-                }
-                const T igam = (T)1 / sqrt((T)1 + (ux * ux + uy * uy + uz * uz) * p.inv_c2);
-                const T vx = ux * igam, vy = uy * igam, vz = uz * igam;
-                // ---- J^{n+1/2} at x^{n+1/2} with v^{n+1/2} (DEPOSIT mode: at x with v)
-                if (MODE == PASS_STEP) {
-                    rx += drift_axis(ix, fx, (vx - p.vgal[0]) * p.hd[0], p.nx);
-                    ry += drift_axis(iy, fy, (vy - p.vgal[1]) * p.hd[1], p.ny);
-                    rz += drift_axis(iz, fz, (vz - p.vgal[2]) * p.hd[2], p.nz);
-                    SH::w(fx, wx);
-                    SH::w(fy, wy);
-                    SH::w(fz, wz);
-                } else {
-                    SH::w(fx, wx);
-                    SH::w(fy, wy);
-                    SH::w(fz, wz);
-                }
-                const T qv[3] = {sp.qw_dv * vx, sp.qw_dv * vy, sp.qw_dv * vz};
-                if (rx == hrx && ry == hry && rz == hrz) {
-                    const P2 qxy = Pair<T>::make(qv[0], qv[1]);
-#pragma unroll
-                    for (int a = 0; a < 2; ++a)
-#pragma unroll
-                        for (int bb = 0; bb < 2; ++bb) {
-                            const T wxy = wx[a] * wy[bb];
-#pragma unroll
-                            for (int cc = 0; cc < 2; ++cc) {
-                                const T w = wxy * wz[cc];
-                                const int n = (a * 2 + bb) * 2 + cc;
-                                aJ[n] = pfma(Pair<T>::make(w, w), qxy, aJ[n]);
-                                aZ[n] = fma(w, qv[2], aZ[n]);
+                    // ---- rho^{n+1} at x^{n+1} (DEPOSIT mode: at x)
+                    if (MODE == PASS_STEP) {
+                        rx += drift_axis(ix, fx, (vx - p.vgal[0]) * p.hd[0], p.nx);
+                        ry += drift_axis(iy, fy, (vy - p.vgal[1]) * p.hd[1], p.ny);
+                        rz += drift_axis(iz, fz, (vz - p.vgal[2]) * p.hd[2], p.nz);
+                        SH::w(fx, wx);
+                        SH::w(fy, wy);
+                        SH::w(fz, wz);
+                    }
+                    const T qr[1] = {sp.qw_dv};
+                    if (rx == hrx && ry == hry && rz == hrz) {
+    #pragma unroll
+                        for (int a = 0; a < 2; ++a)
+    #pragma unroll
+                            for (int bb = 0; bb < 2; ++bb) {
+                                const T wxy = wx[a] * wy[bb];
+    #pragma unroll
+                                for (int cc = 0; cc < 2; ++cc)
+                                    aR[(a * 2 + bb) * 2 + cc] = fma(wxy * wz[cc], qr[0], aR[(a * 2 + bb) * 2 + cc]);
                             }
+                    } else if (in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz)) {
+                        tile_atomic2<T, TE>(sD, (rx * TE + ry) * TE + rz, wx, wy, wz, 3, 1, qr);
+                    } else {
+                        far++;
+                        deposit_global<T, NW, 0>(p, ix, iy, iz, wx, wy, wz, 3, 1, qr);
+                    }
+                    if (MODE == PASS_STEP) {
+                        st_cell[j] = (ix * p.ny + iy) * p.nz + iz;
+                        st_v[0 * CELL_CHUNK + j] = fx;
+                        st_v[1 * CELL_CHUNK + j] = fy;
+                        st_v[2 * CELL_CHUNK + j] = fz;
+                        st_v[3 * CELL_CHUNK + j] = ux;
+                        st_v[4 * CELL_CHUNK + j] = uy;
+                        st_v[5 * CELL_CHUNK + j] = uz;
+                        if (ix < x0 || ix >= x0 + BIN || iy < y0 || iy >= y0 + BIN || iz < z0 || iz >= z0 + BIN)
+                            miss++;
+                    }
+                }
+                __syncwarp();
+                if (MODE == PASS_STEP) {   // stage out, coalesced
+                    for (int j = lane; j < hi - lo; j += 32) {
+                        sp.cell[lo + j] = st_cell[j];
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) {
+                            sp.off[d][lo + j] = st_v[d * CELL_CHUNK + j];
+                            sp.u[d][lo + j] = st_v[(3 + d) * CELL_CHUNK + j];
                         }
-                } else if (in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz)) {
-                    tile_atomic2<T, TE>(sD, (rx * TE + ry) * TE + rz, wx, wy, wz, 0, 3, qv);
-                } else {
-                    deposit_global<T, NW, 0>(p, ix, iy, iz, wx, wy, wz, 0, 3, qv);
+                    }
                 }
-                // ---- rho^{n+1} at x^{n+1} (DEPOSIT mode: at x)
-                if (MODE == PASS_STEP) {
-                    rx += drift_axis(ix, fx, (vx - p.vgal[0]) * p.hd[0], p.nx);
-                    ry += drift_axis(iy, fy, (vy - p.vgal[1]) * p.hd[1], p.ny);
-                    rz += drift_axis(iz, fz, (vz - p.vgal[2]) * p.hd[2], p.nz);
-                    SH::w(fx, wx);
-                    SH::w(fy, wy);
-                    SH::w(fz, wz);
-                }
-                const T qr[1] = {sp.qw_dv};
-                if (rx == hrx && ry == hry && rz == hrz) {
-#pragma unroll
-                    for (int a = 0; a < 2; ++a)
-#pragma unroll
-                        for (int bb = 0; bb < 2; ++bb) {
-                            const T wxy = wx[a] * wy[bb];
-#pragma unroll
-                            for (int cc = 0; cc < 2; ++cc)
-                                aR[(a * 2 + bb) * 2 + cc] = fma(wxy * wz[cc], qr[0], aR[(a * 2 + bb) * 2 + cc]);
-                        }
-                } else if (in_tile<NW, TE>(rx) && in_tile<NW, TE>(ry) && in_tile<NW, TE>(rz)) {
-                    tile_atomic2<T, TE>(sD, (rx * TE + ry) * TE + rz, wx, wy, wz, 3, 1, qr);
-                } else {
-                    far++;
-                    deposit_global<T, NW, 0>(p, ix, iy, iz, wx, wy, wz, 3, 1, qr);
-                }
-                if (MODE == PASS_STEP) {
-                    sp.cell[i] = (ix * p.ny + iy) * p.nz + iz;
-                    sp.off[0][i] = fx;
-                    sp.off[1][i] = fy;
-                    sp.off[2][i] = fz;
-                    sp.u[0][i] = ux;
-                    sp.u[1][i] = uy;
-                    sp.u[2][i] = uz;
-                    if (ix < x0 || ix >= x0 + BIN || iy < y0 || iy >= y0 + BIN || iz < z0 || iz >= z0 + BIN)
-                        miss++;
-                }
+                __syncwarp();
             }
         }
         // the cell's accumulated nodes, once (neighbouring lanes are neighbouring cells along
@@ -1832,10 +1907,13 @@ void fill_passk(const pic_sim* s, PassK<T>& p, const void* F = nullptr, void* S 
         }
         p.sp[k].bin_start = sp.bin_start;
         p.sp[k].cell_start = sp.cell_start;
+        p.sp[k].n = (int32_t)sp.n;
         p.sp[k].qw_dv = (T)(sp.q * sp.w / dV);
         p.sp[k].qdt2m = (T)(sp.q * c.dt / (2.0 * sp.m));
     }
     p.cnt = s->cnt;
+    p.status = s->status;
+    p.inject = s->inject;
 }
 
 // Shared launches over several runs of one shape class: one CTA per (run, bin), the run's

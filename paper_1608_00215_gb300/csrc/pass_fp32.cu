@@ -1,11 +1,18 @@
-// float instantiations of the particle pass (pass.cuh).
+// float entry points of the particle pass (pass.cuh); the kernels of each tile margin are
+// instantiated in pass_fp32_m0.cu and pass_fp32_m1.cu, which compile in parallel.
 #include "pass.cuh"
 
 namespace galpic {
 
-int launch_pass_fp32(pic_sim* s, int mode, cudaStream_t st) {
-    return mode == PASS_STEP ? pass_margin<float, PASS_STEP>(s, st) : pass_margin<float, PASS_DEPOSIT>(s, st);
+int pass_fp32_margin0(pic_sim* s, int mode, cudaStream_t st, const void* descs, int nruns);
+int pass_fp32_margin1(pic_sim* s, int mode, cudaStream_t st, const void* descs, int nruns);
+
+static int dispatch(pic_sim* s, int mode, cudaStream_t st, const void* descs, int nruns) {
+    return s->d.margin == 0 ? pass_fp32_margin0(s, mode, st, descs, nruns)
+                            : pass_fp32_margin1(s, mode, st, descs, nruns);
 }
+
+int launch_pass_fp32(pic_sim* s, int mode, cudaStream_t st) { return dispatch(s, mode, st, nullptr, 0); }
 
 size_t pass_desc_bytes_fp32() { return sizeof(PassK<float>); }
 
@@ -14,8 +21,7 @@ void fill_pass_desc_fp32(const pic_sim* s, void* out, const void* F, void* S, lo
 }
 
 int launch_pass_many_fp32(pic_sim* s0, const void* descs, int nruns, cudaStream_t st) {
-    const ManyLaunch m{descs, nruns};
-    return pass_margin<float, PASS_STEP>(s0, st, &m);
+    return dispatch(s0, PASS_STEP, st, descs, nruns);
 }
 
 int pass_variant_of(const pic_sim* s) { return pass_variant(s); }

@@ -16,13 +16,18 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libgalpic.so")
+# GALPIC_CHECKED=1 loads the checked build (every kernel index tested, violations reported
+# as PIC_STATUS_BOUNDS / PIC_EBOUNDS); the default is the ordinary build.
+CHECKED = os.environ.get("GALPIC_CHECKED", "0") == "1"
+LIB_PATH = os.path.join(_HERE, "libgalpic_checked.so" if CHECKED else "libgalpic.so")
 
 PIC_OK = 0
 ERRORS = {-1: "PIC_EINVAL", -2: "PIC_ENOMEM", -3: "PIC_ECUDA", -4: "PIC_ETIMEOUT",
           -5: "PIC_ENONFINITE", -6: "PIC_EBOUNDS", -7: "PIC_ECUFFT"}
 PIC_MAX_SPECIES = 8
 PIC_STATUS_NONFINITE = 1
+PIC_STATUS_BADINPUT = 2
+PIC_STATUS_BOUNDS = 4
 
 BUF_E, BUF_B, BUF_J, BUF_RHO, BUF_E_HAT, BUF_B_HAT, BUF_RHO_HAT, BUF_SRC_HAT, BUF_TABLES, BUF_STATUS = range(10)
 
@@ -68,6 +73,8 @@ def _load():
         "pic_many_footprint": (c_int, [P, c_int, POINTER(c_size_t)]),
         "pic_step_many": (c_int, [POINTER(P), c_int, c_int, P, c_size_t, P]),
         "pic_step_coupled": (c_int, [POINTER(P), c_int, c_int, P]),
+        "pic_decomposed_footprint": (c_int, [P, c_int, c_int, POINTER(c_size_t)]),
+        "pic_step_decomposed": (c_int, [P, c_int, c_int, c_int, P, c_size_t, P]),
         "pic_diag_energy": (c_int, [P, P, P]),
         "pic_get": (c_int, [P, c_int, P, c_size_t, P]),
         "pic_set": (c_int, [P, c_int, P, c_size_t, P]),
@@ -97,7 +104,7 @@ lib = _load()
 # the exported names, as declared in include/galpic.h
 EXPORTS = ("pic_version", "pic_last_error", "pic_footprint", "pic_init", "pic_destroy", "pic_deposit",
            "pic_gather_push", "pic_field_update", "pic_step", "pic_many_footprint", "pic_step_many",
-           "pic_step_coupled", "pic_diag_energy",
+           "pic_step_coupled", "pic_decomposed_footprint", "pic_step_decomposed", "pic_diag_energy",
            "pic_get", "pic_set", "pic_get_particles", "pic_set_particles", "pic_status",
            "pic_counters", "pic_sizes", "pic_profile", "pic_profile_read", "pic_sort",
            "pic_field_energy_noalloc", "pic_add_fields", "pic_sort_policy", "pic_tune", "pic_get_line")
@@ -200,6 +207,19 @@ class Sim:
     def step(self, nsteps: int = 1):
         check(lib.pic_step(self.handle, nsteps, _stream_ptr(self.stream)))
 
+    def step_decomposed(self, ndomains: int, guard: int, nsteps: int = 1,
+                        workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """pic_step_decomposed: nsteps steps with the field update done on `ndomains`
+        z-subdomains with `guard` guard cells (all on this GPU). Returns the workspace
+        (allocated here if None) for reuse."""
+        if workspace is None:
+            n = c_size_t(0)
+            check(lib.pic_decomposed_footprint(self.handle, ndomains, guard, ctypes.byref(n)))
+            workspace = torch.empty(int(n.value), dtype=torch.uint8, device=self.device)
+        check(lib.pic_step_decomposed(self.handle, ndomains, guard, nsteps, c_void_p(workspace.data_ptr()),
+                                      workspace.numel(), _stream_ptr(self.stream)))
+        return workspace
+
     def energy_async(self, out: torch.Tensor):
         check(lib.pic_diag_energy(self.handle, c_void_p(out.data_ptr()), _stream_ptr(self.stream)))
 
@@ -286,7 +306,7 @@ class Sim:
     def status(self) -> int:
         v = c_int32()
         rc = lib.pic_status(self.handle, ctypes.byref(v))
-        if rc not in (PIC_OK, -5):
+        if rc not in (PIC_OK, -5, -6):
             check(rc)
         return int(v.value)
 
@@ -312,8 +332,15 @@ class Sim:
     def close(self):
         if self.handle:
             (self.stream if self.stream is not None else torch.cuda.current_stream()).synchronize()
+            bounds = 0
+            if CHECKED:   # the checked build: a run must end without an index violation
+                v = c_int32()
+                lib.pic_status(self.handle, ctypes.byref(v))
+                bounds = int(v.value) & PIC_STATUS_BOUNDS
             check(lib.pic_destroy(self.handle))
             self.handle = c_void_p()
+            if bounds:
+                raise GalpicError(-6, "checked build: an index left its buffer's range during this run")
 
     def __del__(self):
         try:

@@ -13,6 +13,14 @@ block scheduler starts the kernels of small runs ahead of the queued blocks of
 large ones: a small run admitted beside a large one finishes in about its own
 time instead of sharing the device evenly with it.
 
+Small runs (up to ``share_max_cells`` cells) of one shape class (grid, precision,
+shape order, tile margin, deposit strategy, species count, deterministic mode) are
+grouped into a bucket that advances in shared launches (``pic_step_many``): one
+launch per stage for all of them, one CUDA graph per bucket composition, on the
+bucket's own stream. A run joins its bucket at the bucket's next chunk after its
+admission and leaves it when it finishes; the bucket's chunk is the smallest number
+of steps any of its runs has left (at most ``chunk``).
+
 All compute goes through the CUDA library (``galpic``); this module is host
 scheduling only.
 """
@@ -63,6 +71,28 @@ class _Active:
     rec: RunRecord = None
     status: Optional[torch.Tensor] = None     # pinned int32 copy of the device status word
     level: int = 0                            # priority level (0 = largest runs)
+    bucket: Optional[tuple] = None            # shape class of a run advanced in shared launches
+
+
+@dataclass
+class _Bucket:
+    """Small runs of one shape class advanced together by pic_step_many."""
+    key: tuple
+    stream: torch.cuda.Stream
+    ws: object                                # galpic.ManyWorkspace
+    runs: List[_Active] = field(default_factory=list)
+    joining: List[_Active] = field(default_factory=list)
+    event: Optional[torch.cuda.Event] = None
+    chunk: int = 0                            # steps of the chunk in flight
+
+
+def share_key(wl, prec: int, margin: int = 1, deposit: int = 0):
+    """Shape class of runs that can share launches (None: the run is stepped alone)."""
+    ns = len(wl.species)
+    mix = ns == 2 and wl.species[0].ppc_total == wl.species[1].ppc_total
+    det = int(getattr(wl, "deterministic", 0))
+    return (wl.nx, wl.ny, wl.nz, prec, wl.shape_order, margin, deposit, ns, det,
+            mix and wl.shape_order > 1)
 
 
 def footprint(wl, precision: Optional[int] = None) -> int:
@@ -138,11 +168,31 @@ class ServeResult:
                 "max_concurrent": self.max_concurrent, "chunk_steps": self.chunk}
 
 
+def warm_shared_plans(workloads, max_slots: int = 64, share_max_cells: int = 64 * 64 * 128,
+                      precision: Optional[int] = None, device: str = "cuda"):
+    """Create the batched transform plans of shared launches (one per power-of-two run
+    count up to max_slots) for every small grid shape among the workloads, so that a
+    service does not create them while it runs."""
+    seen = set()
+    for wl in workloads:
+        key = (wl.nx, wl.ny, wl.nz, precision if precision is not None else wl.precision)
+        if key in seen or wl.nx * wl.ny * wl.nz > share_max_cells:
+            continue
+        seen.add(key)
+        sim = gp.sim_from_workload(wl, precision=precision, device=device)
+        c = 1
+        while c <= max_slots:
+            gp.many_footprint(sim, c)
+            c *= 2
+        sim.close()
+
+
 def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_slots: int = 64,
           chunk: int = 25, precision: Optional[int] = None, device: str = "cuda",
           sleep: float = 2e-4, keep_final_state: bool = False, on_retire=None,
           priorities: bool = True, admit_per_poll: int = 1,
-          max_per_level: Optional[Sequence[int]] = (2, 4, 64, 64)) -> ServeResult:
+          max_per_level: Optional[Sequence[int]] = (2, 4, 64, 64),
+          shared_launches: bool = False, share_max_cells: int = 64 * 64 * 128) -> ServeResult:
     """Run all requests with continuous batching; returns per-run records.
 
     ``max_slots = 1`` gives the serial baseline on the same arrival trace.
@@ -155,6 +205,9 @@ def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_
     ``max_per_level``: most runs of each priority level (0 = largest) active at once
     (with ``priorities``): a large run fills the GPU alone, so more of them at once add
     no throughput, only latency to every run sharing the device with them.
+    ``shared_launches``: advance runs of at most ``share_max_cells`` cells in buckets of
+    one shape class with pic_step_many (max_per_level then applies to the runs stepped
+    alone only).
     """
     prange = torch.cuda.Stream.priority_range() if priorities else (0, 0)
     if hbm_budget is None:
@@ -194,24 +247,59 @@ def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_
             a.event.record(a.stream)
         a.done += n
 
+    buckets = {}
+
+    def retire(a: _Active, ev):
+        nonlocal used
+        a.rec.finish = (ev0.elapsed_time(ev) * 1e-3 if ev is not None else time.perf_counter() - t0)
+        a.rec.status = int(a.status.item())     # copied when the last chunk was enqueued
+        if keep_final_state and on_retire is not None:
+            on_retire(a.req, a.sim)
+        a.sim.close()
+        used -= a.rec.footprint
+        active.remove(a)
+
+    def advance_bucket(bk: _Bucket):
+        """Retire the bucket's finished runs, take in the joining ones, enqueue the next chunk."""
+        if bk.event is not None:
+            for a in bk.runs:
+                a.done += bk.chunk
+            for a in [a for a in bk.runs if a.done >= a.req.steps]:
+                bk.runs.remove(a)
+                retire(a, bk.event)
+            bk.event = None
+        bk.runs += bk.joining
+        bk.joining = []
+        if not bk.runs:
+            return
+        n = min(chunk, min(a.req.steps - a.done for a in bk.runs))
+        with torch.cuda.stream(bk.stream):
+            gp.step_many([a.sim for a in bk.runs], n, workspace=bk.ws.for_runs([a.sim for a in bk.runs]),
+                         stream=bk.stream)
+            for a in bk.runs:
+                if a.done + n >= a.req.steps:
+                    a.sim.status_async(a.status)
+            bk.event = torch.cuda.Event(enable_timing=True)
+            bk.event.record(bk.stream)
+        bk.chunk = n
+
     waiting: List[Request] = []
     while qi < len(queue) or active or waiting:
         now = time.perf_counter() - t0
         # retire or advance
         for a in list(active):
+            if a.bucket is not None:
+                continue
             if a.event is not None and not a.event.query():
                 continue
             if a.done >= a.req.steps:
-                a.rec.finish = (ev0.elapsed_time(a.event) * 1e-3 if a.event is not None
-                                else time.perf_counter() - t0)
-                a.rec.status = int(a.status.item())     # copied when the last chunk was enqueued
-                if keep_final_state and on_retire is not None:
-                    on_retire(a.req, a.sim)
-                a.sim.close()
-                used -= a.rec.footprint
-                active.remove(a)
+                retire(a, a.event)
                 continue
             advance(a)
+        for bk in list(buckets.values()):
+            if bk.event is not None and not bk.event.query():
+                continue
+            advance_bucket(bk)
         # admit: arrived, slot free, footprint fits; with priorities the waiting runs
         # are taken smallest first (a run that does not fit waits, smaller ones go on)
         while qi < len(queue) and queue[qi].arrival <= now:
@@ -224,8 +312,10 @@ def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_
         while wi < len(waiting) and len(active) < max_slots and admitted < admit_per_poll:
             r = waiting[wi]
             lvl = priority_level(work[r.rid])
-            if priorities and max_per_level is not None and \
-                    sum(1 for a in active if a.level == lvl) >= max_per_level[lvl]:
+            wl = r.workload
+            shared = shared_launches and wl.nx * wl.ny * wl.nz <= share_max_cells
+            if priorities and max_per_level is not None and not shared and \
+                    sum(1 for a in active if a.level == lvl and a.bucket is None) >= max_per_level[lvl]:
                 wi += 1
                 continue
             if used + fps[r.rid] > hbm_budget:
@@ -236,7 +326,18 @@ def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_
             waiting.pop(wi)
             rec = records[r.rid]
             rec.priority = stream_priority(priority_level(pushes(r.workload, r.steps)), prange)
-            stream = torch.cuda.Stream(priority=rec.priority)
+            if shared:
+                admitted -= 1          # joining a bucket is cheap: admit every waiting run that fits
+            bk = None
+            if shared:
+                key = share_key(wl, precision if precision is not None else wl.precision)
+                bk = buckets.get(key)
+                if bk is None:
+                    bk = _Bucket(key, torch.cuda.Stream(priority=rec.priority), gp.ManyWorkspace(device))
+                    buckets[key] = bk
+                stream = bk.stream
+            else:
+                stream = torch.cuda.Stream(priority=rec.priority)
             try:
                 with torch.cuda.stream(stream):
                     sim = gp.sim_from_workload(r.workload, precision=precision, stream=stream, device=device)
@@ -246,13 +347,19 @@ def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_
             rec.start = time.perf_counter() - t0
             used += fps[r.rid]
             a = _Active(r, sim, stream, 0, None, rec, torch.zeros(1, dtype=torch.int32).pin_memory(),
-                        priority_level(work[r.rid]))
+                        priority_level(work[r.rid]), bk.key if bk is not None else None)
             active.append(a)
             admitted += 1
             max_conc = max(max_conc, len(active))
-            if r.steps > 0:
+            if bk is not None:
+                bk.joining.append(a)   # enters at the bucket's next chunk
+                if bk.event is None:
+                    advance_bucket(bk)
+            elif r.steps > 0:
                 advance(a)     # its first chunk starts while the next runs are admitted
-        if active and not admitted and all(a.event is not None and not a.event.query() for a in active):
+        busy = all(a.event is not None and not a.event.query() for a in active if a.bucket is None) and \
+            all(bk.event is not None and not bk.event.query() for bk in buckets.values() if bk.runs or bk.joining)
+        if active and not admitted and busy:
             time.sleep(sleep)
         elif not active and not waiting and qi < len(queue):
             wait = queue[qi].arrival - (time.perf_counter() - t0)

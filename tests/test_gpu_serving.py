@@ -91,3 +91,30 @@ def test_percentiles_nearest_rank(gpmod):
     recs = [serve.RunRecord(i, 0.0, 0.0, float(i + 1)) for i in range(200)]
     r = serve.ServeResult(recs, 10.0, 1, 1)
     assert r.percentile(50) == 100.0 and r.percentile(99) == 198.0 and r.percentile(100) == 200.0
+
+
+def test_alone_equals_mix_with_shared_launches(gpmod):
+    """Small runs of one shape advance in shared launches (pic_step_many buckets), joining
+    and leaving their bucket at different steps; each result equals the run alone (1e-4)."""
+    gp, serve = gpmod
+    specs = [((16, 16, 16), 130.0, True, (1, 1, 2), 20), ((16, 16, 16), 10.0, False, (1, 1, 1), 30),
+             ((16, 16, 16), 30.0, True, (2, 2, 2), 15), ((16, 16, 32), 5.0, False, (1, 2, 2), 25),
+             ((16, 16, 32), 130.0, False, (1, 1, 3), 20), ((16, 16, 16), 10.0, True, (2, 1, 1), 35),
+             ((24, 20, 18), 30.0, True, (1, 2, 2), 10)]
+    lattices = {1: (1, 1, 1)}
+    reqs = []
+    for k, (g, gamma, gal, lat, steps) in enumerate(specs):
+        wl = gi.drifting_plasma(*g, gamma, galilean=gal, shape_order=1, precision=32, ppc=lat, jitter=0.05,
+                                seed=300 + k)
+        reqs.append(serve.Request(k, wl, steps, arrival=0.003 * k))
+    mixed = {}
+    res = serve.serve(reqs, max_slots=8, chunk=7, keep_final_state=True, shared_launches=True,
+                      on_retire=lambda r, s: mixed.__setitem__(r.rid, _fields(s)))
+    assert all(r.error is None for r in res.records), [r.error for r in res.records]
+    for r in reqs:
+        sim = gp.sim_from_workload(r.workload)
+        sim.step(r.steps)
+        alone = _fields(sim)
+        sim.close()
+        err = np.linalg.norm(alone - mixed[r.rid]) / np.linalg.norm(alone)
+        assert err < 1e-4, (r.rid, err)
