@@ -141,3 +141,48 @@ def test_nci_absent_at_vgal_equal_drift_and_present_at_zero():
     assert ratios[False][-1] >= 1e3
     slope = np.polyfit(np.arange(151)[50:], np.log(ratios[False][50:]), 1)[0]
     assert slope > 0.02
+
+
+def _thermal_column_energy(nmodes, steps, seed=5):
+    """Field energy after `steps` steps of a neutral plasma column at rest (electrons with
+    a thermal spread of 0.02 c, protons cold at the same places, so rho^0 = 0), modes
+    0 .. nmodes-1, on a 16 x 16 grid."""
+    nr, nz = 16, 16
+    base = cyl.CylConfig(nr, nz, dr=1.0, dz=1.0, dt=1.0, c=1.0, eps0=1.0)
+    cfgs = cp.mode_configs(base, nmodes)
+    rng = np.random.default_rng(seed)
+    n = 2000
+    R = 0.7 * (nr - 1)
+    r, th = R * np.sqrt(rng.random(n)), 2 * np.pi * rng.random(n)
+    x, y, z = r * np.cos(th), r * np.sin(th), nz * rng.random(n)
+    w = np.full(n, 0.04 * np.pi * R * R * nz / n)           # density 0.04: omega_p dt = 0.2
+    u = [0.02 * rng.standard_normal(n) for _ in range(3)]
+    zero = np.zeros(n)
+    species = [cp.CylSpecies(-1.0, 1.0, w, x, y, z, *u),
+               cp.CylSpecies(1.0, 1836.0, w, x.copy(), y.copy(), z.copy(), zero, zero.copy(), zero.copy())]
+    st = cp.init_state(cfgs, species, 0.0)
+    for _ in range(steps):
+        cp.step(cfgs, st)
+    return cp.energy(cfgs, st)
+
+
+def test_thermal_plasma_stays_at_the_noise_level():
+    """With modes 0 .. 2 the field energy of a neutral thermal column after 20 steps stays
+    within a small factor of the mode-0-only run (more modes carry more of the same
+    noise); the forward transforms of orders |n| >= 2 are the Hankel quadrature."""
+    w1 = _thermal_column_energy(1, 20)
+    w3 = _thermal_column_energy(3, 20)
+    assert 0 < w1 and w3 < 10 * w1
+
+
+def test_exact_inverse_for_every_order_is_unstable(monkeypatch):
+    """The planted alternative: forward transforms of every order taken as the synthesis
+    inverse. The same column's field energy then runs away (the orders |n| >= 2 amplify
+    the deposit's irregular part at the axis), which the previous pin would catch."""
+    def exact(cfg, f, n):
+        A = cyl._synthesis(cfg, n)
+        return np.linalg.solve(A, f.reshape(cfg.nr, -1)).reshape(f.shape)
+    w1 = _thermal_column_energy(1, 8)
+    monkeypatch.setattr(cyl, "dht", exact)
+    w3 = _thermal_column_energy(3, 8)
+    assert w3 > 100 * w1
