@@ -174,6 +174,8 @@ def pass_kernel_name(order, margin, deposit, equal_pair):
     choice: three CTAs per SM for linear shapes and for the grouped quadratic/cubic
     deposit at tile margin 0, two for the row and combined-J-and-rho deposits; two
     species of equal size share groups in the grouped and combined deposits."""
+    if order == 1 and deposit == 4:
+        return f"cell_pass_kernel<float,STEP,{margin}>"
     dep = ("GROUP", "ROW", "JR", "ROWU")[deposit] if order > 1 else "GROUP"
     if order == 1 or (margin == 0 and dep == "GROUP"):
         suffix = "_3"
@@ -183,6 +185,42 @@ def pass_kernel_name(order, margin, deposit, equal_pair):
         suffix = ""
     mixed = equal_pair and order > 1 and dep in ("GROUP", "JR")
     return f"particle_pass_kernel{suffix}<float,{order},STEP,{margin},{dep}{',mixed' if mixed else ''}>"
+
+
+def linear_pass_roofline(grid, steps, warmup, hbm, peak_kind):
+    """HBM roofline of the linear-shape particle pass on the same plasma and grid (the
+    config-1 shape order at the bench's size): a run of its own, tuned by pic_tune, timed
+    over `steps` steps with the library's stage events."""
+    import torch
+    from paper_1608_00215_gb300 import galpic as gp
+    wl = workload(grid, order=1)
+    sim = gp.sim_from_workload(wl, precision=32)
+    tuned = sim.tune()
+    for _ in range(warmup):
+        sim.gather_push()
+        sim.field_update()
+    torch.cuda.synchronize()
+    sim.profile(True)
+    for _ in range(steps):
+        sim.gather_push()
+        sim.field_update()
+    torch.cuda.synchronize()
+    stages = sim.profile_read()
+    sim.profile(False)
+    status = sim.status()
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    part = stages["particles"]
+    part_ms = part["ms"] / max(1, part["count"])
+    nbytes = particle_bytes(wl, 32)
+    achieved = nbytes / (part_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": pass_kernel_name(1, tuned["tile_margin"], tuned["deposit"], True),
+            "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+            "peak_kind": peak_kind, "algorithmic_bytes_per_launch": nbytes, "ms_per_launch": part_ms,
+            "ms_per_step": sum(v["ms"] / max(1, v["count"]) for v in stages.values() if v["count"]),
+            "tuned": tuned, "workload": wl.name + " (linear shapes, otherwise the bench plasma)",
+            "device_status": status}
 
 
 def kspace_bytes(wl, precision):
@@ -364,6 +402,8 @@ def run_ours(args, rank, world, local_rank):
         # small-run-heavy trace (32^3 and 64^3 grids only): where launches dominate
         line["serving_small_runs"] = serving_bench(args.serving_requests, args.serving_steps,
                                                    grids=[(32, 32, 32), (64, 64, 64)])
+    if args.order > 1 and not args.no_linear and world == 1:
+        line["roofline_linear"] = linear_pass_roofline(grid, 5, 3, hbm, peak_kind)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(stencil_order=args.stencil_order)
     print(json.dumps(line), flush=True)
@@ -748,6 +788,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--no-linear", action="store_true",
+                    help="skip the roofline_linear leg (the linear-shape pass on the same grid)")
     ap.add_argument("--grid", default=",".join(str(x) for x in GRID),
                     help="nx,ny,nz of the drifting plasma (default: the 256x256x512 workload)")
     ap.add_argument("--order", type=int, default=3, help="shape order (default 3)")

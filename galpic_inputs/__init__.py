@@ -445,3 +445,65 @@ def bunch_particles(wl: Workload):
     zeros = np.zeros(b.n_macro)
     return {"q": -1.0, "m": 1.0, "w": b.charge / b.n_macro, "cell": cell, "off": [fx, fy, fz],
             "u": [zeros, zeros.copy(), np.full(b.n_macro, uz)]}
+
+
+@dataclass
+class CylWorkload:
+    """A quasi-cylindrical run: grid, time step, modes and explicit particles (FP64 arrays).
+    ``species``: dicts with q, m and arrays w, x, y, z, ux, uy, uz."""
+    name: str
+    nr: int
+    nz: int
+    nmodes: int
+    dr: float
+    dz: float
+    dt: float
+    vgal: float
+    c: float
+    eps0: float
+    beta_init: float
+    species: List[dict]
+
+
+def cylindrical_plasma(nr: int, nz: int, gamma: float, *, nmodes: int = 3, ppc: int = 4, dr: float = 1.0,
+                       dz: float = 1.0, dt: Optional[float] = None, c: float = 1.0, eps0: float = 1.0,
+                       n0: float = 1.0, spread: float = 0.05, fill: float = 0.8, seed: int = 1,
+                       galilean: bool = True, electron_only: bool = False) -> CylWorkload:
+    """Electron(-proton) plasma column drifting along +z at Lorentz factor ``gamma``, inside
+    radius fill * (nr - 1) dr, with azimuthal structure: the electrons' cross-section is an
+    ellipse (semi-axes 1 and 0.8 of the column radius) shifted by 0.1 of that radius along
+    x, so modes 1 and 2 carry charge. Positions are uniform in area and in z (seeded numpy
+    PCG64), ppc macro-particles per (r, z) cell of the column's area on average, momenta the
+    drift plus a Gaussian spread of ``spread`` times u_drift per axis. Weights make the
+    density n0. dt defaults to dz / c; v_gal = v_drift when ``galilean``."""
+    rng = np.random.default_rng(seed)
+    u = drift_u(gamma, c)
+    R = fill * (nr - 1) * dr
+    L = nz * dz
+    area_cells = math.pi * R * R / (dr * dr)
+    n = max(1, int(round(ppc * area_cells * nz / (2.0 * nr))))   # the column's cells as (r, z) cells
+    w = n0 * math.pi * R * R * L / n
+
+    def column(a, b, shift):
+        r = np.sqrt(rng.random(n))
+        th = 2 * np.pi * rng.random(n)
+        x = R * (shift + a * r * np.cos(th))
+        y = R * b * r * np.sin(th)
+        return x, y, L * rng.random(n)
+
+    def momenta():
+        return (spread * u * rng.standard_normal(n), spread * u * rng.standard_normal(n),
+                u + spread * u * rng.standard_normal(n))
+
+    species = []
+    x, y, z = column(0.85, 0.68, 0.1)
+    ux, uy, uz = momenta()
+    species.append(dict(q=-1.0, m=1.0, w=np.full(n, w), x=x, y=y, z=z, ux=ux, uy=uy, uz=uz))
+    if not electron_only:
+        x, y, z = column(1.0, 1.0, 0.0)
+        ux, uy, uz = momenta()
+        species.append(dict(q=1.0, m=PROTON_MASS_RATIO, w=np.full(n, w), x=x, y=y, z=z, ux=ux, uy=uy, uz=uz))
+    return CylWorkload(name=f"cylindrical_plasma_{nr}x{nz}_m{nmodes}_g{gamma:g}", nr=nr, nz=nz, nmodes=nmodes,
+                       dr=dr, dz=dz, dt=dz / c if dt is None else dt, c=c, eps0=eps0,
+                       vgal=drift_v(gamma, c) if galilean else 0.0, beta_init=drift_v(gamma, c) / c,
+                       species=species)

@@ -412,6 +412,97 @@ int pic_sizes(pic_sim* sim, int64_t* n_cells, int64_t* n_modes);
 int pic_field_energy_noalloc(const void* fields, int64_t n_cells, int precision, double eps0, double c,
                              double dV, double* out_dev, void* stream);
 
+/* ---- Quasi-cylindrical geometry ---------------------------------------------------------
+ *
+ * The paper runs its boosted-frame results in a quasi-cylindrical spectral code (the
+ * implementation paragraph after the update equations): fields are azimuthal modes
+ * F(r, theta, z) = F_0 + 2 Re sum_{m=1}^{M-1} F_m(r, z) e^{i m theta} on radial nodes
+ * r_j = (j + 1/2) dr (j < nr) and axial nodes z_l = l dz (l < nz, periodic, Galilean
+ * coordinate). The paper prints no formulas for this geometry; the readings are:
+ *   - Spectral state of mode m: the Cartesian amplitudes at phi = 0, for a vector
+ *     F_x + i F_y = -i H_{m+1}[F_r + i F_theta], F_x - i F_y = i H_{m-1}[F_r - i F_theta],
+ *     F_z = H_m[F_z]; scalars H_m[g]; H_n the discrete Hankel transform of order n on the
+ *     spectral nodes k_i = alpha_i / R (alpha_i the zeros of J_b, b = max(m - 1, 0),
+ *     R = nr dr; inverse transform f(r_j) = sum_i w_i J_n(k_i r_j) F_i with
+ *     w_i = 2 / (R^2 J_{b+1}(alpha_i)^2); forward transform: that matrix's inverse for
+ *     |n| <= 1, the midpoint quadrature sum_j f(r_j) J_n(k_i r_j) r_j dr of the Hankel
+ *     integral for |n| >= 2), times the FFT along z (forward e^{-i k_z z}); the Nyquist
+ *     plane of an even nz is held at zero.
+ *   - Field update: the Galilean-PSATD update (v_gal along z) at k = (k_r, 0, k_z) on
+ *     these amplitudes, with FP64-built factors, current correction optional.
+ *   - Particles: Cartesian positions (x, y, z) and momenta u = gamma v, Boris push and
+ *     Galilean drift as in the Cartesian step; linear shapes in r and z; mode deposits
+ *     sum q w S_r S_z e^{-i m theta} / V_j with V_j = 2 pi r_j dr dz; the node below the
+ *     axis folds onto node 0 with factor (-1)^m (scalars, z components) or (-1)^(m+1)
+ *     (r, theta components). Every particle must satisfy r < (nr - 1/2) dr.
+ * Memory follows the Cartesian API: one caller-owned device workspace of
+ * pic_cyl_footprint() bytes; the handle owns its cuFFT plans and host struct. */
+typedef struct pic_cyl pic_cyl;
+
+typedef struct {
+    double dr, dz;        /* radial and axial spacing */
+    double dt;
+    double vgal;          /* Galilean velocity along z */
+    double c, eps0;
+    double beta_init;     /* initial fields: the boosted-Coulomb field of rho^0 moving at
+                             beta_init c along z (0: electrostatic field of rho^0) */
+    int32_t nr, nz;       /* 2 <= nr <= 1024, nz >= 2 */
+    int32_t nmodes;       /* azimuthal modes kept, 1 .. 4 */
+    int32_t precision;    /* 32 or 64 (transform matrices and factors built in FP64) */
+    int32_t current_correction;
+    int32_t pad_;
+} pic_cyl_config;
+
+typedef struct {
+    double q, m;          /* charge and mass of one physical particle */
+    int64_t n;            /* macro-particles, 0 .. 2^31 - 1 */
+    const void* w;        /* n macro weights (reals of the run's precision; host or device) */
+    const void* x[3];     /* n positions x, y, z (z in [0, nz dz)) */
+    const void* u[3];     /* n momenta per mass u_x, u_y, u_z */
+} pic_cyl_species;
+
+enum pic_cyl_buffer {
+    PIC_CYL_EB_HAT = 0,   /* spectral E, B: [M][6][nr][nz] complex (E_x, E_y, E_z, B_x, B_y, B_z) */
+    PIC_CYL_RHO_HAT = 1,  /* spectral rho^n: [M][nr][nz] complex */
+    PIC_CYL_FIELDS = 2,   /* real-space mode fields: [M][6][nr][nz] complex (E_r, E_theta, E_z,
+                             B_r, B_theta, B_z) */
+    PIC_CYL_SOURCES = 3,  /* last deposits: [M][4][nr][nz] complex (J_r, J_theta, J_z at
+                             (n+1/2) dt, rho at (n+1) dt) */
+    PIC_CYL_K = 4,        /* wavenumbers of each mode: [M][nr + 1 + nz] double: k_r, 0, k_z */
+    PIC_CYL_STATUS = 5    /* the device status word (int32, PIC_STATUS_* bits) */
+};
+
+/* Workspace bytes of a quasi-cylindrical run (creates and destroys its cuFFT plans).
+ * Errors: PIC_EINVAL (configuration out of range), PIC_ECUFFT. */
+int pic_cyl_footprint(const pic_cyl_config* cfg, const pic_cyl_species* species, int nspecies,
+                      size_t* bytes_out);
+
+/* Create a run in `workspace` (device, 256-byte aligned, >= pic_cyl_footprint()):
+ * copies the particles, builds the Bessel zeros, transform matrices (FP64; Gauss-Jordan
+ * inverses for the orders |n| <= 1) and update factors on the GPU, deposits rho^0 and sets the initial fields.
+ * Synchronises `stream`. Errors: PIC_EINVAL (also when a particle lies outside the
+ * radial extent or a transform matrix is singular), PIC_ENOMEM, PIC_ECUDA, PIC_ECUFFT. */
+int pic_cyl_init(const pic_cyl_config* cfg, const pic_cyl_species* species, int nspecies,
+                 void* workspace, size_t ws_bytes, void* stream, pic_cyl** out);
+
+/* Advance nsteps steps: gather at x^n, Boris push, half drift, J^{n+1/2}, half drift,
+ * rho^{n+1}; forward transforms; Galilean-PSATD update of every mode; inverse
+ * transforms. A particle that leaves the radial extent sets PIC_STATUS_BADINPUT and
+ * is not deposited. Asynchronous on `stream`. */
+int pic_cyl_step(pic_cyl* run, int nsteps, void* stream);
+
+/* Copy a PIC_CYL_* buffer to dst (host or device); `bytes` must equal its size. */
+int pic_cyl_get(pic_cyl* run, int which, void* dst, size_t bytes, void* stream);
+
+/* Copy species k's positions and momenta out (any pointer may be NULL). */
+int pic_cyl_get_particles(pic_cyl* run, int species, void* x[3], void* u[3], void* stream);
+
+/* Field energy W = (eps0/2) sum_m (1 for m = 0, else 2) sum_{j,l} (|E_m|^2 + c^2 |B_m|^2) V_j
+ * of the real mode fields, one double written to the DEVICE address out_dev. */
+int pic_cyl_energy(pic_cyl* run, double* out_dev, void* stream);
+
+int pic_cyl_destroy(pic_cyl* run);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,8 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libgalpic.so")
 LIB_CHECKED = os.path.join(HERE, "libgalpic_checked.so")
 SOURCES = ("pass_fp32_m0.cu", "pass_fp32_m1.cu", "pass_fp64_m0.cu", "pass_fp64_m1.cu", "pass_fp32.cu",
-           "pass_fp64.cu", "particles.cu", "api.cu", "fields.cu", "noalloc.cu", "many.cu", "decomp.cu")
+           "pass_fp64.cu", "particles.cu", "api.cu", "fields.cu", "noalloc.cu", "many.cu", "decomp.cu",
+           "cyl.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")

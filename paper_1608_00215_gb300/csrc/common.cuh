@@ -262,6 +262,13 @@ int launch_kspace_windows(const pic_sim* s, const void* descs, int nwin, int64_t
 // The mutex that serialises the set-stream / set-work-area / execute sequence of a run's
 // shared single-run cuFFT plans (api.cu).
 std::mutex* plan_mutex(pic_sim* s);
+// Quasi-cylindrical modes (cyl.cu): factors at k = (k_r, 0, k_z) from K = [k_r (nr), 0,
+// k_z (nz)], the k-space parameters of one mode, and the k-space launch over n modes.
+int launch_cyl_tables(int precision, int nr, int nz, const double* K, void* tab, double dt, double vgal, double c,
+                      double eps0, int cc, cudaStream_t st);
+void fill_cyl_kspace_desc(int precision, void* out, int nr, int nz, void* EBh, const void* Sh, void* Rn,
+                          void* scratch, const void* tab, const void* Kt, double c, int cc);
+int launch_kspace_descs(int precision, const void* descs, int n, int64_t M, cudaStream_t st);
 // Pieces of the single-run step that the decomposed step reuses (api.cu).
 int gather_push_stage(pic_sim* s, cudaStream_t st);
 int r2c_on(pic_sim* s, void* in, void* out, cudaStream_t st);

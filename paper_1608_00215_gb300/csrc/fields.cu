@@ -250,12 +250,19 @@ struct KParams {
     T invN;
     T bg[3];          // N rho_bg v_gal: background current at k = 0
     int cc;
-    int keep_nyquist; // 1: update the Nyquist planes like any mode (decomposed windows)
+    int nyq_mask;     // Nyquist planes held at zero: bit 0 x, bit 1 y, bit 2 z (7 for a run;
+                      // 0 for decomposed windows; 4 for quasi-cylindrical modes, whose first
+                      // axis is the radial spectrum)
 };
 
 __device__ __forceinline__ bool is_nyquist(int mx, int my, int mz, int nx, int ny, int nz) {
     return ((nx & 1) == 0 && mx == nx / 2) || ((ny & 1) == 0 && my == ny / 2) ||
            ((nz & 1) == 0 && mz == nz / 2);
+}
+
+__device__ __forceinline__ bool is_nyquist_masked(int mx, int my, int mz, int nx, int ny, int nz, int mask) {
+    return ((mask & 1) && (nx & 1) == 0 && mx == nx / 2) || ((mask & 2) && (ny & 1) == 0 && my == ny / 2) ||
+           ((mask & 4) && (nz & 1) == 0 && mz == nz / 2);
 }
 
 // One thread per mode: reads E, B, J, rho^{n+1}, rho^n and the six factors;
@@ -271,7 +278,7 @@ __device__ __forceinline__ void kspace_update_body(const KParams<T>& p) {
         int64_t r = m / p.nzh;
         int my = (int)(r % p.ny);
         int mx = (int)(r / p.ny);
-        if (!p.keep_nyquist && is_nyquist(mx, my, mz, p.nx, p.ny, p.nz)) {
+        if (is_nyquist_masked(mx, my, mz, p.nx, p.ny, p.nz, p.nyq_mask)) {
             C z = mk<C>(0.0, 0.0);
 #pragma unroll
             for (int q = 0; q < 6; ++q) {
@@ -591,6 +598,7 @@ static void fill_kparams(const pic_sim* s, KParams<T>& p, void* EBs, const void*
     p.invN = (T)(1.0 / (double)s->d.N);
     for (int d = 0; d < 3; ++d) p.bg[d] = (T)((double)s->d.N * c.rho_bg * c.vgal[d]);
     p.cc = c.current_correction;
+    p.nyq_mask = 7;
 }
 
 template <typename T>
@@ -664,7 +672,7 @@ static void fill_window_kparams(const pic_sim* s, KParams<T>& p, int nz_w, void*
     p.invN = (T)(1.0 / (double)N);
     for (int d = 0; d < 3; ++d) p.bg[d] = (T)((double)N * c.rho_bg * c.vgal[d]);
     p.cc = c.current_correction;
-    p.keep_nyquist = 1;
+    p.nyq_mask = 0;
 }
 
 void fill_window_kspace_desc(const pic_sim* s, void* out, int nz_w, void* spec, void* ebs, const void* Kt,
@@ -681,6 +689,65 @@ int launch_kspace_windows(const pic_sim* s, const void* descs, int nwin, int64_t
         kspace_update_many_kernel<double><<<dim3(gx, nwin), 256, 0, st>>>((const KParams<double>*)descs);
     else
         kspace_update_many_kernel<float><<<dim3(gx, nwin), 256, 0, st>>>((const KParams<float>*)descs);
+    GP_CUDA(cudaGetLastError());
+    return PIC_OK;
+}
+
+// Quasi-cylindrical modes: per-mode factors at k = (k_r, 0, k_z) (no mirror symmetry along
+// the radial spectrum) and the k-space parameters of one mode's arrays.
+int launch_cyl_tables(int precision, int nr, int nz, const double* K, void* tab, double dt, double vgal, double c,
+                      double eps0, int cc, cudaStream_t st) {
+    GaussLegendre gl = gauss_legendre();
+    const int64_t M = (int64_t)nr * nz;
+    const int grid = grid_for(M, 128);
+    if (precision == 64)
+        build_tables_kernel<double2><<<grid, 128, 0, st>>>((double2*)tab, K, nr, 1, nz, nz, M, dt, 0.0, 0.0, vgal, c,
+                                                           eps0, cc, gl, 0, 0);
+    else
+        build_tables_kernel<float2><<<grid, 128, 0, st>>>((float2*)tab, K, nr, 1, nz, nz, M, dt, 0.0, 0.0, vgal, c,
+                                                          eps0, cc, gl, 0, 0);
+    GP_CUDA(cudaGetLastError());
+    return PIC_OK;
+}
+
+template <typename T>
+static void fill_cyl_kparams(KParams<T>& p, int nr, int nz, void* EBh, const void* Sh, void* Rn, void* scratch,
+                             const void* tab, const void* Kt, double c, int cc) {
+    typedef typename cplx<T>::type C;
+    memset(&p, 0, sizeof(p));
+    p.EBh = (C*)EBh;
+    p.EBs = (C*)scratch;
+    p.Sh = (const C*)Sh;
+    p.Rn = (C*)Rn;
+    p.tab = (const C*)tab;
+    p.M = (int64_t)nr * nz;
+    p.nx = nr;
+    p.ny = 1;
+    p.nz = nz;
+    p.nzh = nz;
+    p.kx = (const T*)Kt;
+    p.ky = p.kx + nr;
+    p.kz = p.ky + 1;
+    p.c2 = (T)(c * c);
+    p.invN = (T)1;
+    p.cc = cc;
+    p.nyq_mask = 4;
+}
+
+void fill_cyl_kspace_desc(int precision, void* out, int nr, int nz, void* EBh, const void* Sh, void* Rn,
+                          void* scratch, const void* tab, const void* Kt, double c, int cc) {
+    if (precision == 64)
+        fill_cyl_kparams<double>(*static_cast<KParams<double>*>(out), nr, nz, EBh, Sh, Rn, scratch, tab, Kt, c, cc);
+    else
+        fill_cyl_kparams<float>(*static_cast<KParams<float>*>(out), nr, nz, EBh, Sh, Rn, scratch, tab, Kt, c, cc);
+}
+
+int launch_kspace_descs(int precision, const void* descs, int n, int64_t M, cudaStream_t st) {
+    const int gx = std::max(1, grid_for(M, 256) / std::max(1, std::min(n, 16)));
+    if (precision == 64)
+        kspace_update_many_kernel<double><<<dim3(gx, n), 256, 0, st>>>((const KParams<double>*)descs);
+    else
+        kspace_update_many_kernel<float><<<dim3(gx, n), 256, 0, st>>>((const KParams<float>*)descs);
     GP_CUDA(cudaGetLastError());
     return PIC_OK;
 }

@@ -49,6 +49,21 @@ class PicSpecies(ctypes.Structure):
                 ("u", c_void_p * 3)]
 
 
+class PicCylConfig(ctypes.Structure):
+    _fields_ = [("dr", c_double), ("dz", c_double), ("dt", c_double), ("vgal", c_double), ("c", c_double),
+                ("eps0", c_double), ("beta_init", c_double), ("nr", c_int32), ("nz", c_int32),
+                ("nmodes", c_int32), ("precision", c_int32), ("current_correction", c_int32),
+                ("pad_", c_int32)]
+
+
+class PicCylSpecies(ctypes.Structure):
+    _fields_ = [("q", c_double), ("m", c_double), ("n", c_int64), ("w", c_void_p), ("x", c_void_p * 3),
+                ("u", c_void_p * 3)]
+
+
+CYL_EB_HAT, CYL_RHO_HAT, CYL_FIELDS, CYL_SOURCES, CYL_K, CYL_STATUS = range(6)
+
+
 class GalpicError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{ERRORS.get(code, code)}: {msg}")
@@ -91,6 +106,14 @@ def _load():
         "pic_profile_read": (c_int, [P, POINTER(c_double), POINTER(c_int64)]),
         "pic_sizes": (c_int, [P, POINTER(c_int64), POINTER(c_int64)]),
         "pic_field_energy_noalloc": (c_int, [P, c_int64, c_int, c_double, c_double, c_double, P, P]),
+        "pic_cyl_footprint": (c_int, [POINTER(PicCylConfig), POINTER(PicCylSpecies), c_int, POINTER(c_size_t)]),
+        "pic_cyl_init": (c_int, [POINTER(PicCylConfig), POINTER(PicCylSpecies), c_int, P, c_size_t, P,
+                                 POINTER(P)]),
+        "pic_cyl_step": (c_int, [P, c_int, P]),
+        "pic_cyl_get": (c_int, [P, c_int, P, c_size_t, P]),
+        "pic_cyl_get_particles": (c_int, [P, c_int, POINTER(P), POINTER(P), P]),
+        "pic_cyl_energy": (c_int, [P, P, P]),
+        "pic_cyl_destroy": (c_int, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -107,7 +130,9 @@ EXPORTS = ("pic_version", "pic_last_error", "pic_footprint", "pic_init", "pic_de
            "pic_step_coupled", "pic_decomposed_footprint", "pic_step_decomposed", "pic_diag_energy",
            "pic_get", "pic_set", "pic_get_particles", "pic_set_particles", "pic_status",
            "pic_counters", "pic_sizes", "pic_profile", "pic_profile_read", "pic_sort",
-           "pic_field_energy_noalloc", "pic_add_fields", "pic_sort_policy", "pic_tune", "pic_get_line")
+           "pic_field_energy_noalloc", "pic_add_fields", "pic_sort_policy", "pic_tune", "pic_get_line",
+           "pic_cyl_footprint", "pic_cyl_init", "pic_cyl_step", "pic_cyl_get", "pic_cyl_get_particles",
+           "pic_cyl_energy", "pic_cyl_destroy")
 
 STAGES = ("sort", "particles", "fft_r2c", "kspace", "fft_c2r", "energy")
 
@@ -341,6 +366,85 @@ class Sim:
             self.handle = c_void_p()
             if bounds:
                 raise GalpicError(-6, "checked build: an index left its buffer's range during this run")
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class CylSim:
+    """One quasi-cylindrical run (pic_cyl_*): owns its device workspace and the handle.
+    species: dicts with q, m and arrays w, x, y, z, ux, uy, uz (numpy or torch, any device),
+    each converted to the run's precision."""
+
+    def __init__(self, *, nr: int, nz: int, nmodes: int, dr=1.0, dz=1.0, dt=1.0, vgal=0.0, c=1.0, eps0=1.0,
+                 beta_init=0.0, precision=64, current_correction=True, species=(), stream=None, device="cuda"):
+        self.cfg = PicCylConfig(dr=dr, dz=dz, dt=dt, vgal=vgal, c=c, eps0=eps0, beta_init=beta_init, nr=nr,
+                                nz=nz, nmodes=nmodes, precision=precision,
+                                current_correction=int(bool(current_correction)), pad_=0)
+        self.real = torch.float64 if precision == 64 else torch.float32
+        self.cplx = torch.complex128 if precision == 64 else torch.complex64
+        self.device = device
+        self.stream = stream
+        keep, sps = [], []
+        for sp in species:
+            arrs = [torch.as_tensor(np.asarray(sp[k]) if not torch.is_tensor(sp[k]) else sp[k])
+                    .to(device=device, dtype=self.real).contiguous() for k in ("w", "x", "y", "z", "ux", "uy", "uz")]
+            keep.append(arrs)
+            n = arrs[0].numel()
+            ptr = [c_void_p(a.data_ptr()) for a in arrs]
+            sps.append(PicCylSpecies(q=sp["q"], m=sp["m"], n=n, w=ptr[0], x=(c_void_p * 3)(*ptr[1:4]),
+                                     u=(c_void_p * 3)(*ptr[4:7])))
+        self.n = [int(s.n) for s in sps]
+        arr = (PicCylSpecies * max(1, len(sps)))(*sps)
+        nbytes = c_size_t(0)
+        check(lib.pic_cyl_footprint(ctypes.byref(self.cfg), arr, len(sps), ctypes.byref(nbytes)))
+        self.footprint = int(nbytes.value)
+        self.workspace = torch.empty(self.footprint, dtype=torch.uint8, device=device)
+        self.handle = c_void_p()
+        check(lib.pic_cyl_init(ctypes.byref(self.cfg), arr, len(sps), c_void_p(self.workspace.data_ptr()),
+                               self.footprint, _stream_ptr(stream), ctypes.byref(self.handle)))
+        self._energy = torch.zeros(1, dtype=torch.float64, device=device)
+
+    def step(self, nsteps: int = 1):
+        check(lib.pic_cyl_step(self.handle, nsteps, _stream_ptr(self.stream)))
+
+    def _shape(self, which: int):
+        M, nr, nz = self.cfg.nmodes, self.cfg.nr, self.cfg.nz
+        return {CYL_EB_HAT: ((M, 6, nr, nz), self.cplx), CYL_RHO_HAT: ((M, nr, nz), self.cplx),
+                CYL_FIELDS: ((M, 6, nr, nz), self.cplx), CYL_SOURCES: ((M, 4, nr, nz), self.cplx),
+                CYL_K: ((M, nr + 1 + nz), torch.float64), CYL_STATUS: ((1,), torch.int32)}[which]
+
+    def get(self, which: int, device=None) -> torch.Tensor:
+        shape, dt = self._shape(which)
+        out = torch.empty(shape, dtype=dt, device=device or self.device)
+        check(lib.pic_cyl_get(self.handle, which, c_void_p(out.data_ptr()), out.numel() * out.element_size(),
+                              _stream_ptr(self.stream)))
+        return out
+
+    def get_particles(self, k: int, device=None) -> Dict[str, torch.Tensor]:
+        n = self.n[k]
+        out = {name: torch.empty(n, dtype=self.real, device=device or self.device)
+               for name in ("x", "y", "z", "ux", "uy", "uz")}
+        xs = (c_void_p * 3)(*(c_void_p(out[a].data_ptr()) for a in ("x", "y", "z")))
+        us = (c_void_p * 3)(*(c_void_p(out[a].data_ptr()) for a in ("ux", "uy", "uz")))
+        check(lib.pic_cyl_get_particles(self.handle, k, xs, us, _stream_ptr(self.stream)))
+        return out
+
+    def energy(self) -> float:
+        check(lib.pic_cyl_energy(self.handle, c_void_p(self._energy.data_ptr()), _stream_ptr(self.stream)))
+        return float(self._energy.item())
+
+    def status(self) -> int:
+        return int(self.get(CYL_STATUS, device="cpu").item())
+
+    def close(self):
+        if self.handle:
+            (self.stream if self.stream is not None else torch.cuda.current_stream()).synchronize()
+            check(lib.pic_cyl_destroy(self.handle))
+            self.handle = c_void_p()
 
     def __del__(self):
         try:
