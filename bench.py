@@ -223,6 +223,55 @@ def linear_pass_roofline(grid, steps, warmup, hbm, peak_kind):
             "device_status": status}
 
 
+def cylindrical_leg(steps, warmup, hbm, peak_kind, nr=256, nz=2048, nmodes=2, ppc=16):
+    """The quasi-cylindrical step (pic_cyl_*) on a gamma = 130 plasma column, FP32: whole-step
+    throughput timed with CUDA events on the run's stream, then the stage times from the
+    library's stage events, with the rooflines of its two dominant kernels: the particle
+    kernel (HBM bytes of the particle arrays and the mode fields and deposits) and the radial
+    matrix products (FP32 flops: 8 nr^2 nz per batch, 10 batches per mode per step)."""
+    import torch
+    import galpic_inputs as gi
+    from paper_1608_00215_gb300 import galpic as gp
+    wl = gi.cylindrical_plasma(nr, nz, 130.0, nmodes=nmodes, ppc=ppc, spread=0.01, seed=2)
+    P = sum(len(s["x"]) for s in wl.species)
+    sim = gp.CylSim(nr=wl.nr, nz=wl.nz, nmodes=wl.nmodes, dr=wl.dr, dz=wl.dz, dt=wl.dt, vgal=wl.vgal,
+                    c=wl.c, eps0=wl.eps0, beta_init=wl.beta_init, precision=32, species=wl.species)
+    sim.step(warmup)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    sim.step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    sim.profile(True)
+    sim.step(steps)
+    st = sim.profile_read()
+    sim.profile(False)
+    status = sim.status()
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    stage = {k: v["ms"] / max(1, v["count"]) for k, v in st.items()}
+    G = nr * nz
+    part_bytes = P * (7 + 6) * 4 + nmodes * G * 8 * (6 + 4)
+    part_gbs = part_bytes / (stage["particles"] * 1e-3) / 1e9
+    mm_flops = 8.0 * nr * nr * nz * 10 * nmodes
+    mm_tf = mm_flops / (stage["radial_products"] * 2 * 1e-3) / 1e12   # two launches per step
+    fpk = fp32_peak_tflops()
+    return {"workload": f"{wl.name} (FP32, {P} particles, {nmodes} modes)", "ms_per_step": ms,
+            "particle_pushes_per_s": P / (ms * 1e-3), "stages_ms_per_step": stage,
+            "roofline_particles": {"bound": "hbm", "kernel": "cyl_particle_kernel<float>", "achieved": part_gbs,
+                                   "peak": hbm, "unit": "GB/s", "frac": part_gbs / hbm, "traffic": None,
+                                   "peak_kind": peak_kind, "algorithmic_bytes_per_launch": part_bytes,
+                                   "note": "deposit by global float atomics (16 per particle per mode)"},
+            "roofline_radial_products": {"bound": "alu", "kernel": "radial_matmul_kernel<float>",
+                                         "achieved": mm_tf, "peak": fpk, "unit": "TFLOP/s", "frac": mm_tf / fpk,
+                                         "algorithmic_flops_per_launch": mm_flops / 2},
+            "device_status": status}
+
+
 def kspace_bytes(wl, precision):
     """Algorithmic HBM bytes of one k-space update: reads E, B, J, rho^{n+1}, rho^n and six
     factors; writes E, B twice (master and inverse-FFT copy) and rho^n (complex)."""
@@ -402,6 +451,8 @@ def run_ours(args, rank, world, local_rank):
         # small-run-heavy trace (32^3 and 64^3 grids only): where launches dominate
         line["serving_small_runs"] = serving_bench(args.serving_requests, args.serving_steps,
                                                    grids=[(32, 32, 32), (64, 64, 64)])
+    if not args.no_cyl and world == 1:
+        line["quasi_cylindrical"] = cylindrical_leg(10, 3, hbm, peak_kind)
     if args.order > 1 and not args.no_linear and world == 1:
         line["roofline_linear"] = linear_pass_roofline(grid, 5, 3, hbm, peak_kind)
     if not args.no_cpu_baseline and world == 1:
@@ -788,6 +839,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--no-cyl", action="store_true", help="skip the quasi-cylindrical leg")
     ap.add_argument("--no-linear", action="store_true",
                     help="skip the roofline_linear leg (the linear-shape pass on the same grid)")
     ap.add_argument("--grid", default=",".join(str(x) for x in GRID),

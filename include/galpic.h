@@ -501,6 +501,17 @@ int pic_cyl_get_particles(pic_cyl* run, int species, void* x[3], void* u[3], voi
  * of the real mode fields, one double written to the DEVICE address out_dev. */
 int pic_cyl_energy(pic_cyl* run, double* out_dev, void* stream);
 
+/* Stage timing (tracing). While enabled, pic_cyl_step records a CUDA event pair around
+ * each stage on its stream and waits for it at the end of every step (and for the radial
+ * products inside the transforms): 0 particle kernel (with the deposit arrays' clear),
+ * 1 sources to spectral space, 2 k-space update, 3 fields to real space, 4 the radial
+ * matrix products (inside stages 1 and 3). Enabling clears old records. */
+int pic_cyl_profile(pic_cyl* run, int enable);
+
+/* Per stage, the summed milliseconds and the number of recorded intervals since the last
+ * read (or enable); clears the records. */
+int pic_cyl_profile_read(pic_cyl* run, double ms[5], int64_t count[5]);
+
 int pic_cyl_destroy(pic_cyl* run);
 
 #ifdef __cplusplus

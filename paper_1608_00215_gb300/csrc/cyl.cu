@@ -75,6 +75,12 @@ struct pic_cyl {
     void* fftwork;
     cufftHandle plan6 = 0, plan4 = 0;   // C2C along z: M*6*nr and M*4*nr rows
     int64_t steps = 0;
+    // stage timing (pic_cyl_profile): 0 particles, 1 sources to spectral space, 2 k-space
+    // update, 3 fields to real space, 4 the radial products inside stages 1 and 3
+    bool prof = false;
+    cudaEvent_t ev[5][2] = {};
+    double prof_ms[5] = {};
+    int64_t prof_n[5] = {};
 };
 
 namespace galpic {
@@ -761,6 +767,12 @@ int radial_products(pic_cyl* s, int set, int nb, cudaStream_t st) {
     return PIC_OK;
 }
 
+// Stage timing: an event pair around stage q when profiling is on; the pair is read (and
+// the stream waited for) at the end of the step.
+void prof_mark(pic_cyl* s, int q, int end, cudaStream_t st) {
+    if (s->prof) cudaEventRecord(s->ev[q][end], st);
+}
+
 int exec_z(pic_cyl* s, cufftHandle plan, void* data, int dir, cudaStream_t st) {
     GP_CUFFT(cufftSetStream(plan, st));
     GP_CUFFT(cufftSetWorkArea(plan, s->fftwork));
@@ -780,7 +792,16 @@ int fields_to_real(pic_cyl* s, cudaStream_t st) {
     else
         spectral_to_pq_kernel<float2><<<gridn(M * 2 * G), 256, 0, st>>>((float2*)s->W1, (const float2*)s->EBh, M, G);
     GP_CUDA(cudaGetLastError());
+    prof_mark(s, 4, 0, st);
     GP_CHECK(radial_products(s, 0, M * 6, st));
+    prof_mark(s, 4, 1, st);
+    if (s->prof) {
+        float a = 0.f;
+        GP_CUDA(cudaEventSynchronize(s->ev[4][1]));
+        GP_CUDA(cudaEventElapsedTime(&a, s->ev[4][0], s->ev[4][1]));
+        s->prof_ms[4] += a;
+        s->prof_n[4] += 1;
+    }
     GP_CHECK(exec_z(s, s->plan6, s->W2, CUFFT_INVERSE, st));
     if (s->cfg.precision == 64)
         pq_to_polar_kernel<double2, double><<<gridn(M * 2 * G), 256, 0, st>>>((double2*)s->Fr, (const double2*)s->W2, M,
@@ -802,7 +823,16 @@ int sources_to_spectral(pic_cyl* s, cudaStream_t st) {
         polar_to_cd_kernel<float2><<<gridn(M * G), 256, 0, st>>>((float2*)s->W1, (const float2*)s->Dr, M, G);
     GP_CUDA(cudaGetLastError());
     GP_CHECK(exec_z(s, s->plan4, s->W1, CUFFT_FORWARD, st));
+    prof_mark(s, 4, 0, st);
     GP_CHECK(radial_products(s, 1, M * 4, st));
+    prof_mark(s, 4, 1, st);
+    if (s->prof) {
+        float a = 0.f;
+        GP_CUDA(cudaEventSynchronize(s->ev[4][1]));
+        GP_CUDA(cudaEventElapsedTime(&a, s->ev[4][0], s->ev[4][1]));
+        s->prof_ms[4] += a;
+        s->prof_n[4] += 1;
+    }
     if (s->cfg.precision == 64)
         cd_to_spectral_kernel<double2><<<gridn(M * G), 256, 0, st>>>((double2*)s->Sh, (const double2*)s->W2, M, G);
     else
@@ -898,6 +928,9 @@ int pic_cyl_footprint(const pic_cyl_config* cfg, const pic_cyl_species* species,
 
 int pic_cyl_destroy(pic_cyl* s) {
     if (!s) return PIC_OK;
+    for (int q = 0; q < 5; ++q)
+        for (int e = 0; e < 2; ++e)
+            if (s->ev[q][e]) cudaEventDestroy(s->ev[q][e]);
     if (s->plan6) cufftDestroy(s->plan6);
     if (s->plan4) cufftDestroy(s->plan4);
     delete s;
@@ -1076,11 +1109,52 @@ int pic_cyl_step(pic_cyl* s, int nsteps, void* stream) {
     if (nsteps < 0) return fail(PIC_EINVAL, "nsteps < 0");
     cudaStream_t st = (cudaStream_t)stream;
     for (int i = 0; i < nsteps; ++i) {
+        prof_mark(s, 0, 0, st);
         GP_CHECK(particles(s, 1, st));
+        prof_mark(s, 0, 1, st);
+        prof_mark(s, 1, 0, st);
         GP_CHECK(sources_to_spectral(s, st));
+        prof_mark(s, 1, 1, st);
+        prof_mark(s, 2, 0, st);
         GP_CHECK(launch_kspace_descs(s->cfg.precision, s->kdesc, s->cfg.nmodes, s->G, st));
+        prof_mark(s, 2, 1, st);
+        prof_mark(s, 3, 0, st);
         GP_CHECK(fields_to_real(s, st));
+        prof_mark(s, 3, 1, st);
+        if (s->prof) {
+            GP_CUDA(cudaEventSynchronize(s->ev[3][1]));
+            for (int q = 0; q < 4; ++q) {
+                float a = 0.f;
+                GP_CUDA(cudaEventElapsedTime(&a, s->ev[q][0], s->ev[q][1]));
+                s->prof_ms[q] += a;
+                s->prof_n[q] += 1;
+            }
+        }
         s->steps += 1;
+    }
+    return PIC_OK;
+}
+
+int pic_cyl_profile(pic_cyl* s, int enable) {
+    if (!s) return fail(PIC_EINVAL, "cyl run is NULL");
+    if (enable && !s->ev[0][0])
+        for (int q = 0; q < 5; ++q)
+            for (int e = 0; e < 2; ++e) GP_CUDA(cudaEventCreate(&s->ev[q][e]));
+    s->prof = enable != 0;
+    for (int q = 0; q < 5; ++q) {
+        s->prof_ms[q] = 0.0;
+        s->prof_n[q] = 0;
+    }
+    return PIC_OK;
+}
+
+int pic_cyl_profile_read(pic_cyl* s, double ms[5], int64_t count[5]) {
+    if (!s || !ms || !count) return fail(PIC_EINVAL, "NULL argument");
+    for (int q = 0; q < 5; ++q) {
+        ms[q] = s->prof_ms[q];
+        count[q] = s->prof_n[q];
+        s->prof_ms[q] = 0.0;
+        s->prof_n[q] = 0;
     }
     return PIC_OK;
 }

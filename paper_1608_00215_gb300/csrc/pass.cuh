@@ -126,6 +126,15 @@ __device__ __forceinline__ double2 pmul(double2 a, double2 b) {
     return make_double2(a.x * b.x, a.y * b.y);
 }
 
+// 1/sqrt(x) and a/b of the Boris push: FP32 runs take the hardware reciprocal square root
+// and the fast division (CUDA's rsqrtf and __fdividef, within 2 ulp, against a 1e-5 FP32
+// step tolerance) instead of the correctly rounded sequences with their special-case
+// branches; FP64 runs keep the correctly rounded forms.
+__device__ __forceinline__ float boris_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double boris_rsqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float boris_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double boris_div(double a, double b) { return a / b; }
+
 template <typename T> struct Pair;
 template <> struct Pair<float> {
     typedef float2 type;
@@ -233,11 +242,15 @@ __host__ __device__ constexpr int stage_rows(int NW, bool jr) { return jr ? 4 + 
 // Per-warp particle staging of the one-thread-per-cell pass: CELL_CHUNK particles of one
 // species (cell, three offsets, three momenta), loaded and stored coalesced. A warp's 32
 // cells hold 256 particles of a species at 8 per cell, which one chunk then covers, so
-// that every lane has its cell's particles in the same chunk.
+// that every lane has its cell's particles in the same chunk. Entry j sits at slot
+// j + j/32 of each array: lanes then read their cells' particles (strides of a few
+// entries, 8 for the bench plasma) from distinct banks instead of 8-way conflicts.
 constexpr int CELL_CHUNK = 256;
+constexpr int CELL_STRIDE = CELL_CHUNK + CELL_CHUNK / 32;
+__host__ __device__ __forceinline__ int cell_slot(int j) { return j + (j >> 5); }
 
 __host__ __device__ constexpr size_t stage_bytes(int NW, size_t T, int dep) {
-    return dep == DEP_CELL ? align16((size_t)CELL_CHUNK * (4 + 6 * T))
+    return dep == DEP_CELL ? align16((size_t)CELL_STRIDE * (4 + 6 * T))
            : (T == 4 && NW == 4 && (dep == DEP_ROW || dep == DEP_ROWU))
                ? RowStage::BYTES
                : align16((size_t)stage_rows(NW, NW == 2 || dep == DEP_JR) * 34 * T);
@@ -1220,9 +1233,9 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p, const int 
                     // ---- relativistic Boris push u^{n-1/2} -> u^{n+1/2}
                     const T a = sp.qdt2m;
                     const T umx = ux + a * E[0], umy = uy + a * E[1], umz = uz + a * E[2];
-                    const T igm = (T)1 / sqrt((T)1 + (umx * umx + umy * umy + umz * umz) * p.inv_c2);
+                    const T igm = boris_rsqrt((T)1 + (umx * umx + umy * umy + umz * umz) * p.inv_c2);
                     const T tx = a * B[0] * igm, ty = a * B[1] * igm, tz = a * B[2] * igm;
-                    const T s2 = (T)2 / ((T)1 + tx * tx + ty * ty + tz * tz);
+                    const T s2 = boris_div((T)2, (T)1 + tx * tx + ty * ty + tz * tz);
                     const T sx = s2 * tx, sy = s2 * ty, sz = s2 * tz;
                     const T upx = umx + (umy * tz - umz * ty);
                     const T upy = umy + (umz * tx - umx * tz);
@@ -1231,7 +1244,7 @@ __device__ __forceinline__ void particle_pass_body(const PassK<T>& p, const int 
                     uy = umy + (upz * sx - upx * sz) + a * E[1];
                     uz = umz + (upx * sy - upy * sx) + a * E[2];
                 }
-                const T igam = (T)1 / sqrt((T)1 + (ux * ux + uy * uy + uz * uz) * p.inv_c2);
+                const T igam = boris_rsqrt((T)1 + (ux * ux + uy * uy + uz * uz) * p.inv_c2);
                 vx = ux * igam;
                 vy = uy * igam;
                 vz = uz * igam;
@@ -1604,10 +1617,11 @@ __device__ __forceinline__ void cell_pass_body(const PassK<T>& p, const int b) {
 
     unsigned long long miss = 0, far = 0;
     const int warp = threadIdx.x >> 5;
-    // this warp's particle staging: cell[CELL_CHUNK] then off x, y, z and u x, y, z
+    // this warp's particle staging: cell[CELL_STRIDE] then off x, y, z and u x, y, z, entry j
+    // of a chunk at slot cell_slot(j)
     unsigned char* const wst = smem_raw + L.stage + (size_t)warp * stage_bytes(NW, sizeof(T), DEP_CELL);
     int32_t* const st_cell = reinterpret_cast<int32_t*>(wst);
-    T* const st_v = reinterpret_cast<T*>(wst + CELL_CHUNK * 4);   // [6][CELL_CHUNK]
+    T* const st_v = reinterpret_cast<T*>(wst + CELL_STRIDE * 4);   // [6][CELL_STRIDE]
     // warp w takes the 32 consecutive cells (keys) 32 w .. 32 w + 31, then 256 + 32 w ..;
     // lane t the cell 32 w + t of each group: the group's particles are one contiguous
     // range per species, staged CELL_CHUNK at a time
@@ -1640,22 +1654,24 @@ __device__ __forceinline__ void cell_pass_body(const PassK<T>& p, const int b) {
                 const int hi = min(lo + CELL_CHUNK, Bend);
                 // stage in, coalesced
                 for (int j = lane; j < hi - lo; j += 32) {
-                    st_cell[j] = sp.cell[lo + j];
+                    const int q = cell_slot(j);
+                    st_cell[q] = sp.cell[lo + j];
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
-                        st_v[d * CELL_CHUNK + j] = sp.off[d][lo + j];
-                        st_v[(3 + d) * CELL_CHUNK + j] = sp.u[d][lo + j];
+                        st_v[d * CELL_STRIDE + q] = sp.off[d][lo + j];
+                        st_v[(3 + d) * CELL_STRIDE + q] = sp.u[d][lo + j];
                     }
                 }
                 __syncwarp();
                 const int i0 = max(beg, lo), i1 = min(end, hi);
                 for (int i = i0; i < i1; ++i) {
-                    const int j = i - lo;
-                    if (!PIC_INDEX_OK(j, CELL_CHUNK, p.status)) break;
+                    const int j0 = i - lo;
+                    if (!PIC_INDEX_OK(j0, CELL_CHUNK, p.status)) break;
+                    const int j = cell_slot(j0);
                     const int c = st_cell[j];
                     if (!PIC_INDEX_OK(c, N, p.status)) continue;
-                    T fx = st_v[0 * CELL_CHUNK + j], fy = st_v[1 * CELL_CHUNK + j], fz = st_v[2 * CELL_CHUNK + j];
-                    T ux = st_v[3 * CELL_CHUNK + j], uy = st_v[4 * CELL_CHUNK + j], uz = st_v[5 * CELL_CHUNK + j];
+                    T fx = st_v[0 * CELL_STRIDE + j], fy = st_v[1 * CELL_STRIDE + j], fz = st_v[2 * CELL_STRIDE + j];
+                    T ux = st_v[3 * CELL_STRIDE + j], uy = st_v[4 * CELL_STRIDE + j], uz = st_v[5 * CELL_STRIDE + j];
                     int ix = hx, iy = hy, iz = hz, rx = hrx, ry = hry, rz = hrz;
                     if (c != home) {   // moved since the sort
                         ix = p.div_nynz.div(c);
@@ -1708,9 +1724,9 @@ __device__ __forceinline__ void cell_pass_body(const PassK<T>& p, const int b) {
                         // ---- relativistic Boris push u^{n-1/2} -> u^{n+1/2}
                         const T a = sp.qdt2m;
                         const T umx = ux + a * E[0], umy = uy + a * E[1], umz = uz + a * E[2];
-                        const T igm = (T)1 / sqrt((T)1 + (umx * umx + umy * umy + umz * umz) * p.inv_c2);
+                        const T igm = boris_rsqrt((T)1 + (umx * umx + umy * umy + umz * umz) * p.inv_c2);
                         const T tx = a * B[0] * igm, ty = a * B[1] * igm, tz = a * B[2] * igm;
-                        const T s2 = (T)2 / ((T)1 + tx * tx + ty * ty + tz * tz);
+                        const T s2 = boris_div((T)2, (T)1 + tx * tx + ty * ty + tz * tz);
                         const T sx = s2 * tx, sy = s2 * ty, sz = s2 * tz;
                         const T upx = umx + (umy * tz - umz * ty);
                         const T upy = umy + (umz * tx - umx * tz);
@@ -1719,7 +1735,7 @@ __device__ __forceinline__ void cell_pass_body(const PassK<T>& p, const int b) {
                         uy = umy + (upz * sx - upx * sz) + a * E[1];
                         uz = umz + (upx * sy - upy * sx) + a * E[2];
                     }
-                    const T igam = (T)1 / sqrt((T)1 + (ux * ux + uy * uy + uz * uz) * p.inv_c2);
+                    const T igam = boris_rsqrt((T)1 + (ux * ux + uy * uy + uz * uz) * p.inv_c2);
                     const T vx = ux * igam, vy = uy * igam, vz = uz * igam;
                     // ---- J^{n+1/2} at x^{n+1/2} with v^{n+1/2} (DEPOSIT mode: at x with v)
                     if (MODE == PASS_STEP) {
@@ -1783,12 +1799,12 @@ __device__ __forceinline__ void cell_pass_body(const PassK<T>& p, const int b) {
                     }
                     if (MODE == PASS_STEP) {
                         st_cell[j] = (ix * p.ny + iy) * p.nz + iz;
-                        st_v[0 * CELL_CHUNK + j] = fx;
-                        st_v[1 * CELL_CHUNK + j] = fy;
-                        st_v[2 * CELL_CHUNK + j] = fz;
-                        st_v[3 * CELL_CHUNK + j] = ux;
-                        st_v[4 * CELL_CHUNK + j] = uy;
-                        st_v[5 * CELL_CHUNK + j] = uz;
+                        st_v[0 * CELL_STRIDE + j] = fx;
+                        st_v[1 * CELL_STRIDE + j] = fy;
+                        st_v[2 * CELL_STRIDE + j] = fz;
+                        st_v[3 * CELL_STRIDE + j] = ux;
+                        st_v[4 * CELL_STRIDE + j] = uy;
+                        st_v[5 * CELL_STRIDE + j] = uz;
                         if (ix < x0 || ix >= x0 + BIN || iy < y0 || iy >= y0 + BIN || iz < z0 || iz >= z0 + BIN)
                             miss++;
                     }
@@ -1796,11 +1812,12 @@ __device__ __forceinline__ void cell_pass_body(const PassK<T>& p, const int b) {
                 __syncwarp();
                 if (MODE == PASS_STEP) {   // stage out, coalesced
                     for (int j = lane; j < hi - lo; j += 32) {
-                        sp.cell[lo + j] = st_cell[j];
+                        const int q = cell_slot(j);
+                        sp.cell[lo + j] = st_cell[q];
 #pragma unroll
                         for (int d = 0; d < 3; ++d) {
-                            sp.off[d][lo + j] = st_v[d * CELL_CHUNK + j];
-                            sp.u[d][lo + j] = st_v[(3 + d) * CELL_CHUNK + j];
+                            sp.off[d][lo + j] = st_v[d * CELL_STRIDE + q];
+                            sp.u[d][lo + j] = st_v[(3 + d) * CELL_STRIDE + q];
                         }
                     }
                 }

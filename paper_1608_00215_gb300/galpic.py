@@ -62,6 +62,7 @@ class PicCylSpecies(ctypes.Structure):
 
 
 CYL_EB_HAT, CYL_RHO_HAT, CYL_FIELDS, CYL_SOURCES, CYL_K, CYL_STATUS = range(6)
+CYL_STAGES = ("particles", "to_spectral", "kspace", "to_real", "radial_products")
 
 
 class GalpicError(RuntimeError):
@@ -114,6 +115,8 @@ def _load():
         "pic_cyl_get_particles": (c_int, [P, c_int, POINTER(P), POINTER(P), P]),
         "pic_cyl_energy": (c_int, [P, P, P]),
         "pic_cyl_destroy": (c_int, [P]),
+        "pic_cyl_profile": (c_int, [P, c_int]),
+        "pic_cyl_profile_read": (c_int, [P, POINTER(c_double), POINTER(c_int64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -132,7 +135,7 @@ EXPORTS = ("pic_version", "pic_last_error", "pic_footprint", "pic_init", "pic_de
            "pic_counters", "pic_sizes", "pic_profile", "pic_profile_read", "pic_sort",
            "pic_field_energy_noalloc", "pic_add_fields", "pic_sort_policy", "pic_tune", "pic_get_line",
            "pic_cyl_footprint", "pic_cyl_init", "pic_cyl_step", "pic_cyl_get", "pic_cyl_get_particles",
-           "pic_cyl_energy", "pic_cyl_destroy")
+           "pic_cyl_energy", "pic_cyl_destroy", "pic_cyl_profile", "pic_cyl_profile_read")
 
 STAGES = ("sort", "particles", "fft_r2c", "kspace", "fft_c2r", "energy")
 
@@ -439,6 +442,15 @@ class CylSim:
 
     def status(self) -> int:
         return int(self.get(CYL_STATUS, device="cpu").item())
+
+    def profile(self, enable: bool = True):
+        check(lib.pic_cyl_profile(self.handle, int(enable)))
+
+    def profile_read(self) -> Dict[str, Dict[str, float]]:
+        ms = (c_double * 5)()
+        cnt = (c_int64 * 5)()
+        check(lib.pic_cyl_profile_read(self.handle, ms, cnt))
+        return {name: {"ms": ms[i], "count": int(cnt[i])} for i, name in enumerate(CYL_STAGES)}
 
     def close(self):
         if self.handle:
