@@ -135,6 +135,22 @@ __device__ __forceinline__ double boris_rsqrt(double x) { return 1.0 / sqrt(x); 
 __device__ __forceinline__ float boris_div(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double boris_div(double a, double b) { return a / b; }
 
+// Relativistic Boris push u^{n-1/2} -> u^{n+1/2} of momentum per mass u with a = q dt / 2m.
+template <typename T>
+__device__ __forceinline__ void boris_push(const T a, const T* E, const T* B, const T inv_c2, T& ux, T& uy, T& uz) {
+    const T umx = ux + a * E[0], umy = uy + a * E[1], umz = uz + a * E[2];
+    const T igm = boris_rsqrt((T)1 + (umx * umx + umy * umy + umz * umz) * inv_c2);
+    const T tx = a * B[0] * igm, ty = a * B[1] * igm, tz = a * B[2] * igm;
+    const T s2 = boris_div((T)2, (T)1 + tx * tx + ty * ty + tz * tz);
+    const T sx = s2 * tx, sy = s2 * ty, sz = s2 * tz;
+    const T upx = umx + (umy * tz - umz * ty);
+    const T upy = umy + (umz * tx - umx * tz);
+    const T upz = umz + (umx * ty - umy * tx);
+    ux = umx + (upy * sz - upz * sy) + a * E[0];
+    uy = umy + (upz * sx - upx * sz) + a * E[1];
+    uz = umz + (upx * sy - upy * sx) + a * E[2];
+}
+
 template <typename T> struct Pair;
 template <> struct Pair<float> {
     typedef float2 type;
@@ -1597,6 +1613,10 @@ __device__ __forceinline__ void cell_pass_body(const PassK<T>& p, const int b) {
     const int x0 = bx * BIN, y0 = by * BIN, z0 = bz * BIN;
     const int ox = x0 - MARGIN, oy = y0 - MARGIN, oz = z0 - MARGIN;
     const int64_t N = p.N;
+    // the step's scalars, read once (the shared-launch kernels keep the run's parameters in
+    // shared memory, which would otherwise be read at every use)
+    const T inv_c2 = p.inv_c2;
+    const T vg[3] = {p.vgal[0], p.vgal[1], p.vgal[2]}, hd[3] = {p.hd[0], p.hd[1], p.hd[2]};
     for (int idx = threadIdx.x; idx < R; idx += blockDim.x) {
         const int rx = idx / (TE * TE);
         const int rem = idx - rx * (TE * TE);
@@ -1643,6 +1663,7 @@ __device__ __forceinline__ void cell_pass_body(const PassK<T>& p, const int b) {
         }
         for (int s = 0; s < p.nspecies; ++s) {
             const SpeciesK<T>& sp = p.sp[s];
+            const T qdt2m = sp.qdt2m, qw_dv = sp.qw_dv;
             int beg = sp.cell_start[key], end = sp.cell_start[key + 1];
             // checked build: a cell range outside the species' particles is flagged and emptied
             if (!(PIC_INDEX_OK(beg, (int64_t)sp.n + 1, p.status) && PIC_INDEX_OK(end, (int64_t)sp.n + 1, p.status) &&
@@ -1664,14 +1685,10 @@ __device__ __forceinline__ void cell_pass_body(const PassK<T>& p, const int b) {
                 }
                 __syncwarp();
                 const int i0 = max(beg, lo), i1 = min(end, hi);
-                for (int i = i0; i < i1; ++i) {
-                    const int j0 = i - lo;
-                    if (!PIC_INDEX_OK(j0, CELL_CHUNK, p.status)) break;
-                    const int j = cell_slot(j0);
-                    const int c = st_cell[j];
-                    if (!PIC_INDEX_OK(c, N, p.status)) continue;
-                    T fx = st_v[0 * CELL_STRIDE + j], fy = st_v[1 * CELL_STRIDE + j], fz = st_v[2 * CELL_STRIDE + j];
-                    T ux = st_v[3 * CELL_STRIDE + j], uy = st_v[4 * CELL_STRIDE + j], uz = st_v[5 * CELL_STRIDE + j];
+                // one particle at staging slot j from its loaded values; `pushed`: E, B were
+                // gathered at its home cell and u pushed already
+                auto one = [&](const int j, const int c, T fx, T fy, T fz, T ux, T uy, T uz, const bool pushed) {
+                    if (!PIC_INDEX_OK(c, N, p.status)) return;
                     int ix = hx, iy = hy, iz = hz, rx = hrx, ry = hry, rz = hrz;
                     if (c != home) {   // moved since the sort
                         ix = p.div_nynz.div(c);
@@ -1683,7 +1700,7 @@ __device__ __forceinline__ void cell_pass_body(const PassK<T>& p, const int b) {
                         rz = tile_coord(iz, z0, p.nz, MARGIN);
                     }
                     T wx[2], wy[2], wz[2];
-                    if (MODE == PASS_STEP) {
+                    if (MODE == PASS_STEP && !pushed) {
                         // ---- gather E^n, B^n at x^n
                         SH::w(fx, wx);
                         SH::w(fy, wy);
@@ -1722,26 +1739,15 @@ __device__ __forceinline__ void cell_pass_body(const PassK<T>& p, const int b) {
                                 }
                         }
                         // ---- relativistic Boris push u^{n-1/2} -> u^{n+1/2}
-                        const T a = sp.qdt2m;
-                        const T umx = ux + a * E[0], umy = uy + a * E[1], umz = uz + a * E[2];
-                        const T igm = boris_rsqrt((T)1 + (umx * umx + umy * umy + umz * umz) * p.inv_c2);
-                        const T tx = a * B[0] * igm, ty = a * B[1] * igm, tz = a * B[2] * igm;
-                        const T s2 = boris_div((T)2, (T)1 + tx * tx + ty * ty + tz * tz);
-                        const T sx = s2 * tx, sy = s2 * ty, sz = s2 * tz;
-                        const T upx = umx + (umy * tz - umz * ty);
-                        const T upy = umy + (umz * tx - umx * tz);
-                        const T upz = umz + (umx * ty - umy * tx);
-                        ux = umx + (upy * sz - upz * sy) + a * E[0];
-                        uy = umy + (upz * sx - upx * sz) + a * E[1];
-                        uz = umz + (upx * sy - upy * sx) + a * E[2];
+                        boris_push(qdt2m, E, B, inv_c2, ux, uy, uz);
                     }
-                    const T igam = boris_rsqrt((T)1 + (ux * ux + uy * uy + uz * uz) * p.inv_c2);
+                    const T igam = boris_rsqrt((T)1 + (ux * ux + uy * uy + uz * uz) * inv_c2);
                     const T vx = ux * igam, vy = uy * igam, vz = uz * igam;
                     // ---- J^{n+1/2} at x^{n+1/2} with v^{n+1/2} (DEPOSIT mode: at x with v)
                     if (MODE == PASS_STEP) {
-                        rx += drift_axis(ix, fx, (vx - p.vgal[0]) * p.hd[0], p.nx);
-                        ry += drift_axis(iy, fy, (vy - p.vgal[1]) * p.hd[1], p.ny);
-                        rz += drift_axis(iz, fz, (vz - p.vgal[2]) * p.hd[2], p.nz);
+                        rx += drift_axis(ix, fx, (vx - vg[0]) * hd[0], p.nx);
+                        ry += drift_axis(iy, fy, (vy - vg[1]) * hd[1], p.ny);
+                        rz += drift_axis(iz, fz, (vz - vg[2]) * hd[2], p.nz);
                         SH::w(fx, wx);
                         SH::w(fy, wy);
                         SH::w(fz, wz);
@@ -1750,7 +1756,7 @@ __device__ __forceinline__ void cell_pass_body(const PassK<T>& p, const int b) {
                         SH::w(fy, wy);
                         SH::w(fz, wz);
                     }
-                    const T qv[3] = {sp.qw_dv * vx, sp.qw_dv * vy, sp.qw_dv * vz};
+                    const T qv[3] = {qw_dv * vx, qw_dv * vy, qw_dv * vz};
                     if (rx == hrx && ry == hry && rz == hrz) {
                         const P2 qxy = Pair<T>::make(qv[0], qv[1]);
     #pragma unroll
@@ -1773,14 +1779,14 @@ __device__ __forceinline__ void cell_pass_body(const PassK<T>& p, const int b) {
                     }
                     // ---- rho^{n+1} at x^{n+1} (DEPOSIT mode: at x)
                     if (MODE == PASS_STEP) {
-                        rx += drift_axis(ix, fx, (vx - p.vgal[0]) * p.hd[0], p.nx);
-                        ry += drift_axis(iy, fy, (vy - p.vgal[1]) * p.hd[1], p.ny);
-                        rz += drift_axis(iz, fz, (vz - p.vgal[2]) * p.hd[2], p.nz);
+                        rx += drift_axis(ix, fx, (vx - vg[0]) * hd[0], p.nx);
+                        ry += drift_axis(iy, fy, (vy - vg[1]) * hd[1], p.ny);
+                        rz += drift_axis(iz, fz, (vz - vg[2]) * hd[2], p.nz);
                         SH::w(fx, wx);
                         SH::w(fy, wy);
                         SH::w(fz, wz);
                     }
-                    const T qr[1] = {sp.qw_dv};
+                    const T qr[1] = {qw_dv};
                     if (rx == hrx && ry == hry && rz == hrz) {
     #pragma unroll
                         for (int a = 0; a < 2; ++a)
@@ -1807,6 +1813,127 @@ __device__ __forceinline__ void cell_pass_body(const PassK<T>& p, const int b) {
                         st_v[5 * CELL_STRIDE + j] = uz;
                         if (ix < x0 || ix >= x0 + BIN || iy < y0 || iy >= y0 + BIN || iz < z0 || iz >= z0 + BIN)
                             miss++;
+                    }
+                };
+                auto load = [&](const int j, T* f, T* u) {
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        f[d] = st_v[d * CELL_STRIDE + j];
+                        u[d] = st_v[(3 + d) * CELL_STRIDE + j];
+                    }
+                };
+                if (MODE != PASS_STEP || sizeof(T) != 4) {   // FP64: one at a time (registers)
+                    for (int i = i0; i < i1; ++i) {
+                        const int j0 = i - lo;
+                        if (!PIC_INDEX_OK(j0, CELL_CHUNK, p.status)) break;
+                        const int j = cell_slot(j0);
+                        T f[3], u[3];
+                        load(j, f, u);
+                        one(j, st_cell[j], f[0], f[1], f[2], u[0], u[1], u[2], false);
+                    }
+                } else {
+                    // Particles two at a time: a pair at rest in the home cell through both
+                    // half drifts (the common case on a Galilean grid) runs as two independent
+                    // instruction streams; any other particle takes the general path. The
+                    // second member of an odd tail repeats the first with zero charge and is
+                    // not stored. Per accumulator the additions come in particle order, as
+                    // one at a time.
+                    for (int i = i0; i < i1; i += 2) {
+                        const bool has1 = i + 1 < i1;
+                        const int ja0 = i - lo, jb0 = (has1 ? i + 1 : i) - lo;
+                        if (!(PIC_INDEX_OK(ja0, CELL_CHUNK, p.status) && PIC_INDEX_OK(jb0, CELL_CHUNK, p.status))) break;
+                        const int j[2] = {cell_slot(ja0), cell_slot(jb0)};
+                        const int c[2] = {st_cell[j[0]], st_cell[j[1]]};
+                        T f[2][3], u[2][3];
+                        load(j[0], f[0], u[0]);
+                        load(j[1], f[1], u[1]);
+                        if (c[0] != home || c[1] != home) {
+                            one(j[0], c[0], f[0][0], f[0][1], f[0][2], u[0][0], u[0][1], u[0][2], false);
+                            if (has1) one(j[1], c[1], f[1][0], f[1][1], f[1][2], u[1][0], u[1][1], u[1][2], false);
+                            continue;
+                        }
+                        int gbase = hbase;
+#ifdef PIC_CHECKED
+                        gbase += p.inject;
+                        if (!PIC_INDEX_OK(gbase, R - (TE * TE + TE + 1), p.status)) gbase = 0;
+#endif
+                        T g1[2][3], g2[2][3];
+                        bool stay = true;
+#pragma unroll
+                        for (int k = 0; k < 2; ++k) {
+                            T wx[2], wy[2], wz[2], E[3], B[3];
+                            SH::w(f[k][0], wx);
+                            SH::w(f[k][1], wy);
+                            SH::w(f[k][2], wz);
+                            gather2<T, TE>(tile, gbase, wx, wy, wz, E, B);
+                            boris_push(qdt2m, E, B, inv_c2, u[k][0], u[k][1], u[k][2]);
+                            const T igam = boris_rsqrt((T)1 + (u[k][0] * u[k][0] + u[k][1] * u[k][1] +
+                                                                u[k][2] * u[k][2]) * inv_c2);
+#pragma unroll
+                            for (int d = 0; d < 3; ++d) {
+                                const T dd = (u[k][d] * igam - vg[d]) * hd[d];
+                                g1[k][d] = f[k][d] + dd;
+                                g2[k][d] = g1[k][d] + dd;
+                                stay = stay && g1[k][d] >= (T)0 && g1[k][d] < (T)1 && g2[k][d] >= (T)0 &&
+                                       g2[k][d] < (T)1;
+                            }
+                        }
+                        if (!stay) {
+                            one(j[0], c[0], f[0][0], f[0][1], f[0][2], u[0][0], u[0][1], u[0][2], true);
+                            if (has1) one(j[1], c[1], f[1][0], f[1][1], f[1][2], u[1][0], u[1][1], u[1][2], true);
+                            continue;
+                        }
+#pragma unroll
+                        for (int k = 0; k < 2; ++k) {
+                            const T qk = (k == 0 || has1) ? qw_dv : (T)0;
+                            const T igam = boris_rsqrt((T)1 + (u[k][0] * u[k][0] + u[k][1] * u[k][1] +
+                                                                u[k][2] * u[k][2]) * inv_c2);
+                            const T qv[3] = {qk * (u[k][0] * igam), qk * (u[k][1] * igam), qk * (u[k][2] * igam)};
+                            T wx[2], wy[2], wz[2];
+                            SH::w(g1[k][0], wx);
+                            SH::w(g1[k][1], wy);
+                            SH::w(g1[k][2], wz);
+                            const P2 qxy = Pair<T>::make(qv[0], qv[1]);
+#pragma unroll
+                            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                                for (int bb = 0; bb < 2; ++bb) {
+                                    const T wxy = wx[a] * wy[bb];
+#pragma unroll
+                                    for (int cc = 0; cc < 2; ++cc) {
+                                        const T w = wxy * wz[cc];
+                                        const int n = (a * 2 + bb) * 2 + cc;
+                                        aJ[n] = pfma(Pair<T>::make(w, w), qxy, aJ[n]);
+                                        aZ[n] = fma(w, qv[2], aZ[n]);
+                                    }
+                                }
+                        }
+#pragma unroll
+                        for (int k = 0; k < 2; ++k) {
+                            const T qk = (k == 0 || has1) ? qw_dv : (T)0;
+                            T wx[2], wy[2], wz[2];
+                            SH::w(g2[k][0], wx);
+                            SH::w(g2[k][1], wy);
+                            SH::w(g2[k][2], wz);
+#pragma unroll
+                            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                                for (int bb = 0; bb < 2; ++bb) {
+                                    const T wxy = wx[a] * wy[bb];
+#pragma unroll
+                                    for (int cc = 0; cc < 2; ++cc)
+                                        aR[(a * 2 + bb) * 2 + cc] = fma(wxy * wz[cc], qk, aR[(a * 2 + bb) * 2 + cc]);
+                                }
+                        }
+#pragma unroll
+                        for (int k = 0; k < 2; ++k) {
+                            if (k == 1 && !has1) break;
+#pragma unroll
+                            for (int d = 0; d < 3; ++d) {
+                                st_v[d * CELL_STRIDE + j[k]] = g2[k][d];
+                                st_v[(3 + d) * CELL_STRIDE + j[k]] = u[k][d];
+                            }
+                        }
                     }
                 }
                 __syncwarp();

@@ -86,6 +86,14 @@ class _Bucket:
     chunk: int = 0                            # steps of the chunk in flight
 
 
+def run_strategy(wl, prec: int):
+    """Tile margin and deposit strategy of a served run: FP32 linear-shape runs take the
+    one-thread-per-cell pass (deposit strategy 4, faster than the grouped deposit on every
+    serving grid), the others the library's default grouped deposit; margin 1."""
+    det = int(getattr(wl, "deterministic", 0))
+    return (1, 4) if (wl.shape_order == 1 and prec == 32 and not det) else (1, 0)
+
+
 def share_key(wl, prec: int, margin: int = 1, deposit: int = 0):
     """Shape class of runs that can share launches (None: the run is stepped alone)."""
     ns = len(wl.species)
@@ -179,7 +187,9 @@ def warm_shared_plans(workloads, max_slots: int = 64, share_max_cells: int = 64 
         if key in seen or wl.nx * wl.ny * wl.nz > share_max_cells:
             continue
         seen.add(key)
-        sim = gp.sim_from_workload(wl, precision=precision, device=device)
+        prec = precision if precision is not None else wl.precision
+        margin, deposit = run_strategy(wl, prec)
+        sim = gp.sim_from_workload(wl, precision=precision, device=device, tile_margin=margin, deposit=deposit)
         c = 1
         while c <= max_slots:
             gp.many_footprint(sim, c)
@@ -329,8 +339,10 @@ def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_
             if shared:
                 admitted -= 1          # joining a bucket is cheap: admit every waiting run that fits
             bk = None
+            prec = precision if precision is not None else wl.precision
+            margin, deposit = run_strategy(wl, prec)
             if shared:
-                key = share_key(wl, precision if precision is not None else wl.precision)
+                key = share_key(wl, prec, margin, deposit)
                 bk = buckets.get(key)
                 if bk is None:
                     bk = _Bucket(key, torch.cuda.Stream(priority=rec.priority), gp.ManyWorkspace(device))
@@ -340,7 +352,8 @@ def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_
                 stream = torch.cuda.Stream(priority=rec.priority)
             try:
                 with torch.cuda.stream(stream):
-                    sim = gp.sim_from_workload(r.workload, precision=precision, stream=stream, device=device)
+                    sim = gp.sim_from_workload(r.workload, precision=precision, stream=stream, device=device,
+                                               tile_margin=margin, deposit=deposit)
             except Exception as e:            # allocation or validation failure: reject this run only
                 rec.error = str(e)
                 continue
