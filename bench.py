@@ -452,7 +452,8 @@ def run_ours(args, rank, world, local_rank):
         line["serving_small_runs"] = serving_bench(args.serving_requests, args.serving_steps,
                                                    grids=[(32, 32, 32), (64, 64, 64)])
     if not args.no_cyl and world == 1:
-        line["quasi_cylindrical"] = cylindrical_leg(10, 3, hbm, peak_kind)
+        nr, nz, nm, ppc = (int(v) for v in args.cyl_grid.split(","))
+        line["quasi_cylindrical"] = cylindrical_leg(10, 3, hbm, peak_kind, nr=nr, nz=nz, nmodes=nm, ppc=ppc)
     if args.order > 1 and not args.no_linear and world == 1:
         line["roofline_linear"] = linear_pass_roofline(grid, 5, 3, hbm, peak_kind)
     if not args.no_cpu_baseline and world == 1:
@@ -840,6 +841,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-cyl", action="store_true", help="skip the quasi-cylindrical leg")
+    ap.add_argument("--cyl-only", action="store_true",
+                    help="only the quasi-cylindrical leg (sizes from --cyl-grid), one JSON line")
+    ap.add_argument("--cyl-grid", default="256,2048,2,16",
+                    help="nr,nz,modes,ppc of the quasi-cylindrical leg")
     ap.add_argument("--no-linear", action="store_true",
                     help="skip the roofline_linear leg (the linear-shape pass on the same grid)")
     ap.add_argument("--grid", default=",".join(str(x) for x in GRID),
@@ -894,6 +899,14 @@ def main():
         return
     if args.coupled:
         coupled_run(args)
+        return
+    if args.cyl_only:
+        from paper_1608_00215_gb300 import build
+        build.build()
+        nr, nz, nm, ppc = (int(v) for v in args.cyl_grid.split(","))
+        hbm, peak_kind = peaks()
+        out = cylindrical_leg(args.steps, args.warmup, hbm, peak_kind, nr=nr, nz=nz, nmodes=nm, ppc=ppc)
+        print(json.dumps({"mode": "quasi_cylindrical", **out}), flush=True)
         return
     if args.serving_only:
         from paper_1608_00215_gb300 import build

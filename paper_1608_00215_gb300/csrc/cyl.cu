@@ -47,8 +47,13 @@ struct pic_cyl {
     struct Sp {
         double q, m;
         int64_t n;
-        void *w, *x[3], *u[3];
+        void *w, *x[3], *u[3];   // current arrays (sorted by bin)
+        void* alt[7];            // the other buffer of w, x, u (sort target, scratch)
+        int32_t *pid, *pid_alt;  // input index of each particle
     } sp[PIC_MAX_SPECIES];
+    int32_t *key, *rank;         // per particle of the largest species: bin and rank in bin
+    int32_t *counts, *starts;    // per bin: particles, first particle (nbins + 1)
+    int nbz = 0, nbins = 0;
     int64_t G;          // nr * nz
     char* ws;
     // device arrays (carved from the caller's workspace)
@@ -90,8 +95,15 @@ size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
 struct CylLayout {
     size_t alpha, Kd, Kt, syn, fwd, tmp64, tab, EBh, Sh, Rn, Fr, Dr, W1, W2, scratch, kdesc, gdesc, wsum, status,
-        sp[PIC_MAX_SPECIES][7], fftwork, total;
+        sp[PIC_MAX_SPECIES][7], alt[PIC_MAX_SPECIES][7], pid[PIC_MAX_SPECIES][2], key, rank, counts, starts, fftwork,
+        total;
 };
+
+// Particle bins of the sorted deposit: CBR x CBZ cells in (r, z); the deposit tile of a bin
+// reaches CPAD cells past it on every side.
+constexpr int CBR = 8, CBZ = 16, CPAD = 2, CTR = CBR + 2 * CPAD, CTZ = CBZ + 2 * CPAD;
+int cyl_nbz(int nz) { return (nz + CBZ - 1) / CBZ; }
+int cyl_nbins(int nr, int nz) { return ((nr + CBR - 1) / CBR) * cyl_nbz(nz); }
 
 constexpr int GDESC_MAX = 64;   // matrix-product batches per launch: M * 6
 
@@ -124,8 +136,19 @@ CylLayout cyl_layout(const pic_cyl_config& c, const int64_t* n, int ns, size_t f
     L.gdesc = take(2 * 3 * GDESC_MAX * sizeof(void*));
     L.wsum = take(1024 * 8);
     L.status = take(8);
-    for (int k = 0; k < ns; ++k)
+    int64_t nmax = 0;
+    for (int k = 0; k < ns; ++k) {
         for (int q = 0; q < 7; ++q) L.sp[k][q] = take(n[k] * T);
+        for (int q = 0; q < 7; ++q) L.alt[k][q] = take(n[k] * T);
+        L.pid[k][0] = take(n[k] * 4);
+        L.pid[k][1] = take(n[k] * 4);
+        nmax = std::max(nmax, n[k]);
+    }
+    L.key = take(nmax * 4);
+    L.rank = take(nmax * 4);
+    const size_t nb = cyl_nbins(c.nr, c.nz);
+    L.counts = take(nb * 4);
+    L.starts = take((nb + 1) * 4);
     L.fftwork = take(std::max<size_t>(fft_work, 1));
     L.total = o;
     return L;
@@ -558,9 +581,12 @@ __device__ void cyl_gather(const CylPassK<T>& p, T x, T y, T z, T* E, T* B, bool
 }
 
 // Add values val[0..nq) (component offsets q0 ..) at (x, y, z) to the mode deposits:
-// sum val S_r S_z e^{-i m theta} / V_j, fold factors by component kind.
+// sum val S_r S_z e^{-i m theta} / V_j, fold factors by component kind. Nodes inside the
+// bin's shared-memory tile (rows tj0 .. tj0 + CTR - 1, columns tl0 .. tl0 + CTZ - 1 modulo
+// nz; layout [M][4][CTR][CTZ] complex) are added there, the others to global memory.
 template <typename T>
-__device__ void cyl_deposit(const CylPassK<T>& p, T x, T y, T z, int q0, int nq, const T* val) {
+__device__ void cyl_deposit(const CylPassK<T>& p, T* tile, int tj0, int tl0, T x, T y, T z, int q0, int nq,
+                            const T* val) {
     typedef typename cplx<T>::type C;
     const T r = sqrt(x * x + y * y);
     const T cs = r > (T)0 ? x / r : (T)1, sn = r > (T)0 ? y / r : (T)0;
@@ -571,6 +597,27 @@ __device__ void cyl_deposit(const CylPassK<T>& p, T x, T y, T z, int q0, int nq,
     axial_stencil(p, z, l0, l1, wz0, wz1);
     const int64_t G = (int64_t)p.nr * p.nz;
     const T iv0 = (T)1 / (p.c2pi_drdz * ((T)j0 + (T)0.5)), iv1 = (T)1 / (p.c2pi_drdz * ((T)j1 + (T)0.5));
+    // tile coordinates of the four nodes (-1: outside the tile)
+    auto tcol = [&](int l) {
+        int d = l - tl0;
+        if (d < 0) d += p.nz;
+        if (d >= p.nz) d -= p.nz;
+        return d < CTZ ? d : -1;
+    };
+    const int tr0 = (j0 - tj0 >= 0 && j0 - tj0 < CTR) ? j0 - tj0 : -1;
+    const int tr1 = (j1 - tj0 >= 0 && j1 - tj0 < CTR) ? j1 - tj0 : -1;
+    const int tc0 = tcol(l0), tc1 = tcol(l1);
+    auto add = [&](int m, int q, int jj, int ll, int tr, int tc, T re, T im) {
+        if (tile && tr >= 0 && tc >= 0) {
+            T* t = tile + 2 * ((((int64_t)m * 4 + q) * CTR + tr) * CTZ + tc);
+            atomicAdd(t, re);
+            atomicAdd(t + 1, im);
+        } else {
+            T* d = reinterpret_cast<T*>(p.D + ((int64_t)m * 4 + q) * G + (int64_t)jj * p.nz + ll);
+            atomicAdd(d, re);
+            atomicAdd(d + 1, im);
+        }
+    };
     C ph = mk<C>(1.0, 0.0);                // e^{-i m theta}
     const C rot = mk<C>(cs, -sn);
     for (int m = 0; m < p.M; ++m) {
@@ -580,20 +627,11 @@ __device__ void cyl_deposit(const CylPassK<T>& p, T x, T y, T z, int q0, int nq,
             const int q = q0 + k;
             const T fac = ghost ? ((q >= 2) ? sflip : vflip) : (T)1;   // J_z, rho: scalars
             const T a0 = val[k] * wr0 * fac * iv0, a1 = val[k] * wr1 * iv1;
-            C* D = p.D + ((int64_t)m * 4 + q) * G;
             const T c00 = a0 * wz0, c01 = a0 * wz1, c10 = a1 * wz0, c11 = a1 * wz1;
-            T* d00 = reinterpret_cast<T*>(&D[(int64_t)j0 * p.nz + l0]);
-            T* d01 = reinterpret_cast<T*>(&D[(int64_t)j0 * p.nz + l1]);
-            T* d10 = reinterpret_cast<T*>(&D[(int64_t)j1 * p.nz + l0]);
-            T* d11 = reinterpret_cast<T*>(&D[(int64_t)j1 * p.nz + l1]);
-            atomicAdd(d00, c00 * ph.x);
-            atomicAdd(d00 + 1, c00 * ph.y);
-            atomicAdd(d01, c01 * ph.x);
-            atomicAdd(d01 + 1, c01 * ph.y);
-            atomicAdd(d10, c10 * ph.x);
-            atomicAdd(d10 + 1, c10 * ph.y);
-            atomicAdd(d11, c11 * ph.x);
-            atomicAdd(d11 + 1, c11 * ph.y);
+            add(m, q, j0, l0, tr0, tc0, c00 * ph.x, c00 * ph.y);
+            add(m, q, j0, l1, tr0, tc1, c01 * ph.x, c01 * ph.y);
+            add(m, q, j1, l0, tr1, tc0, c10 * ph.x, c10 * ph.y);
+            add(m, q, j1, l1, tr1, tc1, c11 * ph.x, c11 * ph.y);
         }
         ph = cmul(ph, rot);
     }
@@ -607,17 +645,30 @@ __device__ __forceinline__ T wrap_len(T z, T L) {
     return z;
 }
 
-// One thread per particle. step: gather at x^n, Boris, half drift, J^{n+1/2}, half
-// drift, rho^{n+1}; deposit only (step = 0): rho at the current positions.
+// One CTA per (r, z) bin of CBR x CBZ cells, its particles (sorted by bin) one per thread.
+// step: gather at x^n, Boris, half drift, J^{n+1/2}, half drift, rho^{n+1}; deposit only
+// (step = 0): rho at the current positions. The deposits of the bin's particles are summed
+// in a shared-memory tile reaching CPAD cells past the bin, which is then added to the
+// global mode arrays once; a particle whose stencil leaves the tile adds there directly.
 template <typename T>
-__global__ void __launch_bounds__(256) cyl_particle_kernel(CylPassK<T> p, int step) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n; i += (int64_t)gridDim.x * blockDim.x) {
+__global__ void __launch_bounds__(256) cyl_particle_kernel(CylPassK<T> p, const int32_t* __restrict__ starts,
+                                                           int nbz, int step) {
+    typedef typename cplx<T>::type C;
+    extern __shared__ __align__(16) unsigned char cyl_smem[];
+    T* tile = reinterpret_cast<T*>(cyl_smem);
+    const int nt = p.M * 4 * CTR * CTZ;
+    const int bin = blockIdx.x;
+    const int tj0 = (bin / nbz) * CBR - CPAD, tl0 = (bin % nbz) * CBZ - CPAD;
+    for (int t = threadIdx.x; t < 2 * nt; t += blockDim.x) tile[t] = (T)0;
+    __syncthreads();
+    const int beg = starts[bin], end = starts[bin + 1];
+    for (int i = beg + threadIdx.x; i < end; i += blockDim.x) {
         T x = p.x[i], y = p.y[i], z = p.z[i];
         T ux = p.ux[i], uy = p.uy[i], uz = p.uz[i];
         const T qw = p.q * p.w[i];
         if (!step) {
             const T val[1] = {qw};
-            cyl_deposit(p, x, y, z, 3, 1, val);
+            cyl_deposit(p, tile, tj0, tl0, x, y, z, 3, 1, val);
             continue;
         }
         T E[3], B[3];
@@ -644,13 +695,13 @@ __global__ void __launch_bounds__(256) cyl_particle_kernel(CylPassK<T> p, int st
             const T r = sqrt(x * x + y * y);
             const T cs = r > (T)0 ? x / r : (T)1, sn = r > (T)0 ? y / r : (T)0;
             const T val[3] = {qw * (vx * cs + vy * sn), qw * (-vx * sn + vy * cs), qw * vz};
-            cyl_deposit(p, x, y, z, 0, 3, val);
+            cyl_deposit(p, tile, tj0, tl0, x, y, z, 0, 3, val);
         }
         x += vx * p.hdt;
         y += vy * p.hdt;
         z = wrap_len(z + (vz - p.vgal) * p.hdt, p.Lz);
         const T val[1] = {qw};
-        cyl_deposit(p, x, y, z, 3, 1, val);
+        cyl_deposit(p, tile, tj0, tl0, x, y, z, 3, 1, val);
         p.x[i] = x;
         p.y[i] = y;
         p.z[i] = z;
@@ -658,6 +709,93 @@ __global__ void __launch_bounds__(256) cyl_particle_kernel(CylPassK<T> p, int st
         p.uy[i] = uy;
         p.uz[i] = uz;
     }
+    __syncthreads();
+    const int64_t G = (int64_t)p.nr * p.nz;
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+        const T re = tile[2 * t], im = tile[2 * t + 1];
+        if (re == (T)0 && im == (T)0) continue;
+        const int tc = t % CTZ, tr = (t / CTZ) % CTR, mq = t / (CTZ * CTR);
+        const int jj = tj0 + tr;
+        int ll = tl0 + tc;
+        if (ll < 0) ll += p.nz;
+        if (ll >= p.nz) ll -= p.nz;
+        if (jj < 0 || jj >= p.nr || ll < 0 || ll >= p.nz) continue;   // never written
+        T* d = reinterpret_cast<T*>(p.D + (int64_t)mq * G + (int64_t)jj * p.nz + ll);
+        atomicAdd(d, re);
+        atomicAdd(d + 1, im);
+    }
+}
+
+// ---- sorting particles into (r, z) bins (counting sort; order inside a bin follows the
+// atomic ranks) -------------------------------------------------------------------------
+
+template <typename T>
+__global__ void cyl_key_kernel(const T* __restrict__ x, const T* __restrict__ y, const T* __restrict__ z, int64_t n,
+                               T inv_dr, T inv_dz, int nr, int nz, int nbz, int32_t* key, int32_t* rank,
+                               int32_t* counts) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const T r = sqrt(x[i] * x[i] + y[i] * y[i]);
+        const T u = r * inv_dr, v = floor(z[i] * inv_dz);
+        int jc = (u >= (T)0 && u < (T)nr) ? (int)u : nr - 1;   // beyond the extent (flagged later): last bin row
+        int lc = (v >= (T)-nz && v < (T)(2 * nz)) ? (int)v : 0;
+        if (lc < 0) lc += nz;
+        if (lc >= nz) lc -= nz;
+        const int k = (jc / CBR) * nbz + lc / CBZ;
+        key[i] = k;
+        rank[i] = atomicAdd(&counts[k], 1);
+    }
+}
+
+// Exclusive scan of the bin counts (one CTA of 1024 threads, each a contiguous segment).
+__global__ void __launch_bounds__(1024) cyl_scan_kernel(const int32_t* __restrict__ counts, int32_t* starts,
+                                                        int nbins) {
+    __shared__ int32_t part[1024];
+    const int per = (nbins + 1023) / 1024;
+    const int a = threadIdx.x * per, e = min(a + per, nbins);
+    int sum = 0;
+    for (int i = a; i < e; ++i) sum += counts[i];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int run = part[threadIdx.x] - sum;
+    for (int i = a; i < e; ++i) {
+        starts[i] = run;
+        run += counts[i];
+    }
+    if (threadIdx.x == 1023) starts[nbins] = part[1023];
+}
+
+struct CylArrays {
+    void* a[7];      // w, x, y, z, ux, uy, uz
+    int32_t* pid;
+};
+
+template <typename T>
+__global__ void cyl_scatter_kernel(CylArrays src, CylArrays dst, int64_t n, const int32_t* __restrict__ key,
+                                   const int32_t* __restrict__ rank, const int32_t* __restrict__ starts) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = (int64_t)starts[key[i]] + rank[i];
+#pragma unroll
+        for (int q = 0; q < 7; ++q) reinterpret_cast<T*>(dst.a[q])[o] = reinterpret_cast<const T*>(src.a[q])[i];
+        dst.pid[o] = src.pid[i];
+    }
+}
+
+__global__ void cyl_iota_kernel(int32_t* pid, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        pid[i] = (int32_t)i;
+}
+
+// dst[pid[i]] = src[i]: a species array back in input order.
+template <typename T>
+__global__ void cyl_unpermute_kernel(const T* __restrict__ src, const int32_t* __restrict__ pid, T* dst, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[pid[i]] = src[i];
 }
 
 // W = (eps0/2) sum_m (1 or 2) sum_{j,l} (|E|^2 + c^2 |B|^2) V_j over the real mode fields.
@@ -873,18 +1011,54 @@ CylPassK<T> passk(pic_cyl* s, int k) {
     return p;
 }
 
-int particles(pic_cyl* s, int step, cudaStream_t st) {
-    const size_t C = s->cfg.precision == 64 ? 16 : 8;
-    GP_CUDA(cudaMemsetAsync(s->Dr, 0, (size_t)s->cfg.nmodes * 4 * s->G * C, st));
+// Counting sort of species k into the (r, z) bins: keys and ranks, bin starts, scatter of
+// every array (and the input indices) into the other buffer, then the buffers swap.
+template <typename T>
+int sort_species(pic_cyl* s, int k, cudaStream_t st) {
+    pic_cyl::Sp& sp = s->sp[k];
+    const int64_t n = sp.n;
+    GP_CUDA(cudaMemsetAsync(s->counts, 0, (size_t)s->nbins * 4, st));
+    cyl_key_kernel<T><<<gridn(n), 256, 0, st>>>((const T*)sp.x[0], (const T*)sp.x[1], (const T*)sp.x[2], n,
+                                                (T)(1.0 / s->cfg.dr), (T)(1.0 / s->cfg.dz), s->cfg.nr, s->cfg.nz,
+                                                s->nbz, s->key, s->rank, s->counts);
+    cyl_scan_kernel<<<1, 1024, 0, st>>>(s->counts, s->starts, s->nbins);
+    CylArrays src, dst;
+    void* cur[7] = {sp.w, sp.x[0], sp.x[1], sp.x[2], sp.u[0], sp.u[1], sp.u[2]};
+    for (int q = 0; q < 7; ++q) {
+        src.a[q] = cur[q];
+        dst.a[q] = sp.alt[q];
+    }
+    src.pid = sp.pid;
+    dst.pid = sp.pid_alt;
+    cyl_scatter_kernel<T><<<gridn(n), 256, 0, st>>>(src, dst, n, s->key, s->rank, s->starts);
+    GP_CUDA(cudaGetLastError());
+    sp.w = dst.a[0];
+    for (int d = 0; d < 3; ++d) {
+        sp.x[d] = dst.a[1 + d];
+        sp.u[d] = dst.a[4 + d];
+    }
+    for (int q = 0; q < 7; ++q) sp.alt[q] = cur[q];
+    std::swap(sp.pid, sp.pid_alt);
+    return PIC_OK;
+}
+
+template <typename T>
+int particles_t(pic_cyl* s, int step, cudaStream_t st) {
+    const size_t tile = (size_t)s->cfg.nmodes * 4 * CTR * CTZ * 2 * sizeof(T);
+    GP_CUDA(cudaFuncSetAttribute(cyl_particle_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile));
     for (int k = 0; k < s->nspecies; ++k) {
         if (s->sp[k].n == 0) continue;
-        if (s->cfg.precision == 64)
-            cyl_particle_kernel<double><<<gridn(s->sp[k].n), 256, 0, st>>>(passk<double>(s, k), step);
-        else
-            cyl_particle_kernel<float><<<gridn(s->sp[k].n), 256, 0, st>>>(passk<float>(s, k), step);
+        GP_CHECK(sort_species<T>(s, k, st));
+        cyl_particle_kernel<T><<<s->nbins, 256, tile, st>>>(passk<T>(s, k), s->starts, s->nbz, step);
         GP_CUDA(cudaGetLastError());
     }
     return PIC_OK;
+}
+
+int particles(pic_cyl* s, int step, cudaStream_t st) {
+    const size_t C = s->cfg.precision == 64 ? 16 : 8;
+    GP_CUDA(cudaMemsetAsync(s->Dr, 0, (size_t)s->cfg.nmodes * 4 * s->G * C, st));
+    return s->cfg.precision == 64 ? particles_t<double>(s, step, st) : particles_t<float>(s, step, st);
 }
 
 int make_plans(pic_cyl* s, size_t* work) {
@@ -995,7 +1169,16 @@ int pic_cyl_init(const pic_cyl_config* cfg, const pic_cyl_species* species, int 
             s->sp[k].x[d] = w + L.sp[k][1 + d];
             s->sp[k].u[d] = w + L.sp[k][4 + d];
         }
+        for (int q = 0; q < 7; ++q) s->sp[k].alt[q] = w + L.alt[k][q];
+        s->sp[k].pid = (int32_t*)(w + L.pid[k][0]);
+        s->sp[k].pid_alt = (int32_t*)(w + L.pid[k][1]);
     }
+    s->key = (int32_t*)(w + L.key);
+    s->rank = (int32_t*)(w + L.rank);
+    s->counts = (int32_t*)(w + L.counts);
+    s->starts = (int32_t*)(w + L.starts);
+    s->nbz = cyl_nbz(cfg->nz);
+    s->nbins = cyl_nbins(cfg->nr, cfg->nz);
 #define CYL_TRY(expr)           \
     do {                        \
         int rc_ = (expr);       \
@@ -1011,6 +1194,7 @@ int pic_cyl_init(const pic_cyl_config* cfg, const pic_cyl_species* species, int 
         const size_t b = (size_t)species[k].n * T;
         if (!b) continue;
         CYL_CUDA(cudaMemcpyAsync(s->sp[k].w, species[k].w, b, cudaMemcpyDefault, st));
+        cyl_iota_kernel<<<gridn(species[k].n), 256, 0, st>>>(s->sp[k].pid, species[k].n);
         for (int d = 0; d < 3; ++d) {
             CYL_CUDA(cudaMemcpyAsync(s->sp[k].x[d], species[k].x[d], b, cudaMemcpyDefault, st));
             CYL_CUDA(cudaMemcpyAsync(s->sp[k].u[d], species[k].u[d], b, cudaMemcpyDefault, st));
@@ -1180,10 +1364,23 @@ int pic_cyl_get(pic_cyl* s, int which, void* dst, size_t bytes, void* stream) {
 
 int pic_cyl_get_particles(pic_cyl* s, int k, void* x[3], void* u[3], void* stream) {
     if (!s || k < 0 || k >= s->nspecies || !x || !u) return fail(PIC_EINVAL, "bad cyl run, species or arrays");
-    const size_t b = (size_t)s->sp[k].n * (s->cfg.precision == 64 ? 8 : 4);
-    for (int d = 0; d < 3; ++d) {
-        if (x[d]) GP_CUDA(cudaMemcpyAsync(x[d], s->sp[k].x[d], b, cudaMemcpyDefault, (cudaStream_t)stream));
-        if (u[d]) GP_CUDA(cudaMemcpyAsync(u[d], s->sp[k].u[d], b, cudaMemcpyDefault, (cudaStream_t)stream));
+    // the run keeps its particles sorted by bin: each array goes back to input order through
+    // the sort's other buffer (free between steps), then out
+    cudaStream_t st = (cudaStream_t)stream;
+    const pic_cyl::Sp& sp = s->sp[k];
+    const int64_t n = sp.n;
+    const size_t b = (size_t)n * (s->cfg.precision == 64 ? 8 : 4);
+    for (int d = 0; d < 6; ++d) {
+        void* dst = d < 3 ? x[d] : u[d - 3];
+        if (!dst || n == 0) continue;
+        const void* src = d < 3 ? sp.x[d] : sp.u[d - 3];
+        void* tmp = sp.alt[1 + d];
+        if (s->cfg.precision == 64)
+            cyl_unpermute_kernel<double><<<gridn(n), 256, 0, st>>>((const double*)src, sp.pid, (double*)tmp, n);
+        else
+            cyl_unpermute_kernel<float><<<gridn(n), 256, 0, st>>>((const float*)src, sp.pid, (float*)tmp, n);
+        GP_CUDA(cudaGetLastError());
+        GP_CUDA(cudaMemcpyAsync(dst, tmp, b, cudaMemcpyDefault, st));
     }
     return PIC_OK;
 }

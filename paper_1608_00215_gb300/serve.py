@@ -202,7 +202,8 @@ def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_
           sleep: float = 2e-4, keep_final_state: bool = False, on_retire=None,
           priorities: bool = True, admit_per_poll: int = 1,
           max_per_level: Optional[Sequence[int]] = (2, 4, 64, 64),
-          shared_launches: bool = False, share_max_cells: int = 64 * 64 * 128) -> ServeResult:
+          shared_launches: bool = False, share_max_cells: int = 64 * 64 * 128,
+          shared_bucket_runs: int = 8) -> ServeResult:
     """Run all requests with continuous batching; returns per-run records.
 
     ``max_slots = 1`` gives the serial baseline on the same arrival trace.
@@ -217,7 +218,8 @@ def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_
     no throughput, only latency to every run sharing the device with them.
     ``shared_launches``: advance runs of at most ``share_max_cells`` cells in buckets of
     one shape class with pic_step_many (max_per_level then applies to the runs stepped
-    alone only).
+    alone only); a bucket takes at most ``shared_bucket_runs`` runs, further runs of the
+    class open further buckets on streams of their own.
     """
     prange = torch.cuda.Stream.priority_range() if priorities else (0, 0)
     if hbm_budget is None:
@@ -342,11 +344,20 @@ def serve(requests: Sequence[Request], *, hbm_budget: Optional[int] = None, max_
             prec = precision if precision is not None else wl.precision
             margin, deposit = run_strategy(wl, prec)
             if shared:
+                # buckets of one shape class hold at most shared_bucket_runs runs each, on
+                # streams of their own, so that one bucket's sort and transforms overlap
+                # another's particle pass
                 key = share_key(wl, prec, margin, deposit)
-                bk = buckets.get(key)
-                if bk is None:
-                    bk = _Bucket(key, torch.cuda.Stream(priority=rec.priority), gp.ManyWorkspace(device))
-                    buckets[key] = bk
+                idx = 0
+                while True:
+                    bk = buckets.get((key, idx))
+                    if bk is None:
+                        bk = _Bucket((key, idx), torch.cuda.Stream(priority=rec.priority), gp.ManyWorkspace(device))
+                        buckets[(key, idx)] = bk
+                        break
+                    if len(bk.runs) + len(bk.joining) < shared_bucket_runs:
+                        break
+                    idx += 1
                 stream = bk.stream
             else:
                 stream = torch.cuda.Stream(priority=rec.priority)
