@@ -265,7 +265,7 @@ def cylindrical_leg(steps, warmup, hbm, peak_kind, nr=256, nz=2048, nmodes=2, pp
             "roofline_particles": {"bound": "hbm", "kernel": "cyl_particle_kernel<float>", "achieved": part_gbs,
                                    "peak": hbm, "unit": "GB/s", "frac": part_gbs / hbm, "traffic": None,
                                    "peak_kind": peak_kind, "algorithmic_bytes_per_launch": part_bytes,
-                                   "note": "deposit by global float atomics (16 per particle per mode)"},
+                                   "note": "bin tiles in shared memory summed in 64-bit fixed point, added to the global mode arrays once per bin"},
             "roofline_radial_products": {"bound": "alu", "kernel": "radial_matmul_kernel<float>",
                                          "achieved": mm_tf, "peak": fpk, "unit": "TFLOP/s", "frac": mm_tf / fpk,
                                          "algorithmic_flops_per_launch": mm_flops / 2},

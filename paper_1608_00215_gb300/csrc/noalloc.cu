@@ -18,7 +18,9 @@ constexpr int NOALLOC_BLOCKS = 1024;
 constexpr size_t NOALLOC_PART_BYTES = 2 * NOALLOC_BLOCKS * sizeof(double);   // 16 KiB
 constexpr int64_t NOALLOC_MAX_CELLS = (int64_t)1 << 30;
 
-// [0, 16 KiB): per-block sums of E^2 and B^2; then one int32 status word.
+// [0, 16 KiB): per-block sums of E^2 and B^2; then one int32 word that receives the
+// shared energy launcher's non-finite flag. Nothing reads that word (a non-finite field
+// makes W itself non-finite, which is what callers see), so it is never cleared.
 static __device__ __align__(256) unsigned char g_energy_scratch[NOALLOC_PART_BYTES + 256];
 
 // Device address of g_energy_scratch per device ordinal (the symbol's name is only a
@@ -62,7 +64,6 @@ extern "C" int pic_field_energy_noalloc(const void* fields, int64_t n_cells, int
     cudaStream_t st = (cudaStream_t)stream;
     double* part = (double*)scratch;
     int32_t* status = (int32_t*)((char*)scratch + NOALLOC_PART_BYTES);
-    GP_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), st));
     int64_t nb = (n_cells + 2047) / 2048;
     if (nb > NOALLOC_BLOCKS) nb = NOALLOC_BLOCKS;
     return launch_energy_on(fields, n_cells, precision, part, (int)nb, status, 0.5 * eps0 * dV,
