@@ -1673,6 +1673,7 @@ __device__ __forceinline__ void cell_pass_body(const PassK<T>& p, const int b) {
             if (!PIC_INDEX_OK(Bend - A, (int64_t)sp.n + 1, p.status)) A = Bend = 0;
             for (int lo = A; lo < Bend; lo += CELL_CHUNK) {
                 const int hi = min(lo + CELL_CHUNK, Bend);
+                bool moved = false;   // a particle of this lane changed cell in this chunk
                 // stage in, coalesced
                 for (int j = lane; j < hi - lo; j += 32) {
                     const int q = cell_slot(j);
@@ -1804,7 +1805,9 @@ __device__ __forceinline__ void cell_pass_body(const PassK<T>& p, const int b) {
                         deposit_global<T, NW, 0>(p, ix, iy, iz, wx, wy, wz, 3, 1, qr);
                     }
                     if (MODE == PASS_STEP) {
-                        st_cell[j] = (ix * p.ny + iy) * p.nz + iz;
+                        const int nc = (ix * p.ny + iy) * p.nz + iz;
+                        moved = moved || nc != c;
+                        st_cell[j] = nc;
                         st_v[0 * CELL_STRIDE + j] = fx;
                         st_v[1 * CELL_STRIDE + j] = fy;
                         st_v[2 * CELL_STRIDE + j] = fz;
@@ -1937,10 +1940,11 @@ __device__ __forceinline__ void cell_pass_body(const PassK<T>& p, const int b) {
                     }
                 }
                 __syncwarp();
-                if (MODE == PASS_STEP) {   // stage out, coalesced
+                if (MODE == PASS_STEP) {   // stage out, coalesced; the cells only if one changed
+                    const bool any_moved = __any_sync(0xffffffffu, moved);
                     for (int j = lane; j < hi - lo; j += 32) {
                         const int q = cell_slot(j);
-                        sp.cell[lo + j] = st_cell[q];
+                        if (any_moved) sp.cell[lo + j] = st_cell[q];
 #pragma unroll
                         for (int d = 0; d < 3; ++d) {
                             sp.off[d][lo + j] = st_v[d * CELL_STRIDE + q];
