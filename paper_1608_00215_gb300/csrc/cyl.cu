@@ -541,9 +541,12 @@ __device__ __forceinline__ void axial_stencil(const CylPassK<T>& p, T z, int& l0
     w1 = f;
 }
 
-// Real E and B (Cartesian) at (x, y, z) from the mode fields.
+// Real E and B (Cartesian) at (x, y, z) from the mode fields: from the bin's field tile
+// ftile ([M][6][CTR][CTZ] complex, rows tj0 .., columns tl0 .. modulo nz) when the stencil
+// lies inside it, else from global memory.
 template <typename T>
-__device__ void cyl_gather(const CylPassK<T>& p, T x, T y, T z, T* E, T* B, bool& ok) {
+__device__ void cyl_gather(const CylPassK<T>& p, const typename cplx<T>::type* ftile, int tj0, int tl0, T x, T y,
+                           T z, T* E, T* B, bool& ok) {
     typedef typename cplx<T>::type C;
     const T r = sqrt(x * x + y * y);
     const T cs = r > (T)0 ? x / r : (T)1, sn = r > (T)0 ? y / r : (T)0;
@@ -555,18 +558,34 @@ __device__ void cyl_gather(const CylPassK<T>& p, T x, T y, T z, T* E, T* B, bool
     if (ok) {
         axial_stencil(p, z, l0, l1, wz0, wz1);
         const int64_t G = (int64_t)p.nr * p.nz;
+        int tc0 = l0 - tl0, tc1 = l1 - tl0;
+        if (tc0 < 0) tc0 += p.nz;
+        if (tc1 < 0) tc1 += p.nz;
+        const int tr0 = j0 - tj0, tr1 = j1 - tj0;
+        const bool intile = ftile && tr0 >= 0 && tr1 < CTR && tc0 < CTZ && tc1 < CTZ;
         C ph = mk<C>(1.0, 0.0);            // e^{i m theta}
         const C rot = mk<C>(cs, sn);
         for (int m = 0; m < p.M; ++m) {
             const T sflip = (m & 1) ? (T)-1 : (T)1;   // (-1)^m: scalars, z components
             const T vflip = -sflip;                    // (-1)^(m+1): r and theta components
             for (int q = 0; q < 6; ++q) {
-                const C* F = p.F + ((int64_t)m * 6 + q) * G;
                 const T fac = ghost ? ((q == 2 || q == 5) ? sflip : vflip) : (T)1;
                 const T a0 = wr0 * fac, a1 = wr1;
                 C v = mk<C>(0.0, 0.0);
-                const C f00 = F[(int64_t)j0 * p.nz + l0], f01 = F[(int64_t)j0 * p.nz + l1];
-                const C f10 = F[(int64_t)j1 * p.nz + l0], f11 = F[(int64_t)j1 * p.nz + l1];
+                C f00, f01, f10, f11;
+                if (intile) {
+                    const C* F = ftile + ((int64_t)m * 6 + q) * CTR * CTZ;
+                    f00 = F[tr0 * CTZ + tc0];
+                    f01 = F[tr0 * CTZ + tc1];
+                    f10 = F[tr1 * CTZ + tc0];
+                    f11 = F[tr1 * CTZ + tc1];
+                } else {
+                    const C* F = p.F + ((int64_t)m * 6 + q) * G;
+                    f00 = F[(int64_t)j0 * p.nz + l0];
+                    f01 = F[(int64_t)j0 * p.nz + l1];
+                    f10 = F[(int64_t)j1 * p.nz + l0];
+                    f11 = F[(int64_t)j1 * p.nz + l1];
+                }
                 v.x = a0 * (wz0 * f00.x + wz1 * f01.x) + a1 * (wz0 * f10.x + wz1 * f11.x);
                 v.y = a0 * (wz0 * f00.y + wz1 * f01.y) + a1 * (wz0 * f10.y + wz1 * f11.y);
                 Fr[q] += (m == 0) ? v.x : (T)2 * (v.x * ph.x - v.y * ph.y);
@@ -659,11 +678,24 @@ __global__ void __launch_bounds__(256) cyl_particle_kernel(CylPassK<T> p, const 
                                                            int nbz, int step) {
     typedef typename cplx<T>::type C;
     extern __shared__ __align__(16) unsigned char cyl_smem[];
-    T* tile = reinterpret_cast<T*>(cyl_smem);
     const int nt = p.M * 4 * CTR * CTZ;
+    T* tile = reinterpret_cast<T*>(cyl_smem);
+    C* ftile = reinterpret_cast<C*>(cyl_smem + (size_t)2 * nt * sizeof(T));   // [M][6][CTR][CTZ]
     const int bin = blockIdx.x;
     const int tj0 = (bin / nbz) * CBR - CPAD, tl0 = (bin % nbz) * CBZ - CPAD;
     for (int t = threadIdx.x; t < 2 * nt; t += blockDim.x) tile[t] = (T)0;
+    if (step) {   // the bin's mode fields (nodes outside 0 .. nr - 1 are never read)
+        const int64_t G = (int64_t)p.nr * p.nz;
+        for (int t = threadIdx.x; t < p.M * 6 * CTR * CTZ; t += blockDim.x) {
+            const int tc = t % CTZ, tr = (t / CTZ) % CTR, mq = t / (CTZ * CTR);
+            const int jj = tj0 + tr;
+            int ll = tl0 + tc;
+            if (ll < 0) ll += p.nz;
+            if (ll >= p.nz) ll -= p.nz;
+            ftile[t] = (jj >= 0 && jj < p.nr && ll >= 0 && ll < p.nz) ? p.F[(int64_t)mq * G + (int64_t)jj * p.nz + ll]
+                                                                     : mk<C>(0.0, 0.0);
+        }
+    }
     __syncthreads();
     const int beg = starts[bin], end = starts[bin + 1];
     for (int i = beg + threadIdx.x; i < end; i += blockDim.x) {
@@ -677,7 +709,7 @@ __global__ void __launch_bounds__(256) cyl_particle_kernel(CylPassK<T> p, const 
         }
         T E[3], B[3];
         bool ok;
-        cyl_gather(p, x, y, z, E, B, ok);
+        cyl_gather(p, ftile, tj0, tl0, x, y, z, E, B, ok);
         const T a = p.qdt2m;
         const T umx = ux + a * E[0], umy = uy + a * E[1], umz = uz + a * E[2];
         const T igm = (T)1 / sqrt((T)1 + (umx * umx + umy * umy + umz * umz) * p.inv_c2);
@@ -1056,7 +1088,7 @@ int sort_species(pic_cyl* s, int k, cudaStream_t st) {
 
 template <typename T>
 int particles_t(pic_cyl* s, int step, cudaStream_t st) {
-    const size_t tile = (size_t)s->cfg.nmodes * 4 * CTR * CTZ * 2 * sizeof(T);
+    const size_t tile = (size_t)s->cfg.nmodes * CTR * CTZ * (4 * 2 * sizeof(T) + 6 * 2 * sizeof(T));
     GP_CUDA(cudaFuncSetAttribute(cyl_particle_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile));
     for (int k = 0; k < s->nspecies; ++k) {
         if (s->sp[k].n == 0) continue;
