@@ -60,3 +60,20 @@ def test_nearest_rank_percentiles(serve):
     assert res.percentile(50) == 3.0 and res.percentile(99) == 5.0 and res.percentile(1) == 1.0
     assert res.runs_per_s == 1.0
     assert math.isnan(serve.ServeResult([bad], 1.0, 1, 1).percentile(50))
+
+
+def test_run_strategy_and_share_key(serve):
+    """FP32 linear runs take the one-thread-per-cell pass; cubic, FP64 and deterministic
+    runs the default grouped deposit; the strategy is part of the shared-launch key, so
+    runs of different strategies never share launches."""
+    lin = gi.drifting_plasma(32, 32, 32, 10.0, shape_order=1, precision=32)
+    cub = gi.drifting_plasma(32, 32, 32, 10.0, shape_order=3, precision=32)
+    assert serve.run_strategy(lin, 32) == (1, 4)
+    assert serve.run_strategy(lin, 64) == (1, 0)
+    assert serve.run_strategy(cub, 32) == (1, 0)
+    det = gi.drifting_plasma(32, 32, 32, 10.0, shape_order=1, precision=32)
+    det.deterministic = 1
+    assert serve.run_strategy(det, 32) == (1, 0)
+    assert serve.share_key(lin, 32, 1, 4) != serve.share_key(lin, 32, 1, 0)
+    assert serve.share_key(lin, 32, 1, 4) == serve.share_key(
+        gi.drifting_plasma(32, 32, 32, 30.0, shape_order=1, precision=32, seed=9), 32, 1, 4)
