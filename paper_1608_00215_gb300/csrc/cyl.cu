@@ -604,10 +604,12 @@ __device__ void cyl_gather(const CylPassK<T>& p, const typename cplx<T>::type* f
 // Add values val[0..nq) (component offsets q0 ..) at (x, y, z) to the mode deposits:
 // sum val S_r S_z e^{-i m theta} / V_j, fold factors by component kind. Nodes inside the
 // bin's shared-memory tile (rows tj0 .. tj0 + CTR - 1, columns tl0 .. tl0 + CTZ - 1 modulo
-// nz; layout [M][4][CTR][CTZ] complex) are added there, the others to global memory.
+// nz; layout [M][4][CTR][CTZ] complex) are added there, the others to global memory. With
+// itile (FP32 runs) the tile holds 32-bit fixed point, value * scale rounded: native
+// integer atomics instead of the compare-and-swap loops of shared float atomics.
 template <typename T>
 __device__ void cyl_deposit(const CylPassK<T>& p, T* tile, int tj0, int tl0, T x, T y, T z, int q0, int nq,
-                            const T* val) {
+                            const T* val, int* itile = nullptr, T scale = (T)1) {
     typedef typename cplx<T>::type C;
     const T r = sqrt(x * x + y * y);
     const T cs = r > (T)0 ? x / r : (T)1, sn = r > (T)0 ? y / r : (T)0;
@@ -629,7 +631,11 @@ __device__ void cyl_deposit(const CylPassK<T>& p, T* tile, int tj0, int tl0, T x
     const int tr1 = (j1 - tj0 >= 0 && j1 - tj0 < CTR) ? j1 - tj0 : -1;
     const int tc0 = tcol(l0), tc1 = tcol(l1);
     auto add = [&](int m, int q, int jj, int ll, int tr, int tc, T re, T im) {
-        if (tile && tr >= 0 && tc >= 0) {
+        if (itile && tr >= 0 && tc >= 0) {
+            int* t = itile + 2 * (((m * 4 + q) * CTR + tr) * CTZ + tc);
+            atomicAdd(t, __float2int_rn((float)(re * scale)));
+            atomicAdd(t + 1, __float2int_rn((float)(im * scale)));
+        } else if (tile && tr >= 0 && tc >= 0) {
             T* t = tile + 2 * ((((int64_t)m * 4 + q) * CTR + tr) * CTZ + tc);
             atomicAdd(t, re);
             atomicAdd(t + 1, im);
@@ -696,15 +702,36 @@ __global__ void __launch_bounds__(256) cyl_particle_kernel(CylPassK<T> p, const 
                                                                      : mk<C>(0.0, 0.0);
         }
     }
-    __syncthreads();
     const int beg = starts[bin], end = starts[bin + 1];
+    // FP32: the tile sums in 32-bit fixed point. No node of the bin's deposit exceeds
+    // S = max(1, c) sum |q w| / V (V the smallest annulus of the tile), so with 2 S < 2^E
+    // the scale 2^(30 - E) keeps every sum inside 31 bits.
+    __shared__ float s_abs[8];
+    int* itile = nullptr;
+    T scale = (T)1;
+    if constexpr (sizeof(T) == 4) {
+        float a = 0.f;
+        for (int i = beg + threadIdx.x; i < end; i += blockDim.x) a += fabsf((float)(p.q * p.w[i]));
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if ((threadIdx.x & 31) == 0) s_abs[threadIdx.x >> 5] = a;
+        __syncthreads();
+        float sum = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += s_abs[w];
+        const float vmin = (float)p.c2pi_drdz * ((float)max(tj0, 0) + 0.5f);
+        const float bound = 2.f * fmaxf(1.f, sqrtf(1.f / (float)p.inv_c2)) * sum / vmin;
+        int E = 0;
+        if (bound > 0.f && bound < 3.0e38f) frexpf(bound, &E);
+        scale = (T)ldexpf(1.f, 30 - E);
+        itile = reinterpret_cast<int*>(tile);
+    }
+    __syncthreads();
     for (int i = beg + threadIdx.x; i < end; i += blockDim.x) {
         T x = p.x[i], y = p.y[i], z = p.z[i];
         T ux = p.ux[i], uy = p.uy[i], uz = p.uz[i];
         const T qw = p.q * p.w[i];
         if (!step) {
             const T val[1] = {qw};
-            cyl_deposit(p, tile, tj0, tl0, x, y, z, 3, 1, val);
+            cyl_deposit(p, tile, tj0, tl0, x, y, z, 3, 1, val, itile, scale);
             continue;
         }
         T E[3], B[3];
@@ -731,13 +758,13 @@ __global__ void __launch_bounds__(256) cyl_particle_kernel(CylPassK<T> p, const 
             const T r = sqrt(x * x + y * y);
             const T cs = r > (T)0 ? x / r : (T)1, sn = r > (T)0 ? y / r : (T)0;
             const T val[3] = {qw * (vx * cs + vy * sn), qw * (-vx * sn + vy * cs), qw * vz};
-            cyl_deposit(p, tile, tj0, tl0, x, y, z, 0, 3, val);
+            cyl_deposit(p, tile, tj0, tl0, x, y, z, 0, 3, val, itile, scale);
         }
         x += vx * p.hdt;
         y += vy * p.hdt;
         z = wrap_len(z + (vz - p.vgal) * p.hdt, p.Lz);
         const T val[1] = {qw};
-        cyl_deposit(p, tile, tj0, tl0, x, y, z, 3, 1, val);
+        cyl_deposit(p, tile, tj0, tl0, x, y, z, 3, 1, val, itile, scale);
         p.x[i] = x;
         p.y[i] = y;
         p.z[i] = z;
@@ -748,8 +775,16 @@ __global__ void __launch_bounds__(256) cyl_particle_kernel(CylPassK<T> p, const 
     __syncthreads();
     const int64_t G = (int64_t)p.nr * p.nz;
     for (int t = threadIdx.x; t < nt; t += blockDim.x) {
-        const T re = tile[2 * t], im = tile[2 * t + 1];
-        if (re == (T)0 && im == (T)0) continue;
+        T re, im;
+        if (itile) {
+            if (itile[2 * t] == 0 && itile[2 * t + 1] == 0) continue;
+            re = (T)itile[2 * t] / scale;
+            im = (T)itile[2 * t + 1] / scale;
+        } else {
+            re = tile[2 * t];
+            im = tile[2 * t + 1];
+            if (re == (T)0 && im == (T)0) continue;
+        }
         const int tc = t % CTZ, tr = (t / CTZ) % CTR, mq = t / (CTZ * CTR);
         const int jj = tj0 + tr;
         int ll = tl0 + tc;
