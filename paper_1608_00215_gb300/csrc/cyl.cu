@@ -49,12 +49,14 @@ struct pic_cyl {
     struct Sp {
         double q, m;
         int64_t n;
-        void *w, *x[3], *u[3];   // current arrays (sorted by bin)
-        void* alt[7];            // the other buffer of w, x, u (sort target, scratch)
-        int32_t *pid, *pid_alt;  // input index of each particle
+        void *w, *x[3], *u[3];   // buffer 0 of the particle arrays
+        void* alt[7];            // buffer 1 (w, x, u); the device state says which is current
+        int32_t *pid, *pid_alt;  // input index of each particle (buffers 0 and 1)
+        int32_t* starts;         // per bin: first particle (nbins + 1), from the last sort
+        void* state;             // CylSortState in device memory
     } sp[PIC_MAX_SPECIES];
     int32_t *key, *rank;         // per particle of the largest species: bin and rank in bin
-    int32_t *counts, *starts;    // per bin: particles, first particle (nbins + 1)
+    int32_t* counts;             // per bin: particles (during a sort)
     int nbz = 0, nbins = 0;
     int64_t G;          // nr * nz
     char* ws;
@@ -97,8 +99,8 @@ size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
 struct CylLayout {
     size_t alpha, Kd, Kt, syn, fwd, tmp64, tab, EBh, Sh, Rn, Fr, Dr, W1, W2, scratch, kdesc, gdesc, wsum, status,
-        sp[PIC_MAX_SPECIES][7], alt[PIC_MAX_SPECIES][7], pid[PIC_MAX_SPECIES][2], key, rank, counts, starts, fftwork,
-        total;
+        sp[PIC_MAX_SPECIES][7], alt[PIC_MAX_SPECIES][7], pid[PIC_MAX_SPECIES][2], starts[PIC_MAX_SPECIES],
+        state[PIC_MAX_SPECIES], key, rank, counts, fftwork, total;
 };
 
 // Particle bins of the sorted deposit: CBR x CBZ cells in (r, z); the deposit tile of a bin
@@ -146,11 +148,14 @@ CylLayout cyl_layout(const pic_cyl_config& c, const int64_t* n, int ns, size_t f
         L.pid[k][1] = take(n[k] * 4);
         nmax = std::max(nmax, n[k]);
     }
+    const size_t nb = cyl_nbins(c.nr, c.nz);
+    for (int k = 0; k < ns; ++k) {
+        L.starts[k] = take((nb + 1) * 4);
+        L.state[k] = take(32);
+    }
     L.key = take(nmax * 4);
     L.rank = take(nmax * 4);
-    const size_t nb = cyl_nbins(c.nr, c.nz);
     L.counts = take(nb * 4);
-    L.starts = take((nb + 1) * 4);
     L.fftwork = take(std::max<size_t>(fft_work, 1));
     L.total = o;
     return L;
@@ -489,13 +494,24 @@ __global__ void cyl_init_fields_kernel(C* EBh, C* Rn, const C* Sh, const double*
 
 // ---- particles -----------------------------------------------------------------------------
 
+// Re-sort bookkeeping of one species, in device memory: the passes count the particles that
+// end a step outside their bin, the next step sorts only when they exceed a threshold (or a
+// sort is forced), and the sort flips which buffer is current.
+struct CylSortState {
+    int sel;                    // current buffer: 0 (w, x, u, pid) or 1 (alt, pid_alt)
+    int force;                  // sort at the next step whatever the count
+    int need;                   // this step sorts
+    int pad;
+    unsigned long long moved;   // particles outside their bin after the last pass
+};
+
 template <typename T>
 struct CylPassK {
     typedef typename cplx<T>::type C;
     const C* F;   // [M][6][nr][nz] E_r, E_t, E_z, B_r, B_t, B_z
     C* D;         // [M][4][nr][nz] J_r, J_t, J_z, rho
-    T *x, *y, *z, *ux, *uy, *uz;
-    const T* w;
+    T* buf[2][7]; // the two particle buffers: w, x, y, z, ux, uy, uz
+    CylSortState* state;
     int64_t n;
     T q, qdt2m, inv_c2, hdt, vgal, dr, dz, Lz, c2pi_drdz;
     int nr, nz, M;
@@ -672,6 +688,19 @@ __device__ __forceinline__ T wrap_len(T z, T L) {
     return z;
 }
 
+// Bin of a particle at (x, y, z): its radial cell floor(r / dr) (beyond the extent, which
+// is flagged elsewhere: the last row) and its axial cell, periodic.
+template <typename T>
+__device__ __forceinline__ int cyl_bin_of(T x, T y, T z, T inv_dr, T inv_dz, int nr, int nz, int nbz) {
+    const T r = sqrt(x * x + y * y);
+    const T u = r * inv_dr, v = floor(z * inv_dz);
+    const int jc = (u >= (T)0 && u < (T)nr) ? (int)u : nr - 1;
+    int lc = (v >= (T)-nz && v < (T)(2 * nz)) ? (int)v : 0;
+    if (lc < 0) lc += nz;
+    if (lc >= nz) lc -= nz;
+    return (jc / CBR) * nbz + lc / CBZ;
+}
+
 // One CTA per (r, z) bin of CBR x CBZ cells, its particles (sorted by bin) one per thread.
 // step: gather at x^n, Boris, half drift, J^{n+1/2}, half drift, rho^{n+1}; deposit only
 // (step = 0): rho at the current positions. The deposits of the bin's particles are summed
@@ -680,8 +709,8 @@ __device__ __forceinline__ T wrap_len(T z, T L) {
 // (Summing the tile in 64-bit fixed point instead was slower: 6.1 against 4.8 ms per step
 // for 16.7M particles.)
 template <typename T>
-__global__ void __launch_bounds__(256) cyl_particle_kernel(CylPassK<T> p, const int32_t* __restrict__ starts,
-                                                           int nbz, int step) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
+    cyl_particle_kernel(CylPassK<T> p, const int32_t* __restrict__ starts, int nbz, int step) {
     typedef typename cplx<T>::type C;
     extern __shared__ __align__(16) unsigned char cyl_smem[];
     const int nt = p.M * 4 * CTR * CTZ;
@@ -689,6 +718,16 @@ __global__ void __launch_bounds__(256) cyl_particle_kernel(CylPassK<T> p, const 
     C* ftile = reinterpret_cast<C*>(cyl_smem + (size_t)2 * nt * sizeof(T));   // [M][6][CTR][CTZ]
     const int bin = blockIdx.x;
     const int tj0 = (bin / nbz) * CBR - CPAD, tl0 = (bin % nbz) * CBZ - CPAD;
+    const int sel = p.state->sel;   // the current particle buffer
+    const T* const pw = p.buf[sel][0];
+    T* const px = p.buf[sel][1];
+    T* const py = p.buf[sel][2];
+    T* const pz = p.buf[sel][3];
+    T* const pux = p.buf[sel][4];
+    T* const puy = p.buf[sel][5];
+    T* const puz = p.buf[sel][6];
+    const T inv_dr = (T)1 / p.dr, inv_dz = (T)1 / p.dz;
+    unsigned moved = 0;
     for (int t = threadIdx.x; t < 2 * nt; t += blockDim.x) tile[t] = (T)0;
     if (step) {   // the bin's mode fields (nodes outside 0 .. nr - 1 are never read)
         const int64_t G = (int64_t)p.nr * p.nz;
@@ -711,7 +750,7 @@ __global__ void __launch_bounds__(256) cyl_particle_kernel(CylPassK<T> p, const 
     T scale = (T)1;
     if constexpr (sizeof(T) == 4) {
         float a = 0.f;
-        for (int i = beg + threadIdx.x; i < end; i += blockDim.x) a += fabsf((float)(p.q * p.w[i]));
+        for (int i = beg + threadIdx.x; i < end; i += blockDim.x) a += fabsf((float)(p.q * pw[i]));
         for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
         if ((threadIdx.x & 31) == 0) s_abs[threadIdx.x >> 5] = a;
         __syncthreads();
@@ -726,9 +765,9 @@ __global__ void __launch_bounds__(256) cyl_particle_kernel(CylPassK<T> p, const 
     }
     __syncthreads();
     for (int i = beg + threadIdx.x; i < end; i += blockDim.x) {
-        T x = p.x[i], y = p.y[i], z = p.z[i];
-        T ux = p.ux[i], uy = p.uy[i], uz = p.uz[i];
-        const T qw = p.q * p.w[i];
+        T x = px[i], y = py[i], z = pz[i];
+        T ux = pux[i], uy = puy[i], uz = puz[i];
+        const T qw = p.q * pw[i];
         if (!step) {
             const T val[1] = {qw};
             cyl_deposit(p, tile, tj0, tl0, x, y, z, 3, 1, val, itile, scale);
@@ -765,13 +804,16 @@ __global__ void __launch_bounds__(256) cyl_particle_kernel(CylPassK<T> p, const 
         z = wrap_len(z + (vz - p.vgal) * p.hdt, p.Lz);
         const T val[1] = {qw};
         cyl_deposit(p, tile, tj0, tl0, x, y, z, 3, 1, val, itile, scale);
-        p.x[i] = x;
-        p.y[i] = y;
-        p.z[i] = z;
-        p.ux[i] = ux;
-        p.uy[i] = uy;
-        p.uz[i] = uz;
+        px[i] = x;
+        py[i] = y;
+        pz[i] = z;
+        pux[i] = ux;
+        puy[i] = uy;
+        puz[i] = uz;
+        moved += cyl_bin_of(x, y, z, inv_dr, inv_dz, p.nr, p.nz, nbz) != bin;
     }
+    for (int o = 16; o > 0; o >>= 1) moved += __shfl_down_sync(0xffffffffu, moved, o);
+    if ((threadIdx.x & 31) == 0 && moved) atomicAdd(&p.state->moved, (unsigned long long)moved);
     __syncthreads();
     const int64_t G = (int64_t)p.nr * p.nz;
     for (int t = threadIdx.x; t < nt; t += blockDim.x) {
@@ -801,17 +843,16 @@ __global__ void __launch_bounds__(256) cyl_particle_kernel(CylPassK<T> p, const 
 // atomic ranks) -------------------------------------------------------------------------
 
 template <typename T>
-__global__ void cyl_key_kernel(const T* __restrict__ x, const T* __restrict__ y, const T* __restrict__ z, int64_t n,
-                               T inv_dr, T inv_dz, int nr, int nz, int nbz, int32_t* key, int32_t* rank,
-                               int32_t* counts) {
+__global__ void cyl_key_kernel(const CylSortState* __restrict__ sst, const T* x0, const T* y0, const T* z0,
+                               const T* x1, const T* y1, const T* z1, int64_t n, T inv_dr, T inv_dz, int nr, int nz,
+                               int nbz, int32_t* key, int32_t* rank, int32_t* counts) {
+    if (!sst->need) return;
+    const bool b = sst->sel != 0;
+    const T* x = b ? x1 : x0;
+    const T* y = b ? y1 : y0;
+    const T* z = b ? z1 : z0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const T r = sqrt(x[i] * x[i] + y[i] * y[i]);
-        const T u = r * inv_dr, v = floor(z[i] * inv_dz);
-        int jc = (u >= (T)0 && u < (T)nr) ? (int)u : nr - 1;   // beyond the extent (flagged later): last bin row
-        int lc = (v >= (T)-nz && v < (T)(2 * nz)) ? (int)v : 0;
-        if (lc < 0) lc += nz;
-        if (lc >= nz) lc -= nz;
-        const int k = (jc / CBR) * nbz + lc / CBZ;
+        const int k = cyl_bin_of(x[i], y[i], z[i], inv_dr, inv_dz, nr, nz, nbz);
         key[i] = k;
         // particles arrive nearly sorted (last step's order), so neighbouring lanes share
         // bins: one atomic per bin and warp, ranks from the lanes' order
@@ -825,9 +866,24 @@ __global__ void cyl_key_kernel(const T* __restrict__ x, const T* __restrict__ y,
     }
 }
 
+// Whether this step re-sorts species' particles: when a sort is forced or more than
+// `threshold` particles ended the last pass outside their bins. Clears the count.
+__global__ void cyl_sort_decide_kernel(CylSortState* sst, unsigned long long threshold) {
+    sst->need = sst->force || sst->moved > threshold;
+    sst->force = 0;
+    sst->moved = 0;
+}
+
+// After a sort, the other buffer is current.
+__global__ void cyl_sort_flip_kernel(CylSortState* sst) {
+    if (sst->need) sst->sel ^= 1;
+}
+
 // Exclusive scan of the bin counts (one CTA of 1024 threads, each a contiguous segment).
-__global__ void __launch_bounds__(1024) cyl_scan_kernel(const int32_t* __restrict__ counts, int32_t* starts,
+__global__ void __launch_bounds__(1024) cyl_scan_kernel(const CylSortState* __restrict__ sst,
+                                                        const int32_t* __restrict__ counts, int32_t* starts,
                                                         int nbins) {
+    if (!sst->need) return;
     __shared__ int32_t part[1024];
     const int per = (nbins + 1023) / 1024;
     const int a = threadIdx.x * per, e = min(a + per, nbins);
@@ -854,9 +910,22 @@ struct CylArrays {
     int32_t* pid;
 };
 
+// Particle buffer b (0 or 1) of a species.
+CylArrays cyl_buffer(const pic_cyl::Sp& sp, int b) {
+    CylArrays a;
+    void* b0[7] = {sp.w, sp.x[0], sp.x[1], sp.x[2], sp.u[0], sp.u[1], sp.u[2]};
+    for (int q = 0; q < 7; ++q) a.a[q] = b ? sp.alt[q] : b0[q];
+    a.pid = b ? sp.pid_alt : sp.pid;
+    return a;
+}
+
 template <typename T>
-__global__ void cyl_scatter_kernel(CylArrays src, CylArrays dst, int64_t n, const int32_t* __restrict__ key,
-                                   const int32_t* __restrict__ rank, const int32_t* __restrict__ starts) {
+__global__ void cyl_scatter_kernel(const CylSortState* __restrict__ sst, CylArrays b0, CylArrays b1, int64_t n,
+                                   const int32_t* __restrict__ key, const int32_t* __restrict__ rank,
+                                   const int32_t* __restrict__ starts) {
+    if (!sst->need) return;
+    const CylArrays& src = sst->sel ? b1 : b0;
+    const CylArrays& dst = sst->sel ? b0 : b1;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t o = (int64_t)starts[key[i]] + rank[i];
 #pragma unroll
@@ -1066,13 +1135,11 @@ CylPassK<T> passk(pic_cyl* s, int k) {
     const pic_cyl_config& c = s->cfg;
     p.F = (const C*)s->Fr;
     p.D = (C*)s->Dr;
-    p.x = (T*)s->sp[k].x[0];
-    p.y = (T*)s->sp[k].x[1];
-    p.z = (T*)s->sp[k].x[2];
-    p.ux = (T*)s->sp[k].u[0];
-    p.uy = (T*)s->sp[k].u[1];
-    p.uz = (T*)s->sp[k].u[2];
-    p.w = (const T*)s->sp[k].w;
+    for (int b = 0; b < 2; ++b) {
+        const CylArrays a = cyl_buffer(s->sp[k], b);
+        for (int q = 0; q < 7; ++q) p.buf[b][q] = (T*)a.a[q];
+    }
+    p.state = (CylSortState*)s->sp[k].state;
     p.n = s->sp[k].n;
     p.q = (T)s->sp[k].q;
     p.qdt2m = (T)(s->sp[k].q * c.dt / (2.0 * s->sp[k].m));
@@ -1090,34 +1157,26 @@ CylPassK<T> passk(pic_cyl* s, int k) {
     return p;
 }
 
-// Counting sort of species k into the (r, z) bins: keys and ranks, bin starts, scatter of
-// every array (and the input indices) into the other buffer, then the buffers swap.
+// Counting sort of species k into the (r, z) bins, when the device decides that it is due
+// (more than 1/64 of the particles outside their bins after the last pass, or forced): keys
+// and ranks, bin starts, scatter of every array (and the input indices) into the other
+// buffer, which then becomes current. Otherwise every kernel of it returns at once.
 template <typename T>
 int sort_species(pic_cyl* s, int k, cudaStream_t st) {
     pic_cyl::Sp& sp = s->sp[k];
     const int64_t n = sp.n;
+    CylSortState* sst = (CylSortState*)sp.state;
+    const CylArrays b0 = cyl_buffer(sp, 0), b1 = cyl_buffer(sp, 1);
+    cyl_sort_decide_kernel<<<1, 1, 0, st>>>(sst, (unsigned long long)(n / 64));
     GP_CUDA(cudaMemsetAsync(s->counts, 0, (size_t)s->nbins * 4, st));
-    cyl_key_kernel<T><<<gridn(n), 256, 0, st>>>((const T*)sp.x[0], (const T*)sp.x[1], (const T*)sp.x[2], n,
+    cyl_key_kernel<T><<<gridn(n), 256, 0, st>>>(sst, (const T*)b0.a[1], (const T*)b0.a[2], (const T*)b0.a[3],
+                                                (const T*)b1.a[1], (const T*)b1.a[2], (const T*)b1.a[3], n,
                                                 (T)(1.0 / s->cfg.dr), (T)(1.0 / s->cfg.dz), s->cfg.nr, s->cfg.nz,
                                                 s->nbz, s->key, s->rank, s->counts);
-    cyl_scan_kernel<<<1, 1024, 0, st>>>(s->counts, s->starts, s->nbins);
-    CylArrays src, dst;
-    void* cur[7] = {sp.w, sp.x[0], sp.x[1], sp.x[2], sp.u[0], sp.u[1], sp.u[2]};
-    for (int q = 0; q < 7; ++q) {
-        src.a[q] = cur[q];
-        dst.a[q] = sp.alt[q];
-    }
-    src.pid = sp.pid;
-    dst.pid = sp.pid_alt;
-    cyl_scatter_kernel<T><<<gridn(n), 256, 0, st>>>(src, dst, n, s->key, s->rank, s->starts);
+    cyl_scan_kernel<<<1, 1024, 0, st>>>(sst, s->counts, sp.starts, s->nbins);
+    cyl_scatter_kernel<T><<<gridn(n), 256, 0, st>>>(sst, b0, b1, n, s->key, s->rank, sp.starts);
+    cyl_sort_flip_kernel<<<1, 1, 0, st>>>(sst);
     GP_CUDA(cudaGetLastError());
-    sp.w = dst.a[0];
-    for (int d = 0; d < 3; ++d) {
-        sp.x[d] = dst.a[1 + d];
-        sp.u[d] = dst.a[4 + d];
-    }
-    for (int q = 0; q < 7; ++q) sp.alt[q] = cur[q];
-    std::swap(sp.pid, sp.pid_alt);
     return PIC_OK;
 }
 
@@ -1128,7 +1187,7 @@ int particles_t(pic_cyl* s, int step, cudaStream_t st) {
     for (int k = 0; k < s->nspecies; ++k) {
         if (s->sp[k].n == 0) continue;
         GP_CHECK(sort_species<T>(s, k, st));
-        cyl_particle_kernel<T><<<s->nbins, 256, tile, st>>>(passk<T>(s, k), s->starts, s->nbz, step);
+        cyl_particle_kernel<T><<<s->nbins, 256, tile, st>>>(passk<T>(s, k), s->sp[k].starts, s->nbz, step);
         GP_CUDA(cudaGetLastError());
     }
     return PIC_OK;
@@ -1255,7 +1314,10 @@ int pic_cyl_init(const pic_cyl_config* cfg, const pic_cyl_species* species, int 
     s->key = (int32_t*)(w + L.key);
     s->rank = (int32_t*)(w + L.rank);
     s->counts = (int32_t*)(w + L.counts);
-    s->starts = (int32_t*)(w + L.starts);
+    for (int k = 0; k < nspecies; ++k) {
+        s->sp[k].starts = (int32_t*)(w + L.starts[k]);
+        s->sp[k].state = w + L.state[k];
+    }
     s->nbz = cyl_nbz(cfg->nz);
     s->nbins = cyl_nbins(cfg->nr, cfg->nz);
 #define CYL_TRY(expr)           \
@@ -1274,6 +1336,8 @@ int pic_cyl_init(const pic_cyl_config* cfg, const pic_cyl_species* species, int 
         if (!b) continue;
         CYL_CUDA(cudaMemcpyAsync(s->sp[k].w, species[k].w, b, cudaMemcpyDefault, st));
         cyl_iota_kernel<<<gridn(species[k].n), 256, 0, st>>>(s->sp[k].pid, species[k].n);
+        const CylSortState init = {0, 1, 0, 0, 0ull};   // buffer 0 current, first step sorts
+        CYL_CUDA(cudaMemcpyAsync(s->sp[k].state, &init, sizeof(init), cudaMemcpyHostToDevice, st));
         for (int d = 0; d < 3; ++d) {
             CYL_CUDA(cudaMemcpyAsync(s->sp[k].x[d], species[k].x[d], b, cudaMemcpyDefault, st));
             CYL_CUDA(cudaMemcpyAsync(s->sp[k].u[d], species[k].u[d], b, cudaMemcpyDefault, st));
@@ -1443,21 +1507,26 @@ int pic_cyl_get(pic_cyl* s, int which, void* dst, size_t bytes, void* stream) {
 
 int pic_cyl_get_particles(pic_cyl* s, int k, void* x[3], void* u[3], void* stream) {
     if (!s || k < 0 || k >= s->nspecies || !x || !u) return fail(PIC_EINVAL, "bad cyl run, species or arrays");
-    // the run keeps its particles sorted by bin: each array goes back to input order through
-    // the sort's other buffer (free between steps), then out
+    // the run keeps its particles sorted by bin, in one of two buffers (the device state
+    // says which): each array goes back to input order through the other buffer, then out
     cudaStream_t st = (cudaStream_t)stream;
     const pic_cyl::Sp& sp = s->sp[k];
     const int64_t n = sp.n;
+    if (n == 0) return PIC_OK;
+    CylSortState h;
+    GP_CUDA(cudaMemcpyAsync(&h, sp.state, sizeof(h), cudaMemcpyDeviceToHost, st));
+    GP_CUDA(cudaStreamSynchronize(st));
+    const CylArrays cur = cyl_buffer(sp, h.sel), other = cyl_buffer(sp, h.sel ^ 1);
     const size_t b = (size_t)n * (s->cfg.precision == 64 ? 8 : 4);
     for (int d = 0; d < 6; ++d) {
         void* dst = d < 3 ? x[d] : u[d - 3];
-        if (!dst || n == 0) continue;
-        const void* src = d < 3 ? sp.x[d] : sp.u[d - 3];
-        void* tmp = sp.alt[1 + d];
+        if (!dst) continue;
+        const void* src = cur.a[1 + d];
+        void* tmp = other.a[1 + d];
         if (s->cfg.precision == 64)
-            cyl_unpermute_kernel<double><<<gridn(n), 256, 0, st>>>((const double*)src, sp.pid, (double*)tmp, n);
+            cyl_unpermute_kernel<double><<<gridn(n), 256, 0, st>>>((const double*)src, cur.pid, (double*)tmp, n);
         else
-            cyl_unpermute_kernel<float><<<gridn(n), 256, 0, st>>>((const float*)src, sp.pid, (float*)tmp, n);
+            cyl_unpermute_kernel<float><<<gridn(n), 256, 0, st>>>((const float*)src, cur.pid, (float*)tmp, n);
         GP_CUDA(cudaGetLastError());
         GP_CUDA(cudaMemcpyAsync(dst, tmp, b, cudaMemcpyDefault, st));
     }

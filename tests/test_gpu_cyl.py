@@ -132,9 +132,12 @@ def test_initial_state(gp, nz):
     sim.close()
 
 
-@pytest.mark.parametrize("nz,nmodes,cc", [(45, 3, True), (32, 2, True), (32, 3, False), (45, 1, True)])
-def test_steps_fp64(gp, nz, nmodes, cc):
-    wl = _workload(nz=nz, nmodes=nmodes)
+@pytest.mark.parametrize("nz,nmodes,cc,galilean", [(45, 3, True, True), (32, 2, True, True), (32, 3, False, True),
+                                                  (45, 1, True, True), (45, 2, True, False)])
+def test_steps_fp64(gp, nz, nmodes, cc, galilean):
+    """galilean = False: the column moves at 0.98 c over a grid at rest, about a cell per
+    step, so the particles leave their bins and the conditional re-sort runs."""
+    wl = _workload(nz=nz, nmodes=nmodes, galilean=galilean)
     sim = _sim(gp, wl, cc=cc)
     cfgs, st = _oracle(wl, cc=cc)
     sim.step(1)
