@@ -494,7 +494,9 @@ int pic_cyl_step(pic_cyl* run, int nsteps, void* stream);
 /* Copy a PIC_CYL_* buffer to dst (host or device); `bytes` must equal its size. */
 int pic_cyl_get(pic_cyl* run, int which, void* dst, size_t bytes, void* stream);
 
-/* Copy species k's positions and momenta out (any pointer may be NULL). */
+/* Copy species k's positions and momenta out, in input order (any pointer may be NULL).
+ * The run keeps its particles sorted by (r, z) bin in one of two buffers; this call reads
+ * which one on `stream` (synchronising it) and restores the input order on the device. */
 int pic_cyl_get_particles(pic_cyl* run, int species, void* x[3], void* u[3], void* stream);
 
 /* Field energy W = (eps0/2) sum_m (1 for m = 0, else 2) sum_{j,l} (|E_m|^2 + c^2 |B_m|^2) V_j
