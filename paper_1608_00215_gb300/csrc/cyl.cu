@@ -341,45 +341,65 @@ __global__ void cyl_wavenumbers_kernel(double* Kd, T* Kt, const double* alpha, i
 // ---- transforms --------------------------------------------------------------------------
 
 // Y_b = A_b X_b for batches b (blockIdx.z): A_b real nr x nr, X_b and Y_b complex nr x nz
-// (z contiguous). 32 x 32 output tiles, 32 x 8 threads, shared-memory tiles of A and X.
+// (z contiguous). 64 x 64 output tiles (rows i, columns z) of 256 threads, each thread 4
+// rows x 4 columns (rows ty + 16 r, columns tx + 16 c); A (transposed) and X staged in
+// shared memory 16 values of j at a time, so that a thread's 8 loads per j feed 32 FMAs.
+constexpr int RM_T = 64, RM_K = 16;
 template <typename T>
 __global__ void __launch_bounds__(256) radial_matmul_kernel(const T* const* __restrict__ As,
                                                             const typename cplx<T>::type* const* __restrict__ Xs,
                                                             typename cplx<T>::type* const* __restrict__ Ys, int nr,
                                                             int nz) {
     typedef typename cplx<T>::type C;
-    __shared__ T sA[32][33];
-    __shared__ C sX[32][33];
+    __shared__ T sA[RM_K][RM_T + 1];   // [j][i]
+    __shared__ C sX[RM_K][RM_T];       // [j][z]
     const T* A = As[blockIdx.z];
     const C* X = Xs[blockIdx.z];
     C* Y = Ys[blockIdx.z];
-    const int i0 = blockIdx.y * 32, z0 = blockIdx.x * 32;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    C acc[4];
+    const int i0 = blockIdx.y * RM_T, z0 = blockIdx.x * RM_T;
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    C acc[4][4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) acc[k] = mk<C>(0.0, 0.0);
-    for (int j0 = 0; j0 < nr; j0 += 32) {
-        for (int k = ty; k < 32; k += 8) {
-            sA[k][tx] = (i0 + k < nr && j0 + tx < nr) ? A[(int64_t)(i0 + k) * nr + j0 + tx] : (T)0;
-            sX[k][tx] = (j0 + k < nr && z0 + tx < nz) ? X[(int64_t)(j0 + k) * nz + z0 + tx] : mk<C>(0.0, 0.0);
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = mk<C>(0.0, 0.0);
+    for (int j0 = 0; j0 < nr; j0 += RM_K) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int idx = t + 256 * e;
+            const int ia = idx >> 4, ka = idx & 15;       // A: row ia, column j0 + ka
+            sA[ka][ia] = (i0 + ia < nr && j0 + ka < nr) ? A[(int64_t)(i0 + ia) * nr + j0 + ka] : (T)0;
+            const int kx = idx >> 6, zx = idx & 63;       // X: row j0 + kx, column z0 + zx
+            sX[kx][zx] = (j0 + kx < nr && z0 + zx < nz) ? X[(int64_t)(j0 + kx) * nz + z0 + zx] : mk<C>(0.0, 0.0);
         }
         __syncthreads();
-#pragma unroll 8
-        for (int jj = 0; jj < 32; ++jj) {
-            const C x = sX[jj][tx];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const T a = sA[ty + 8 * k][jj];
-                acc[k].x = fma(a, x.x, acc[k].x);
-                acc[k].y = fma(a, x.y, acc[k].y);
-            }
+        for (int k = 0; k < RM_K; ++k) {
+            T av[4];
+            C xv[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) av[r] = sA[k][ty + 16 * r];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) xv[c] = sX[k][tx + 16 * c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    acc[r][c].x = fma(av[r], xv[c].x, acc[r][c].x);
+                    acc[r][c].y = fma(av[r], xv[c].y, acc[r][c].y);
+                }
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int i = i0 + ty + 8 * k;
-        if (i < nr && z0 + tx < nz) Y[(int64_t)i * nz + z0 + tx] = acc[k];
+    for (int r = 0; r < 4; ++r) {
+        const int i = i0 + ty + 16 * r;
+        if (i >= nr) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int z = z0 + tx + 16 * c;
+            if (z < nz) Y[(int64_t)i * nz + z] = acc[r][c];
+        }
     }
 }
 
@@ -1038,7 +1058,7 @@ std::vector<const void*> radial_tables(const pic_cyl* s) {
 // One launch of the radial products of table `set` (nb batches).
 int radial_products(pic_cyl* s, int set, int nb, cudaStream_t st) {
     void** d = (void**)s->gdesc + (size_t)set * 3 * GDESC_MAX;
-    const dim3 grid((s->cfg.nz + 31) / 32, (s->cfg.nr + 31) / 32, nb), block(32, 8);
+    const dim3 grid((s->cfg.nz + RM_T - 1) / RM_T, (s->cfg.nr + RM_T - 1) / RM_T, nb), block(256);
     if (s->cfg.precision == 64)
         radial_matmul_kernel<double><<<grid, block, 0, st>>>((const double* const*)d,
                                                              (const double2* const*)(d + GDESC_MAX),
