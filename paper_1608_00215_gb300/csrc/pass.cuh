@@ -265,6 +265,18 @@ constexpr int CELL_CHUNK = 256;
 constexpr int CELL_STRIDE = CELL_CHUNK + CELL_CHUNK / 32;
 __host__ __device__ __forceinline__ int cell_slot(int j) { return j + (j >> 5); }
 
+// Asynchronous copy of one 4- or 8-byte element from global to shared memory (cp.async):
+// the data goes to shared memory without passing through registers, so a lane can have
+// all of its chunk's loads in flight at once. async_wait_all waits for the calling
+// thread's copies; a __syncwarp after it publishes them to the warp.
+template <int BYTES>
+__device__ __forceinline__ void async_copy(void* dst_smem, const void* src) {
+    static_assert(BYTES == 4 || BYTES == 8, "cp.async.ca copies 4, 8 or 16 bytes");
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 __host__ __device__ constexpr size_t stage_bytes(int NW, size_t T, int dep) {
     return dep == DEP_CELL ? align16((size_t)CELL_STRIDE * (4 + 6 * T))
            : (T == 4 && NW == 4 && (dep == DEP_ROW || dep == DEP_ROWU))
@@ -1674,16 +1686,17 @@ __device__ __forceinline__ void cell_pass_body(const PassK<T>& p, const int b) {
             for (int lo = A; lo < Bend; lo += CELL_CHUNK) {
                 const int hi = min(lo + CELL_CHUNK, Bend);
                 bool moved = false;   // a particle of this lane changed cell in this chunk
-                // stage in, coalesced
+                // stage in, coalesced, every load of the chunk in flight at once
                 for (int j = lane; j < hi - lo; j += 32) {
                     const int q = cell_slot(j);
-                    st_cell[q] = sp.cell[lo + j];
+                    async_copy<4>(&st_cell[q], &sp.cell[lo + j]);
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
-                        st_v[d * CELL_STRIDE + q] = sp.off[d][lo + j];
-                        st_v[(3 + d) * CELL_STRIDE + q] = sp.u[d][lo + j];
+                        async_copy<sizeof(T)>(&st_v[d * CELL_STRIDE + q], &sp.off[d][lo + j]);
+                        async_copy<sizeof(T)>(&st_v[(3 + d) * CELL_STRIDE + q], &sp.u[d][lo + j]);
                     }
                 }
+                async_wait_all();
                 __syncwarp();
                 const int i0 = max(beg, lo), i1 = min(end, hi);
                 // one particle at staging slot j from its loaded values; `pushed`: E, B were
