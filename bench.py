@@ -165,8 +165,9 @@ def fp32_peak_tflops(sms=None):
 # dram__bytes_write.sum from ncu captures of the same kernels on the 64x64x128 case of
 # this plasma (16 particles per cell), divided by its particle count (row deposit:
 # 444.4 MB for 8,388,608 particles; grouped deposit, two species sharing groups:
-# 449.5 MB); scaled to a launch by the particles it processes.
-PASS_TRAFFIC = {(3, 32, 0, 0): (53.6, 0.0), (3, 32, 0, 1): (53.0, 0.0)}
+# 449.5 MB; linear shapes, one thread per cell: 411.0 MB); scaled to a launch by the
+# particles it processes.
+PASS_TRAFFIC = {(3, 32, 0, 0): (53.6, 0.0), (3, 32, 0, 1): (53.0, 0.0), (1, 32, 0, 4): (49.0, 0.0)}
 
 
 def pass_kernel_name(order, margin, deposit, equal_pair):
@@ -215,8 +216,10 @@ def linear_pass_roofline(grid, steps, warmup, hbm, peak_kind):
     part_ms = part["ms"] / max(1, part["count"])
     nbytes = particle_bytes(wl, 32)
     achieved = nbytes / (part_ms * 1e-3) / 1e9
+    tr = PASS_TRAFFIC.get((1, 32, tuned["tile_margin"], tuned["deposit"]))
+    traffic = None if tr is None else tr[0] * wl.nparticles + tr[1] * wl.ncells
     return {"bound": "hbm", "kernel": pass_kernel_name(1, tuned["tile_margin"], tuned["deposit"], True),
-            "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+            "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
             "peak_kind": peak_kind, "algorithmic_bytes_per_launch": nbytes, "ms_per_launch": part_ms,
             "ms_per_step": sum(v["ms"] / max(1, v["count"]) for v in stages.values() if v["count"]),
             "tuned": tuned, "workload": wl.name + " (linear shapes, otherwise the bench plasma)",

@@ -301,7 +301,10 @@ int pic_step_decomposed(pic_sim* sim, int ndomains, int guard, int nsteps, void*
 
 /* Field energy W = (eps0/2) sum (|E|^2 + c^2 |B|^2) dV of the real E^n, B^n,
  * written as one double to the DEVICE address out_dev. Sets
- * PIC_STATUS_NONFINITE in the status word if any field value is not finite. */
+ * PIC_STATUS_NONFINITE in the status word if any field value is not finite.
+ * Precision 64 squares and sums in FP64. Precision 32 forms each node's |E|^2
+ * and |B|^2 in FP32 (finite while every component is below 1.8e19) and sums the
+ * nodes in FP64. The same holds for pic_field_energy_noalloc. */
 int pic_diag_energy(pic_sim* sim, double* out_dev, void* stream);
 
 /* Copy a buffer out to dst (host or device, `bytes` must equal its size). */

@@ -577,6 +577,23 @@ int pic_init(const pic_config* cfg, const pic_species* species, int nspecies, vo
                                  st) == cudaSuccess ? PIC_OK : fail(PIC_ECUDA, "threshold"));
     }
     const size_t Tb = real_bytes(s);
+    // The k-space tables depend on the configuration alone: they are built on the run's
+    // private stream while the particles are copied (or generated) and sorted on `st`,
+    // which waits for them before the initial fields.
+    struct EventPair {
+        cudaEvent_t a = nullptr, b = nullptr;
+        ~EventPair() {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } tev;
+    INIT_TRY(cudaEventCreateWithFlags(&tev.a, cudaEventDisableTiming) == cudaSuccess &&
+                     cudaEventCreateWithFlags(&tev.b, cudaEventDisableTiming) == cudaSuccess &&
+                     cudaEventRecord(tev.a, st) == cudaSuccess && cudaStreamWaitEvent(s->priv, tev.a, 0) == cudaSuccess
+                 ? PIC_OK : fail(PIC_ECUDA, "table stream events"));
+    count_launches(s, 2);   // wavenumbers, tables
+    INIT_TRY(launch_build_tables(s, s->priv));
+    INIT_TRY(cudaEventRecord(tev.b, s->priv) == cudaSuccess ? PIC_OK : fail(PIC_ECUDA, "table event"));
     for (int k = 0; k < nspecies; ++k) {
         // every bin range starts empty (a species with no particles is never sorted)
         INIT_TRY(cudaMemsetAsync(s->sp[k].bin_start, 0, (s->d.nbins + 1) * sizeof(int32_t), st) ==
@@ -605,8 +622,8 @@ int pic_init(const pic_config* cfg, const pic_species* species, int nspecies, vo
     }
     INIT_TRY(set_force_sort(s, st));
     INIT_TRY(sort_particles(s, st));
-    count_launches(s, 4);   // wavenumbers, tables, initial fields, scaled copy
-    INIT_TRY(launch_build_tables(s, st));
+    INIT_TRY(cudaStreamWaitEvent(st, tev.b, 0) == cudaSuccess ? PIC_OK : fail(PIC_ECUDA, "table wait"));
+    count_launches(s, 2);   // initial fields, scaled copy
     INIT_TRY(deposit_sources(s, PASS_DEPOSIT, st));
     INIT_TRY(exec_r2c(s, st));
     INIT_TRY(launch_init_fields(s, st));

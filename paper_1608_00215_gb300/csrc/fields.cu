@@ -478,6 +478,10 @@ __global__ void scale_copy_kernel(C* dst, const C* src, int64_t n, T s) {
 // Field energy, pass 1: per-block sums of E^2 and B^2 (FP64) into `part`, and
 // the non-finite flag. Pass 2 adds the partial sums in a fixed order, so the
 // result does not depend on scheduling.
+// FP32 fields: a node's |E|^2 and |B|^2 are formed in FP32 (three squares, relative
+// error a few 2^-24, finite while every component is below 1.8e19) and only the sums
+// over nodes run in FP64; this GPU's FP64 rate is low enough that squaring each
+// component in FP64 made the kernel several times slower than its memory traffic.
 template <typename T>
 __global__ void __launch_bounds__(256) energy_partial_kernel(const T* __restrict__ F, int64_t N,
                                                              double* __restrict__ part,
@@ -486,13 +490,22 @@ __global__ void __launch_bounds__(256) energy_partial_kernel(const T* __restrict
     bool bad = false;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
+        if constexpr (sizeof(T) == 4) {
+            const float e0 = F[i], e1 = F[N + i], e2 = F[2 * N + i];
+            const float b0 = F[3 * N + i], b1 = F[4 * N + i], b2 = F[5 * N + i];
+            se += (double)fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
+            sb += (double)fmaf(b0, b0, fmaf(b1, b1, b2 * b2));
+            bad |= !(isfinite(e0) && isfinite(e1) && isfinite(e2) && isfinite(b0) && isfinite(b1) &&
+                     isfinite(b2));
+        } else {
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            double v = (double)F[q * N + i];
-            double w = (double)F[(3 + q) * N + i];
-            se += v * v;
-            sb += w * w;
-            bad |= !isfinite(v) || !isfinite(w);
+            for (int q = 0; q < 3; ++q) {
+                double v = (double)F[q * N + i];
+                double w = (double)F[(3 + q) * N + i];
+                se += v * v;
+                sb += w * w;
+                bad |= !isfinite(v) || !isfinite(w);
+            }
         }
     }
     __shared__ double s_e[8], s_b[8];
