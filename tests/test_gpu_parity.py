@@ -194,6 +194,30 @@ def test_energy_matches_oracle(gp):
     sim.close()
 
 
+def test_energy_fp32_equals_fp64_sum_of_its_fields(gp):
+    """FP32 runs form each node's |E|^2 and |B|^2 in FP32 and sum the nodes in FP64: the
+    result equals the FP64 sum over the same FP32 field values to a few FP32 roundings;
+    a non-finite FP32 value still sets PIC_STATUS_NONFINITE."""
+    wl = gi.drifting_plasma(16, 12, 20, 10.0, galilean=False, shape_order=2, precision=32, jitter=0.3)
+    sim = gp.sim_from_workload(wl)
+    sim.step(3)
+    W = sim.energy()
+    E = sim.get(gp.BUF_E, device="cpu").double().numpy()
+    B = sim.get(gp.BUF_B, device="cpu").double().numpy()
+    torch.cuda.synchronize()
+    dV = wl.dx * wl.dy * wl.dz
+    ref = 0.5 * wl.eps0 * dV * (float((E * E).sum()) + wl.c ** 2 * float((B * B).sum()))
+    assert ref > 0 and abs(W - ref) < 1e-6 * ref
+    assert sim.status() == 0
+    Eh = sim.get(gp.BUF_E_HAT, device="cpu")
+    torch.cuda.synchronize()
+    Eh[1, 2, 1, 1] = complex(float("inf"), 0.0)
+    sim.set(gp.BUF_E_HAT, Eh)
+    assert not np.isfinite(sim.energy())
+    assert sim.status() & gp.PIC_STATUS_NONFINITE
+    sim.close()
+
+
 def test_graph_replay_equals_uncaptured_calls(gp):
     """pic_step (graph replay) and pic_gather_push + pic_field_update give the same
     state (to the rounding of the atomic deposit order)."""
