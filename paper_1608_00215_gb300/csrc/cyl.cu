@@ -538,6 +538,32 @@ struct CylPassK {
     int32_t* status;
 };
 
+// Divisions and reciprocal square roots of the particle pass: FP32 runs take the fast
+// division and the hardware reciprocal square root (CUDA's __fdividef and rsqrtf, within
+// 2 ulp, against the FP32 mode's 1e-4 tolerance to the FP64 oracle) instead of the
+// correctly rounded sequences and their special-case branches; FP64 runs keep the
+// correctly rounded forms.
+__device__ __forceinline__ float cyl_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double cyl_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float cyl_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double cyl_rsqrt(double x) { return 1.0 / sqrt(x); }
+
+// Radius and direction of (x, y): r, cos(theta), sin(theta) (theta = 0 on the axis).
+template <typename T>
+__device__ __forceinline__ void cyl_polar(T x, T y, T& r, T& cs, T& sn) {
+    const T rr = x * x + y * y;
+    if constexpr (sizeof(T) == 4) {
+        const T ir = rr > (T)0 ? cyl_rsqrt(rr) : (T)0;
+        r = rr * ir;
+        cs = rr > (T)0 ? x * ir : (T)1;
+        sn = y * ir;
+    } else {
+        r = sqrt(rr);
+        cs = r > (T)0 ? x / r : (T)1;
+        sn = r > (T)0 ? y / r : (T)0;
+    }
+}
+
 // Linear radial stencil of a particle at radius r: nodes j0 (folded onto 0 below the axis)
 // and j0 + 1, weights 1 - f and f. Returns false (and flags) outside the radial extent.
 template <typename T>
@@ -547,7 +573,7 @@ __device__ __forceinline__ bool radial_stencil(const CylPassK<T>& p, T r, int& j
         atomicOr(p.status, PIC_STATUS_BADINPUT);
         return false;
     }
-    const T u = r / p.dr - (T)0.5;
+    const T u = cyl_div(r, p.dr) - (T)0.5;
     const T fl = floor(u);
     int j = (int)fl;
     T f = u - fl;
@@ -565,7 +591,7 @@ __device__ __forceinline__ bool radial_stencil(const CylPassK<T>& p, T r, int& j
 
 template <typename T>
 __device__ __forceinline__ void axial_stencil(const CylPassK<T>& p, T z, int& l0, int& l1, T& w0, T& w1) {
-    const T u = z / p.dz;
+    const T u = cyl_div(z, p.dz);
     const T fl = floor(u);
     int l = (int)fl;
     const T f = u - fl;
@@ -584,8 +610,8 @@ template <typename T>
 __device__ void cyl_gather(const CylPassK<T>& p, const typename cplx<T>::type* ftile, int tj0, int tl0, T x, T y,
                            T z, T* E, T* B, bool& ok) {
     typedef typename cplx<T>::type C;
-    const T r = sqrt(x * x + y * y);
-    const T cs = r > (T)0 ? x / r : (T)1, sn = r > (T)0 ? y / r : (T)0;
+    T r, cs, sn;
+    cyl_polar(x, y, r, cs, sn);
     int j0, j1, l0, l1;
     T wr0, wr1, wz0, wz1;
     bool ghost;
@@ -647,15 +673,15 @@ template <typename T>
 __device__ void cyl_deposit(const CylPassK<T>& p, T* tile, int tj0, int tl0, T x, T y, T z, int q0, int nq,
                             const T* val, int* itile = nullptr, T scale = (T)1) {
     typedef typename cplx<T>::type C;
-    const T r = sqrt(x * x + y * y);
-    const T cs = r > (T)0 ? x / r : (T)1, sn = r > (T)0 ? y / r : (T)0;
+    T r, cs, sn;
+    cyl_polar(x, y, r, cs, sn);
     int j0, j1, l0, l1;
     T wr0, wr1, wz0, wz1;
     bool ghost;
     if (!radial_stencil(p, r, j0, j1, wr0, wr1, ghost)) return;
     axial_stencil(p, z, l0, l1, wz0, wz1);
     const int64_t G = (int64_t)p.nr * p.nz;
-    const T iv0 = (T)1 / (p.c2pi_drdz * ((T)j0 + (T)0.5)), iv1 = (T)1 / (p.c2pi_drdz * ((T)j1 + (T)0.5));
+    const T iv0 = cyl_div((T)1, p.c2pi_drdz * ((T)j0 + (T)0.5)), iv1 = cyl_div((T)1, p.c2pi_drdz * ((T)j1 + (T)0.5));
     // tile coordinates of the four nodes (-1: outside the tile)
     auto tcol = [&](int l) {
         int d = l - tl0;
@@ -702,9 +728,14 @@ __device__ void cyl_deposit(const CylPassK<T>& p, T* tile, int tj0, int tl0, T x
 
 template <typename T>
 __device__ __forceinline__ T wrap_len(T z, T L) {
-    z = fmod(z, L);
+    // a half drift moves a particle far less than L: one add or subtract, fmod otherwise
     if (z < (T)0) z += L;
-    if (z >= L) z -= L;
+    else if (z >= L) z -= L;
+    if (!(z >= (T)0 && z < L)) {
+        z = fmod(z, L);
+        if (z < (T)0) z += L;
+        if (z >= L) z -= L;
+    }
     return z;
 }
 
@@ -798,9 +829,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
         cyl_gather(p, ftile, tj0, tl0, x, y, z, E, B, ok);
         const T a = p.qdt2m;
         const T umx = ux + a * E[0], umy = uy + a * E[1], umz = uz + a * E[2];
-        const T igm = (T)1 / sqrt((T)1 + (umx * umx + umy * umy + umz * umz) * p.inv_c2);
+        const T igm = cyl_rsqrt((T)1 + (umx * umx + umy * umy + umz * umz) * p.inv_c2);
         const T tx = a * B[0] * igm, ty = a * B[1] * igm, tz = a * B[2] * igm;
-        const T s2 = (T)2 / ((T)1 + tx * tx + ty * ty + tz * tz);
+        const T s2 = cyl_div((T)2, (T)1 + tx * tx + ty * ty + tz * tz);
         const T sx = s2 * tx, sy = s2 * ty, sz = s2 * tz;
         const T upx = umx + (umy * tz - umz * ty);
         const T upy = umy + (umz * tx - umx * tz);
@@ -808,14 +839,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
         ux = umx + (upy * sz - upz * sy) + a * E[0];
         uy = umy + (upz * sx - upx * sz) + a * E[1];
         uz = umz + (upx * sy - upy * sx) + a * E[2];
-        const T igam = (T)1 / sqrt((T)1 + (ux * ux + uy * uy + uz * uz) * p.inv_c2);
+        const T igam = cyl_rsqrt((T)1 + (ux * ux + uy * uy + uz * uz) * p.inv_c2);
         const T vx = ux * igam, vy = uy * igam, vz = uz * igam;
         x += vx * p.hdt;
         y += vy * p.hdt;
         z = wrap_len(z + (vz - p.vgal) * p.hdt, p.Lz);
         {
-            const T r = sqrt(x * x + y * y);
-            const T cs = r > (T)0 ? x / r : (T)1, sn = r > (T)0 ? y / r : (T)0;
+            T r, cs, sn;
+            cyl_polar(x, y, r, cs, sn);
             const T val[3] = {qw * (vx * cs + vy * sn), qw * (-vx * sn + vy * cs), qw * vz};
             cyl_deposit(p, tile, tj0, tl0, x, y, z, 0, 3, val, itile, scale);
         }
