@@ -24,17 +24,20 @@ Modules:
 * ``cylindrical``  - the quasi-cylindrical field solver, one azimuthal mode with a
   discrete Hankel transform in r;
 * ``cylindrical_pic`` - the particle side of the quasi-cylindrical step (deposit and
-  gather per azimuthal mode, the fold across the axis) and the full step (no CUDA
-  path exists for this geometry yet);
+  gather per azimuthal mode, the fold across the axis) and the full step;
 * ``domain_decomposition`` - the field update on subdomains along z with guard
-  cells, for finite-order stencils (no CUDA path);
+  cells, for finite-order stencils;
 * ``pic``          - grid, deposit, gather, Boris push, Galilean drift,
   spectral current correction, the update, energy and residual diagnostics
   and the full step.
 
 Parity status: the coefficients, the vacuum update, the finite-order stencils,
 the deposit/gather, the FFT and the push are pinned against closed forms, quadrature, library
-routines and invariants in ``tests/test_oracle_*.py``. The full plasma step
-has no printed values in the paper to pin against: "parity unpinned" for the
-plasma step beyond those invariants and the qualitative NCI claim.
+routines and invariants in ``tests/test_oracle_*.py``. The paper prints no worked
+example of a plasma step, so the full step is pinned through what it must satisfy
+(``tests/test_oracle_step.py``): the exact vacuum plane wave over many steps, the
+boosted-Coulomb field as a fixed point, the textbook PSATD step at v_gal = 0, the
+discrete continuity equation and Gauss's law per mode over plasma steps, free
+streaming in Galilean coordinates, and the paper's stability claim (no growth at
+v_gal = v_drift, exponential growth at v_gal = 0).
 """

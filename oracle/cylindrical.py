@@ -2,7 +2,8 @@
 update in (r, z) with a discrete Hankel transform in r.
 
 Test infrastructure only (see ``oracle/__init__``). The particle side and the full
-step are in ``oracle.cylindrical_pic``; no CUDA path exists for this geometry.
+step are in ``oracle.cylindrical_pic``; the CUDA path of this geometry is checked
+against both in ``tests/test_gpu_cyl.py``.
 
 The paper runs its boosted-frame results in the quasi-cylindrical code it names
 (the implementation paragraph after the update equations). Reading, from general

@@ -1,7 +1,8 @@
 """Particle side of the quasi-cylindrical Galilean-PSATD step, and the full step.
 
 Test infrastructure only (see ``oracle/__init__``); the field solver is
-``oracle.cylindrical``. No CUDA path exists for this geometry.
+``oracle.cylindrical``. The CUDA path of this geometry is checked against both in
+``tests/test_gpu_cyl.py``.
 
 Readings (the paper gives no formulas for this geometry):
 

@@ -1,6 +1,7 @@
 """Domain decomposition of the field update with finite-order spectral stencils.
 
-Test infrastructure only (see ``oracle/__init__``). No CUDA path exists for it.
+Test infrastructure only (see ``oracle/__init__``). The CUDA path (all subdomains on
+one GPU) is checked against it in ``tests/test_gpu_decomposed.py``.
 
 The paper's conclusion names parallelisation by domain decomposition with
 arbitrary-order spectral solvers as the route to many processors: each subdomain
